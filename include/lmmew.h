@@ -1,0 +1,210 @@
+/*
+ * lmmew.h -- C ABI of the GB300 (sm_103a) list-mode multi-energy-window
+ * (LM-MEW) OSEM library for 2-D SPECT of isotopes with several emission peaks
+ * (Rahman et al., arXiv 2305.17111).
+ *
+ * The problem (paper Sec. "Problem formulation"): a voxelised activity lambda
+ * (Q voxels), W emission lines E_0^w with yields alpha_w, and J list-mode
+ * events, each with a detector angle, a detected position (here a detector
+ * bin) and a recorded energy.  The library evaluates, on the GPU, the
+ * path-based model of Sec. "Likelihood of list-mode data using path-based
+ * formalism" -- for every event and voxel the system-matrix element
+ *
+ *   a_j[q] = sum_w alpha_w sum_{P in P_q} pr(A_j | P, E_0^w) s(P, E_0^w)
+ *
+ * over the unscattered path and the single-scatter paths through a grid of
+ * scatter points (Eq. s_p with n = 0, 1) -- and runs the LM-OSEM update of
+ * Eq. (os-lm-mlem) with (z_bar_update_os).  The model's readings where the
+ * paper is silent are:
+ *   - pr(A|P,E) = collimator bin probability (Gaussian, FWHM = fwhm0 +
+ *     slope * depth, integrated over the bin) x energy-resolution Gaussian
+ *     density (FWHM/E = frac (E/E_ref)^exponent) at the recorded energy;
+ *   - scatter subpaths: scatter_n x scatter_n cells, density = cell mean,
+ *     quadrature weight A_p / (2 pi d), the emission voxel's own cell skipped,
+ *     Klein-Nishina normalised to the image plane, scatter probability per cm
+ *     = mu;
+ *   - sensitivity = the row integrated over the detector and the windows;
+ *   - subsets interleave angles: subset(a) = a mod n_subsets;
+ *   - mu(r, E) = rho(r) mu_water(E), mu_water linear between knots.
+ *
+ * Conventions (all entry points):
+ *   - return 0 (LMMEW_OK) or a negative LMMEW_ERR_* code; lm_last_error()
+ *     gives a message for the calling thread;
+ *   - geometry, maps and spectra are HOST pointers, copied by lm_create;
+ *   - events, images and outputs are DEVICE pointers owned by the caller; the
+ *     library never frees or permutes them (it sorts a private copy);
+ *   - work is queued on the caller's CUDA stream (a cudaStream_t; 0 = the
+ *     legacy default stream).  Entry points that take events synchronise that
+ *     stream once after validating them (to report out-of-range events and to
+ *     size the work); the rest of the call runs asynchronously.  A device-side
+ *     fault flag (a pipeline wait that ran out of time) is reported by the
+ *     next call that synchronises;
+ *   - a handle serves one stream at a time;
+ *   - there is no CPU fallback: every step runs in this library's kernels.
+ *
+ * Images are n*n arrays in raster order [iy*n + ix]; pixel (ix, iy) has its
+ * centre at ((ix + 0.5 - n/2) h, (iy + 0.5 - n/2) h) cm.  Detector angle a is
+ * theta_a = 2 pi a / n_angles; the detector normal is (cos, sin), the
+ * detector coordinate u = -x sin + y cos, and bin b covers
+ * u in [-n_bins w/2 + b w, -n_bins w/2 + (b+1) w).
+ */
+#ifndef LMMEW_H
+#define LMMEW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LMMEW_OK 0
+#define LMMEW_ERR_INVALID_ARG -1     /* bad sizes, pointers or physics parameters */
+#define LMMEW_ERR_OUT_OF_RANGE -2    /* an event's angle, bin or energy is outside the model */
+#define LMMEW_ERR_CUDA -3            /* a CUDA call failed (message has the CUDA error) */
+#define LMMEW_ERR_OOM -4             /* device allocation failed */
+#define LMMEW_ERR_TIMEOUT -5         /* a kernel's bounded pipeline wait ran out */
+#define LMMEW_ERR_NOT_IMPLEMENTED -6
+
+#define LMMEW_MAX_LINES 8
+#define LMMEW_MAX_WINDOWS 8
+#define LMMEW_MAX_KNOTS 16
+
+/* Opaque handle: owns the device tables of one scanner + object model. */
+typedef struct lm_handle lm_handle;
+
+/* A cudaStream_t, declared without including the CUDA headers. */
+struct CUstream_st;
+typedef struct CUstream_st* lm_stream;
+
+/* Scanner and grid (paper Sec. "SPECT simulation"). */
+typedef struct {
+    int32_t n;               /* image is n x n pixels, n >= 1 */
+    float pixel_cm;          /* pixel size h, cm */
+    int32_t n_angles;        /* detector angles over 360 degrees, 1..65535 */
+    int32_t n_bins;          /* detector bins, 1..65535 */
+    float bin_cm;            /* bin width; <= 0 means n * pixel_cm / n_bins */
+    float r_det_cm;          /* detector face distance from the centre; <= 0 means n * pixel_cm / 2 */
+    float coll_fwhm0_cm;     /* collimator FWHM at the detector face, cm */
+    float coll_fwhm_slope;   /* FWHM growth per cm of depth */
+    float scan_time;         /* T; <= 0 means 1 */
+} lm_geometry;
+
+/* Attenuation (paper Sec. "Synthetic phantom model": water with varying
+ * density, mu linear in energy between knots). */
+typedef struct {
+    const float* rho;          /* host, n*n relative density (water = 1), >= 0 */
+    int32_t n_knots;           /* 1..16 */
+    const float* knot_keV;     /* host, increasing */
+    const float* mu_water_cm;  /* host, water attenuation at the knots, 1/cm */
+    int32_t scatter_n;         /* scatter grid scatter_n^2 cells; must divide n; 0 = no scatter */
+} lm_attenuation;
+
+/* Emission lines E_0^w and yields alpha_w (paper Sec. "Problem formulation"). */
+typedef struct {
+    int32_t n_lines;           /* 1..8 */
+    const float* energy_keV;   /* host */
+    const float* yield;        /* host, >= 0 */
+} lm_lines;
+
+/* Detector energy response and acceptance windows. */
+typedef struct {
+    float fwhm_frac_ref;       /* FWHM / E at e_ref_keV (paper: 0.10 at 140 keV) */
+    float e_ref_keV;
+    float exponent;            /* FWHM / E ~ (E / e_ref)^exponent (paper: -0.5) */
+    int32_t n_windows;         /* 1..8, non-overlapping [lo, hi) */
+    const float* win_lo_keV;   /* host */
+    const float* win_hi_keV;   /* host */
+} lm_energy_model;
+
+/* List-mode events (paper Sec. "Problem formulation": angle, detected
+ * position, recorded energy).  DEVICE pointers, n entries each. */
+typedef struct {
+    const uint16_t* angle;     /* 0 .. n_angles-1 */
+    const uint16_t* bin;       /* 0 .. n_bins-1 */
+    const float* energy_keV;   /* inside one of the windows */
+    int64_t n;                 /* >= 0 */
+} lm_events;
+
+/* Build the model: copies the host inputs, builds on the GPU the path
+ * integrals of Eq. (radpath) (exact line integrals through the density map),
+ * the path sensitivities of Eq. (s_p) for every voxel, scatter point, angle
+ * and line, the collimator tables and the per-angle sensitivity image (FP64).
+ * support: host n*n mask of the voxels that form the model (the LM-OSEM
+ * support, paper App. "GPU implementation": voxels with non-zero initial
+ * activity); NULL means rho > 0.  n_subsets (>= 1) is the default subset
+ * partition used by lm_sensitivity.  Work runs on the legacy default stream
+ * and is complete when the call returns.  On success *out owns all device
+ * memory of the model; free it with lm_destroy.
+ * Errors: INVALID_ARG (sizes, NULL pointers, scatter_n not dividing n,
+ * non-positive collimator or energy blur anywhere in the model, overlapping
+ * windows), OOM, CUDA. */
+int lm_create(const lm_geometry* geometry, const lm_attenuation* attenuation,
+              const lm_lines* lines, const lm_energy_model* energy,
+              const uint8_t* support, int n_subsets, lm_handle** out);
+
+/* Sensitivity image of Eq. (os-lm-mlem)'s denominator,
+ *   sens_s[q] = T sum_{a in s} sum_w alpha_w sum_{P in P_q} s(P, E_0^w)
+ *               x Prob(response on the detector and inside a window),
+ * accumulated in FP64.  subset in [0, n_subsets) of the handle's default
+ * partition, or -1 for all angles.  out: DEVICE double[n*n], zero outside
+ * the support.  Errors: INVALID_ARG, CUDA. */
+int lm_sensitivity(lm_handle* h, int subset, double* out, lm_stream stream);
+
+/* Forward projection y_j = sum_q a_j[q] image[q] (the denominator of
+ * Eq. z_bar_update_os), FP32 with hierarchical sums.  image: DEVICE
+ * float[n*n] (pixels outside the support are ignored); out_y: DEVICE
+ * float[events->n], in the caller's event order.
+ * Errors: INVALID_ARG, OUT_OF_RANGE, OOM, CUDA, TIMEOUT. */
+int lm_forward(lm_handle* h, const lm_events* events, const float* image, float* out_y,
+               lm_stream stream);
+
+/* Back projection out[q] = sum_j weight_j a_j[q].  weight: DEVICE
+ * float[events->n] in the caller's order; out_image: DEVICE float[n*n],
+ * zero outside the support.  Errors: as lm_forward. */
+int lm_backproject(lm_handle* h, const lm_events* events, const float* weight,
+                   float* out_image, lm_stream stream);
+
+/* LM-OSEM (Eq. os-lm-mlem with z_bar_update_os; Algorithm 1):
+ *   for it in [start_iter, n_iters), s in [start_subset (first iteration
+ *   only), n_subsets):
+ *     y_j = sum_q a_j[q] lambda_q for the events of subset s,
+ *     lambda_q <- lambda_q (sum_{j in s, y_j > 0} a_j[q] / y_j) / sens_s[q]
+ *     (0 where sens_s[q] = 0).
+ * image: DEVICE float[n*n], lambda^0 in, lambda out; pixels outside the
+ * support are set to 0.  loglik: NULL or DEVICE double[n_iters*n_subsets];
+ * entry it*n_subsets + s receives sum_{j in s, y_j > 0} log y_j -
+ * sum_q lambda_q sens_s[q] at the image entering that sub-iteration
+ * (Eq. lll_med without J log T - log J!).  Resuming with the image returned
+ * by an earlier call and the next (start_iter, start_subset) reproduces an
+ * uninterrupted run bit for bit.  Errors: as lm_forward. */
+int lm_osem(lm_handle* h, const lm_events* events, int n_subsets, int n_iters,
+            int start_iter, int start_subset, float* image, double* loglik,
+            lm_stream stream);
+
+/* Free every device buffer of the handle (NULL is ignored). */
+int lm_destroy(lm_handle* h);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* lm_last_error(void);
+
+/* Row-kernel timing, for throughput accounting (an instrument of this
+ * library, not part of the paper's method).  While enabled, CUDA events are
+ * recorded on the caller's stream around every launch of the fused
+ * system-matrix row kernel.  lm_profile_read synchronises those events and
+ * writes out4[0] = total row-kernel time in ms, out4[1] = launches,
+ * out4[2] = exponentials evaluated by those launches (one per path term),
+ * out4[3] = system-matrix elements (events x support voxels); then it resets
+ * the counters.  Errors: INVALID_ARG, CUDA. */
+int lm_profile_enable(lm_handle* h, int enable);
+int lm_profile_read(lm_handle* h, double* out4);
+
+/* Model sizes, for work accounting: out8[0] = voxels in the support,
+ * out8[1] = scatter points with rho > 0, out8[2] = emission lines,
+ * out8[3] = angles, out8[4] = bins, out8[5] = exponentials per event row,
+ * out8[6] = bytes of device tables, out8[7] = set-up time in microseconds. */
+int lm_model_info(const lm_handle* h, int64_t* out8);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMMEW_H */

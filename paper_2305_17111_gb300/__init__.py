@@ -1,0 +1,189 @@
+"""GB300-native LM-MEW OSEM (list-mode multi-energy-window SPECT reconstruction).
+
+A thin Python binding over the C ABI in include/lmmew.h: it marshals host
+arrays and torch device tensors into the library's structs and pointers and
+passes torch's current CUDA stream.  Every step of the computation runs in the
+CUDA kernels of liblmmew.so; PyTorch only provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import LmmewError
+
+__all__ = ["Model", "DeviceEvents", "LmmewError", "library_path"]
+
+
+def library_path() -> str:
+    return _native.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class DeviceEvents:
+    """List-mode events resident on the GPU (angle/bin as 16-bit, energy f32)."""
+
+    def __init__(self, angle, bin_, energy_keV, device="cuda"):
+        torch = _torch()
+
+        def as_u16(x):
+            if isinstance(x, torch.Tensor):
+                return x.to(device=device, dtype=torch.int16).contiguous()
+            arr = np.ascontiguousarray(np.asarray(x, dtype=np.uint16)).view(np.int16)
+            return torch.from_numpy(arr.copy()).to(device)
+
+        self.angle = as_u16(angle)
+        self.bin = as_u16(bin_)
+        if isinstance(energy_keV, torch.Tensor):
+            self.energy = energy_keV.to(device=device, dtype=torch.float32).contiguous()
+        else:
+            self.energy = torch.from_numpy(
+                np.ascontiguousarray(np.asarray(energy_keV, dtype=np.float32))).to(device)
+        if not (self.angle.numel() == self.bin.numel() == self.energy.numel()):
+            raise ValueError("angle, bin and energy must have the same length")
+
+    @classmethod
+    def from_list(cls, ev, device="cuda") -> "DeviceEvents":
+        return cls(ev.angle, ev.bin, ev.energy, device=device)
+
+    def __len__(self):
+        return int(self.energy.numel())
+
+    def struct(self) -> _native.Events:
+        return _native.Events(self.angle.data_ptr(), self.bin.data_ptr(), self.energy.data_ptr(),
+                              len(self))
+
+
+class Model:
+    """One scanner + object model on the GPU (an ``lm_handle``)."""
+
+    def __init__(self, *, n, pixel_cm, n_angles, n_bins, rho, knot_keV, mu_water_cm, scatter_n,
+                 line_keV, yields, windows, fwhm_frac=0.10, e_ref_keV=140.0,
+                 fwhm_exponent=-0.5, bin_cm=0.0, r_det_cm=0.0, coll_fwhm0_cm=0.3,
+                 coll_fwhm_slope=0.02, scan_time=1.0, support=None, n_subsets=1):
+        lib = _native.load()
+        self.n = int(n)
+        geo = _native.Geometry(self.n, pixel_cm, n_angles, n_bins, bin_cm, r_det_cm,
+                               coll_fwhm0_cm, coll_fwhm_slope, scan_time)
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float32).reshape(-1))
+        kn = np.ascontiguousarray(np.asarray(knot_keV, dtype=np.float32))
+        mu = np.ascontiguousarray(np.asarray(mu_water_cm, dtype=np.float32))
+        att = _native.Attenuation(_fptr(rho), kn.size, _fptr(kn), _fptr(mu), int(scatter_n))
+        le = np.ascontiguousarray(np.asarray(line_keV, dtype=np.float32))
+        ly = np.ascontiguousarray(np.asarray(yields, dtype=np.float32))
+        lines = _native.Lines(le.size, _fptr(le), _fptr(ly))
+        wlo = np.ascontiguousarray(np.asarray([w[0] for w in windows], dtype=np.float32))
+        whi = np.ascontiguousarray(np.asarray([w[1] for w in windows], dtype=np.float32))
+        en = _native.EnergyModel(fwhm_frac, e_ref_keV, fwhm_exponent, wlo.size, _fptr(wlo),
+                                 _fptr(whi))
+        sup = None
+        if support is not None:
+            sup = np.ascontiguousarray(np.asarray(support).reshape(-1).astype(np.uint8))
+        h = ctypes.c_void_p()
+        _native.check(lib.lm_create(ctypes.byref(geo), ctypes.byref(att), ctypes.byref(lines),
+                                    ctypes.byref(en),
+                                    sup.ctypes.data_as(ctypes.c_void_p) if sup is not None else None,
+                                    int(n_subsets), ctypes.byref(h)))
+        self._h = h
+        self.n_subsets = int(n_subsets)
+        info = (ctypes.c_int64 * 8)()
+        _native.check(lib.lm_model_info(h, info))
+        (self.nq, self.np_scatter, self.n_lines, self.n_angles, self.n_bins,
+         self.terms_per_event, self.table_bytes, setup_us) = [int(v) for v in info]
+        self.setup_ms = setup_us / 1000.0
+
+    @classmethod
+    def from_scenario(cls, sc, rho=None, support=None, n_subsets=None) -> "Model":
+        if rho is None:
+            rho = sc.make_phantom().rho
+        return cls(n=sc.n, pixel_cm=sc.pixel_cm, n_angles=sc.n_angles, n_bins=sc.n_bins, rho=rho,
+                   knot_keV=sc.knot_keV, mu_water_cm=sc.mu_water_cm, scatter_n=sc.scatter_n,
+                   line_keV=sc.line_keV, yields=sc.yields, windows=sc.windows,
+                   fwhm_frac=sc.fwhm_frac, e_ref_keV=sc.e_ref_keV,
+                   fwhm_exponent=sc.fwhm_exponent, bin_cm=sc.bin_cm, r_det_cm=sc.r_det_cm,
+                   coll_fwhm0_cm=sc.coll_fwhm0_cm, coll_fwhm_slope=sc.coll_fwhm_slope,
+                   scan_time=sc.scan_time, support=support,
+                   n_subsets=sc.n_subsets if n_subsets is None else n_subsets)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _native.load().lm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ calls
+    def sensitivity(self, subset=-1, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n * self.n, dtype=torch.float64, device="cuda")
+        _native.check(_native.load().lm_sensitivity(self._h, int(subset),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    _stream(stream)))
+        return out
+
+    def forward(self, events: DeviceEvents, image, out=None, stream=None):
+        torch = _torch()
+        image = image.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
+        if out is None:
+            out = torch.empty(len(events), dtype=torch.float32, device="cuda")
+        ev = events.struct()
+        _native.check(_native.load().lm_forward(self._h, ctypes.byref(ev),
+                                                ctypes.c_void_p(image.data_ptr()),
+                                                ctypes.c_void_p(out.data_ptr()),
+                                                _stream(stream)))
+        return out
+
+    def backproject(self, events: DeviceEvents, weight, out=None, stream=None):
+        torch = _torch()
+        weight = weight.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
+        if out is None:
+            out = torch.empty(self.n * self.n, dtype=torch.float32, device="cuda")
+        ev = events.struct()
+        _native.check(_native.load().lm_backproject(self._h, ctypes.byref(ev),
+                                                    ctypes.c_void_p(weight.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    _stream(stream)))
+        return out
+
+    def osem(self, events: DeviceEvents, image, n_subsets, n_iters, start_iter=0, start_subset=0,
+             loglik=None, stream=None):
+        """Run LM-OSEM in place on ``image`` (a float32 CUDA tensor of n*n)."""
+        torch = _torch()
+        if not (isinstance(image, torch.Tensor) and image.is_cuda and image.dtype == torch.float32
+                and image.is_contiguous()):
+            raise TypeError("image must be a contiguous float32 CUDA tensor")
+        ev = events.struct()
+        llp = ctypes.c_void_p(loglik.data_ptr()) if loglik is not None else None
+        _native.check(_native.load().lm_osem(self._h, ctypes.byref(ev), int(n_subsets),
+                                             int(n_iters), int(start_iter), int(start_subset),
+                                             ctypes.c_void_p(image.data_ptr()), llp,
+                                             _stream(stream)))
+        return image
+
+    def profile_enable(self, on=True):
+        _native.check(_native.load().lm_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        out = (ctypes.c_double * 4)()
+        _native.check(_native.load().lm_profile_read(self._h, out))
+        return {"ms": out[0], "launches": int(out[1]), "terms": out[2], "elements": out[3]}

@@ -1,0 +1,469 @@
+// C ABI entry points (include/lmmew.h): argument checks, scratch management,
+// work planning and the sequence of kernels of each call.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lmmew_internal.cuh"
+
+namespace lmmew {
+
+namespace {
+thread_local std::string g_err;
+constexpr size_t kRowBudgetFloats = size_t(1) << 30;   // 4 GiB of row block per chunk
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LMMEW_ERR_OOM : LMMEW_ERR_CUDA;
+}
+
+namespace {
+
+int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
+    if (s.bytes >= bytes) return LMMEW_OK;
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    if (s.ptr) {
+        cudaFree(s.ptr);
+        s.ptr = nullptr;
+        s.bytes = 0;
+    }
+    const size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&s.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LMMEW_ERR_OOM, "cannot allocate " + std::to_string(want >> 20) +
+                                            " MiB of scratch");
+    }
+    s.bytes = want;
+    (void)h;
+    return LMMEW_OK;
+}
+
+struct Chunk {
+    int t0, t1;         // tile range
+    int64_t e0, e1;     // sorted event range
+};
+
+// Split the tiles of angle ranks [r0, r1) into chunks of at most max_events events.
+std::vector<Chunk> plan_chunks(const SortedEvents& se, int r0, int r1, int64_t max_events) {
+    std::vector<Chunk> out;
+    Chunk cur{-1, -1, 0, 0};
+    for (int r = r0; r < r1; ++r) {
+        for (int t = se.h_tile_start[r]; t < se.h_tile_start[r + 1]; ++t) {
+            const int64_t b = se.h_angle_start[r] + (int64_t)(t - se.h_tile_start[r]) * kET;
+            const int64_t e = std::min<int64_t>(b + kET, se.h_angle_start[r + 1]);
+            if (cur.t0 >= 0 && (e - cur.e0) > max_events) {
+                out.push_back(cur);
+                cur.t0 = -1;
+            }
+            if (cur.t0 < 0) cur = Chunk{t, t, b, b};
+            cur.t1 = t + 1;
+            cur.e1 = e;
+        }
+    }
+    if (cur.t0 >= 0) out.push_back(cur);
+    return out;
+}
+
+int check_events(const lm_handle* h, const lm_events* ev) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    if (!ev) return set_error(LMMEW_ERR_INVALID_ARG, "events is NULL");
+    if (ev->n < 0) return set_error(LMMEW_ERR_INVALID_ARG, "negative event count");
+    if (ev->n >= (int64_t(1) << 31))
+        return set_error(LMMEW_ERR_INVALID_ARG, "at most 2^31 - 1 events per call");
+    if (ev->n > 0 && (!ev->angle || !ev->bin || !ev->energy_keV))
+        return set_error(LMMEW_ERR_INVALID_ARG, "event arrays are NULL");
+    return LMMEW_OK;
+}
+
+int row_stride_of(const lm_handle* h) { return (h->mc.nq + 3) & ~3; }
+
+}  // namespace
+
+int launch_row_profiled(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
+    if (!h->prof_on) return launch_row(h, L, st);
+    if (h->prof_used + 2 > h->prof_ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            LMMEW_CUDA(cudaEventCreate(&e));
+            h->prof_ev.push_back(e);
+        }
+    }
+    cudaEvent_t e0 = h->prof_ev[h->prof_used], e1 = h->prof_ev[h->prof_used + 1];
+    LMMEW_CUDA(cudaEventRecord(e0, st));
+    const int rc = launch_row(h, L, st);
+    if (rc != LMMEW_OK) return rc;
+    LMMEW_CUDA(cudaEventRecord(e1, st));
+    h->prof_used += 2;
+    h->prof_launches += 1;
+    h->prof_terms += (double)L.n_events * (double)h->terms_per_event;
+    h->prof_elems += (double)L.n_events * (double)h->mc.nq;
+    return LMMEW_OK;
+}
+
+}  // namespace lmmew
+
+using namespace lmmew;
+
+extern "C" {
+
+const char* lm_last_error(void) { return g_err.c_str(); }
+
+int lm_create(const lm_geometry* g, const lm_attenuation* at, const lm_lines* ln,
+              const lm_energy_model* em, const uint8_t* support, int n_subsets, lm_handle** out) {
+    if (!out) return set_error(LMMEW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !at || !ln || !em) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    if (g->n < 1 || g->n > 4096) return set_error(LMMEW_ERR_INVALID_ARG, "n must be in 1..4096");
+    if (!(g->pixel_cm > 0.f) || !isfinite(g->pixel_cm))
+        return set_error(LMMEW_ERR_INVALID_ARG, "pixel_cm must be positive");
+    if (g->n_angles < 1 || g->n_angles > 65535 || g->n_bins < 1 || g->n_bins > 65535)
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_angles and n_bins must be in 1..65535");
+    if ((int64_t)g->n_angles * g->n_bins >= (int64_t(1) << 31))
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_angles * n_bins too large");
+    if (n_subsets < 1 || n_subsets > g->n_angles)
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_subsets must be in 1..n_angles");
+    if (!at->rho) return set_error(LMMEW_ERR_INVALID_ARG, "rho is NULL");
+    if (at->n_knots < 1 || at->n_knots > LMMEW_MAX_KNOTS || !at->knot_keV || !at->mu_water_cm)
+        return set_error(LMMEW_ERR_INVALID_ARG, "1..16 attenuation knots required");
+    for (int i = 0; i + 1 < at->n_knots; ++i)
+        if (!(at->knot_keV[i + 1] > at->knot_keV[i]))
+            return set_error(LMMEW_ERR_INVALID_ARG, "knot energies must increase");
+    if (at->scatter_n < 0 || (at->scatter_n > 0 && g->n % at->scatter_n != 0))
+        return set_error(LMMEW_ERR_INVALID_ARG, "scatter_n must divide n (or be 0)");
+    if (ln->n_lines < 1 || ln->n_lines > LMMEW_MAX_LINES || !ln->energy_keV || !ln->yield)
+        return set_error(LMMEW_ERR_INVALID_ARG, "1..8 emission lines required");
+    for (int w = 0; w < ln->n_lines; ++w)
+        if (!(ln->energy_keV[w] > 0.f) || !(ln->yield[w] >= 0.f) || !isfinite(ln->yield[w]))
+            return set_error(LMMEW_ERR_INVALID_ARG, "line energies must be > 0, yields >= 0");
+    if (em->n_windows < 1 || em->n_windows > LMMEW_MAX_WINDOWS || !em->win_lo_keV || !em->win_hi_keV)
+        return set_error(LMMEW_ERR_INVALID_ARG, "1..8 energy windows required");
+    for (int k = 0; k < em->n_windows; ++k) {
+        if (!(em->win_hi_keV[k] > em->win_lo_keV[k]))
+            return set_error(LMMEW_ERR_INVALID_ARG, "each window needs lo < hi");
+        for (int k2 = 0; k2 < k; ++k2)
+            if (em->win_lo_keV[k] < em->win_hi_keV[k2] && em->win_lo_keV[k2] < em->win_hi_keV[k])
+                return set_error(LMMEW_ERR_INVALID_ARG, "energy windows overlap");
+    }
+    if (!(em->fwhm_frac_ref > 0.f) || !(em->e_ref_keV > 0.f) || !isfinite(em->exponent))
+        return set_error(LMMEW_ERR_INVALID_ARG, "energy resolution must be positive");
+    const int n = g->n;
+    for (int i = 0; i < n * n; ++i)
+        if (!(at->rho[i] >= 0.f) || !isfinite(at->rho[i]))
+            return set_error(LMMEW_ERR_INVALID_ARG, "rho must be finite and >= 0");
+
+    lm_handle* h = new lm_handle();
+    ModelConst& m = h->mc;
+    std::memset(&m, 0, sizeof(m));
+    m.n = n;
+    m.h = g->pixel_cm;
+    m.A = g->n_angles;
+    m.B = g->n_bins;
+    m.bin_w = g->bin_cm > 0.f ? (double)g->bin_cm : (double)n * g->pixel_cm / g->n_bins;
+    m.r_det = g->r_det_cm > 0.f ? (double)g->r_det_cm : 0.5 * n * (double)g->pixel_cm;
+    m.fwhm0 = g->coll_fwhm0_cm;
+    m.slope = g->coll_fwhm_slope;
+    m.T = g->scan_time > 0.f ? (double)g->scan_time : 1.0;
+    m.S = at->scatter_n;
+    m.f = m.S > 0 ? n / m.S : 1;
+    m.cell_area = (m.f * m.h) * (m.f * m.h);
+    m.W = ln->n_lines;
+    for (int w = 0; w < m.W; ++w) {
+        m.line_e[w] = ln->energy_keV[w];
+        m.alpha[w] = ln->yield[w];
+    }
+    m.fwhm_frac = em->fwhm_frac_ref;
+    m.e_ref = em->e_ref_keV;
+    m.expo = em->exponent;
+    m.n_win = em->n_windows;
+    for (int k = 0; k < m.n_win; ++k) {
+        m.win_lo[k] = em->win_lo_keV[k];
+        m.win_hi[k] = em->win_hi_keV[k];
+    }
+    m.n_knots = at->n_knots;
+    for (int i = 0; i < m.n_knots; ++i) {
+        m.knot_e[i] = at->knot_keV[i];
+        m.knot_mu[i] = at->mu_water_cm[i];
+    }
+    h->n_subsets_default = n_subsets;
+    int rc = build_tables(h, at->rho, support);
+    if (rc == LMMEW_OK) rc = row_kernel_occupancy(h);
+    if (rc != LMMEW_OK) {
+        std::string keep = g_err;
+        lm_destroy(h);
+        g_err = keep;
+        return rc;
+    }
+    // exponentials per event row: W per voxel (primary) + W per (voxel, scatter
+    // point) path that exists (the emission voxel's own cell has none)
+    {
+        std::vector<int> q_pix(m.nq);
+        cudaMemcpy(q_pix.data(), h->d_q_pix, sizeof(int) * m.nq, cudaMemcpyDeviceToHost);
+        int64_t own = 0;
+        if (m.S > 0) {
+            std::vector<uint8_t> cell_has(m.S * m.S, 0);
+            // a cell is a scatter point iff its mean density is positive
+            for (int c = 0; c < m.S * m.S; ++c) {
+                double sum = 0.0;
+                const int mx = c % m.S, my = c / m.S;
+                for (int iy = my * m.f; iy < (my + 1) * m.f; ++iy)
+                    for (int ix = mx * m.f; ix < (mx + 1) * m.f; ++ix) sum += at->rho[iy * n + ix];
+                cell_has[c] = sum > 0.0;
+            }
+            for (int pix : q_pix) own += cell_has[((pix / n) / m.f) * m.S + (pix % n) / m.f];
+        }
+        h->terms_per_event = (int64_t)m.W * ((int64_t)m.nq * (m.np + 1) - own);
+    }
+    *out = h;
+    return LMMEW_OK;
+}
+
+int lm_destroy(lm_handle* h) {
+    if (!h) return LMMEW_OK;
+    cudaFree(h->d_q_pix);
+    cudaFree(h->d_tab);
+    cudaFree(h->d_cs);
+    cudaFree(h->d_cv);
+    cudaFree(h->d_prim);
+    cudaFree(h->d_sens_a);
+    cudaFree(h->d_status);
+    cudaFree(h->d_sens_sub);
+    cudaFree(h->scratch_sort.ptr);
+    cudaFree(h->scratch_work.ptr);
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    delete h;
+    return LMMEW_OK;
+}
+
+int lm_model_info(const lm_handle* h, int64_t* out8) {
+    if (!h || !out8) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    out8[0] = h->mc.nq;
+    out8[1] = h->mc.np;
+    out8[2] = h->mc.W;
+    out8[3] = h->mc.A;
+    out8[4] = h->mc.B;
+    out8[5] = h->terms_per_event;
+    out8[6] = (int64_t)h->tab_bytes;
+    out8[7] = (int64_t)(h->setup_ms * 1000.0f);
+    return LMMEW_OK;
+}
+
+int lm_sensitivity(lm_handle* h, int subset, double* out, lm_stream stream) {
+    if (!h || !out) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    const int parts = h->n_subsets_default;
+    if (subset < -1 || subset >= parts) return set_error(LMMEW_ERR_INVALID_ARG, "subset out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = subset_sensitivity(h, parts, st);
+    if (rc != LMMEW_OK) return rc;
+    const double* src = h->d_sens_sub + (size_t)(subset < 0 ? parts : subset) * h->mc.nq;
+    return launch_scatter_image_d(h, src, out, st);
+}
+
+int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
+               lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    if (ev->n > 0 && (!image || !out_y)) return set_error(LMMEW_ERR_INVALID_ARG, "NULL image/output");
+    if (ev->n == 0) return LMMEW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ModelConst& m = h->mc;
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events(h, ev, 1, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / m.nqt));
+    std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
+    int64_t biggest = 0;
+    for (const Chunk& c : chunks) biggest = std::max(biggest, c.e1 - c.e0);
+    rc = ensure(h, h->scratch_work,
+                bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * m.nqt * biggest), st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* lam_v = bump<float>(w, m.nq);
+    float* ypart = bump<float>(w, (size_t)m.nqt * std::max<int64_t>(biggest, 1));
+    rc = launch_gather_image(h, image, lam_v, st);
+    if (rc != LMMEW_OK) return rc;
+    for (const Chunk& c : chunks) {
+        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, nullptr, c.e0, 0, ypart,
+                    c.e1 - c.e0, c.e1 - c.e0};
+        rc = launch_row_profiled(h, L, st);
+        if (rc != LMMEW_OK) return rc;
+        rc = launch_forward_out(h, ypart, c.e1 - c.e0, c.e0, c.e1 - c.e0, se.perm, out_y, st);
+        if (rc != LMMEW_OK) return rc;
+    }
+    return LMMEW_OK;
+}
+
+int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float* out_image,
+                   lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    if (!out_image || (ev->n > 0 && !weight))
+        return set_error(LMMEW_ERR_INVALID_ARG, "NULL weight/output");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ModelConst& m = h->mc;
+    if (ev->n == 0) {
+        LMMEW_CUDA(cudaMemsetAsync(out_image, 0, sizeof(float) * m.n * m.n, st));
+        return LMMEW_OK;
+    }
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events(h, ev, 1, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    const int rs = row_stride_of(h);
+    const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / rs));
+    std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
+    int64_t biggest = 0, parts = 0;
+    for (const Chunk& c : chunks) {
+        biggest = std::max(biggest, c.e1 - c.e0);
+        parts += bp_parts(c.e1 - c.e0);
+    }
+    rc = ensure(h, h->scratch_work,
+                bump_bytes(sizeof(float) * rs * biggest) + bump_bytes(sizeof(float) * parts * m.nq) +
+                    bump_bytes(sizeof(double) * m.nq),
+                st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* rows = bump<float>(w, (size_t)rs * biggest);
+    float* bpart = bump<float>(w, (size_t)std::max<int64_t>(parts, 1) * m.nq);
+    double* num = bump<double>(w, m.nq);
+    int64_t row0 = 0;
+    for (const Chunk& c : chunks) {
+        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, nullptr, rows, c.e0, rs, nullptr, 0,
+                    c.e1 - c.e0};
+        rc = launch_row_profiled(h, L, st);
+        if (rc != LMMEW_OK) return rc;
+        rc = launch_bp_partial(h, rows, rs, nullptr, 0, c.e1 - c.e0, se.perm + c.e0, weight, bpart,
+                               row0, nullptr, st);
+        if (rc != LMMEW_OK) return rc;
+        row0 += bp_parts(c.e1 - c.e0);
+    }
+    rc = launch_voxel_reduce(h, bpart, parts, num, st);
+    if (rc != LMMEW_OK) return rc;
+    return launch_num_to_image(h, num, out_image, st);
+}
+
+int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int start_iter,
+            int start_subset, float* image, double* loglik, lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    const ModelConst& m = h->mc;
+    if (!image) return set_error(LMMEW_ERR_INVALID_ARG, "image is NULL");
+    if (n_subsets < 1 || n_subsets > m.A)
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_subsets must be in 1..n_angles");
+    if (n_iters < 0 || start_iter < 0 || start_iter > n_iters || start_subset < 0 ||
+        start_subset >= n_subsets)
+        return set_error(LMMEW_ERR_INVALID_ARG, "iteration range out of bounds");
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = subset_sensitivity(h, n_subsets, st);
+    if (rc != LMMEW_OK) return rc;
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events(h, ev, n_subsets, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+
+    // angle ranks of each subset and the chunks of its events
+    const int rs = row_stride_of(h);
+    const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / rs));
+    std::vector<std::vector<Chunk>> plan(n_subsets);
+    int64_t biggest = 0, parts_max = 0;
+    {
+        int r = 0;
+        for (int s = 0; s < n_subsets; ++s) {
+            const int cnt = (m.A - s + n_subsets - 1) / n_subsets;
+            plan[s] = plan_chunks(se, r, r + cnt, max_ev);
+            int64_t parts = 0;
+            for (const Chunk& c : plan[s]) {
+                biggest = std::max(biggest, c.e1 - c.e0);
+                parts += bp_parts(c.e1 - c.e0);
+            }
+            parts_max = std::max(parts_max, parts);
+            r += cnt;
+        }
+    }
+    const size_t need = bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * rs * biggest) +
+                        bump_bytes(sizeof(float) * m.nqt * biggest) +
+                        bump_bytes(sizeof(float) * std::max<int64_t>(parts_max, 1) * m.nq) +
+                        bump_bytes(sizeof(double) * std::max<int64_t>(parts_max, 1)) +
+                        bump_bytes(sizeof(double) * m.nq);
+    rc = ensure(h, h->scratch_work, need, st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* lam_v = bump<float>(w, m.nq);
+    float* rows = bump<float>(w, (size_t)rs * std::max<int64_t>(biggest, 1));
+    float* ypart = bump<float>(w, (size_t)m.nqt * std::max<int64_t>(biggest, 1));
+    float* bpart = bump<float>(w, (size_t)std::max<int64_t>(parts_max, 1) * m.nq);
+    double* llpart = bump<double>(w, std::max<int64_t>(parts_max, 1));
+    double* num = bump<double>(w, m.nq);
+
+    rc = launch_gather_image(h, image, lam_v, st);
+    if (rc != LMMEW_OK) return rc;
+    for (int it = start_iter; it < n_iters; ++it) {
+        for (int s = (it == start_iter ? start_subset : 0); s < n_subsets; ++s) {
+            int64_t row0 = 0;
+            for (const Chunk& c : plan[s]) {
+                const int64_t cnt = c.e1 - c.e0;
+                RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
+                            cnt, cnt};
+                rc = launch_row_profiled(h, L, st);
+                if (rc != LMMEW_OK) return rc;
+                rc = launch_bp_partial(h, rows, rs, ypart, cnt, cnt, nullptr, nullptr, bpart, row0,
+                                       llpart, st);
+                if (rc != LMMEW_OK) return rc;
+                row0 += bp_parts(cnt);
+            }
+            if (row0 > 0) {
+                rc = launch_voxel_reduce(h, bpart, row0, num, st);
+            } else {
+                LMMEW_CUDA(cudaMemsetAsync(num, 0, sizeof(double) * m.nq, st));
+            }
+            if (rc != LMMEW_OK) return rc;
+            rc = launch_update(h, lam_v, num, h->d_sens_sub + (size_t)s * m.nq, llpart, row0,
+                               loglik ? loglik + (size_t)it * n_subsets + s : nullptr, st);
+            if (rc != LMMEW_OK) return rc;
+        }
+    }
+    return launch_scatter_image(h, lam_v, image, st);
+}
+
+int lm_profile_enable(lm_handle* h, int enable) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    h->prof_on = enable ? 1 : 0;
+    return LMMEW_OK;
+}
+
+int lm_profile_read(lm_handle* h, double* out4) {
+    if (!h || !out4) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < h->prof_used; i += 2) {
+        LMMEW_CUDA(cudaEventSynchronize(h->prof_ev[i + 1]));
+        float t = 0.f;
+        LMMEW_CUDA(cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]));
+        ms += t;
+    }
+    out4[0] = ms;
+    out4[1] = (double)h->prof_launches;
+    out4[2] = h->prof_terms;
+    out4[3] = h->prof_elems;
+    h->prof_used = 0;
+    h->prof_launches = 0;
+    h->prof_terms = 0.0;
+    h->prof_elems = 0.0;
+    return LMMEW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// The rest of an LM-OSEM sub-iteration (Eq. os-lm-mlem with z_bar_update_os):
+// the per-event ratio 1/y_j, the back projection sum_j a_j[q] / y_j by voxel
+// ownership (every voxel's sum is owned by one thread, no global atomics),
+// the FP64 log-likelihood of Eq. (lll_med) and the multiplicative update.
+// All sums run in a fixed order, so an OSEM run is bit-reproducible.
+#include "lmmew_internal.cuh"
+
+namespace lmmew {
+namespace {
+
+constexpr int kBpEvents = 128;    // events per back-projection partial
+constexpr int kBpVoxels = 256;    // voxels per back-projection block
+
+__global__ void k_forward_out(const float* ypart, int64_t stride, int nqt, int64_t count,
+                              const uint32_t* perm, float* out_y) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    float y = 0.f;
+    for (int t = 0; t < nqt; ++t) y += ypart[(size_t)t * stride + j];
+    out_y[perm[j]] = y;
+}
+
+// One block per (chunk of 128 events, 256 voxels).  The block first forms
+// the events' weights: r_j = 1 / y_j from the per-q-tile partial forward
+// sums (0 when y_j <= 0), or the caller's weights.  Blocks of the first voxel
+// column also write the chunk's sum of log y_j (FP64).
+__global__ void __launch_bounds__(kBpVoxels) k_bp_partial(
+    const float* rows, int row_stride, const float* ypart, int64_t ypart_stride, int nqt,
+    int64_t count, const uint32_t* perm, const float* weight, int nq, float* bpart, int64_t row0,
+    double* llpart) {
+    __shared__ float r[kBpEvents];
+    __shared__ double ll[kBpEvents];
+    const int t = threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.x * kBpEvents;
+    if (t < kBpEvents) {
+        const int64_t j = j0 + t;
+        float rv = 0.f;
+        double lv = 0.0;
+        if (j < count) {
+            if (weight) {
+                rv = weight[perm[j]];
+            } else {
+                float y = 0.f;
+                for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
+                if (y > 0.f) {
+                    rv = 1.0f / y;
+                    lv = log((double)y);
+                }
+            }
+        }
+        r[t] = rv;
+        ll[t] = lv;
+    }
+    __syncthreads();
+    if (llpart && blockIdx.y == 0) {
+        for (int off = kBpEvents / 2; off > 0; off >>= 1) {
+            if (t < off) ll[t] += ll[t + off];
+            __syncthreads();
+        }
+        if (t == 0) llpart[row0 + blockIdx.x] = ll[0];
+    }
+    const int q = blockIdx.y * kBpVoxels + t;
+    if (q >= nq) return;
+    const int64_t rem = count - j0;
+    const int n_here = rem < kBpEvents ? (int)rem : kBpEvents;
+    const float* rp = rows + (size_t)j0 * row_stride + q;
+    float acc = 0.f;
+    for (int e = 0; e < n_here; ++e) acc = fmaf(r[e], rp[(size_t)e * row_stride], acc);
+    bpart[(size_t)(row0 + blockIdx.x) * nq + q] = acc;
+}
+
+__global__ void k_voxel_reduce(const float* bpart, int64_t n_parts, int nq, double* num) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double acc = 0.0;
+    for (int64_t i = 0; i < n_parts; ++i) acc += (double)bpart[(size_t)i * nq + q];
+    num[q] = acc;
+}
+
+// Single block: log-likelihood at the incoming image, then the update.
+__global__ void __launch_bounds__(1024) k_update(float* lam, const double* num, const double* sens,
+                                                 int nq, const double* llpart, int64_t n_ll,
+                                                 double* loglik) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x;
+    if (loglik) {
+        double s = 0.0;
+        for (int64_t i = t; i < n_ll; i += 1024) s += llpart[i];
+        for (int q = t; q < nq; q += 1024) s -= (double)lam[q] * sens[q];
+        red[t] = s;
+        __syncthreads();
+        for (int off = 512; off > 0; off >>= 1) {
+            if (t < off) red[t] += red[t + off];
+            __syncthreads();
+        }
+        if (t == 0) *loglik = red[0];
+        __syncthreads();
+    }
+    for (int q = t; q < nq; q += 1024)
+        lam[q] = sens[q] > 0.0 ? (float)((double)lam[q] * num[q] / sens[q]) : 0.f;
+}
+
+__global__ void k_gather(const float* image, const int* q_pix, int nq, float* lam) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) lam[q] = image[q_pix[q]];
+}
+
+__global__ void k_scatter_f(const float* v, const int* q_pix, int nq, float* image) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) image[q_pix[q]] = v[q];
+}
+
+__global__ void k_scatter_d(const double* v, const int* q_pix, int nq, double* image) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) image[q_pix[q]] = v[q];
+}
+
+__global__ void k_scatter_df(const double* v, const int* q_pix, int nq, float* image) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) image[q_pix[q]] = (float)v[q];
+}
+
+}  // namespace
+
+int launch_forward_out(lm_handle* h, const float* ypart, int64_t ypart_stride, int64_t begin,
+                       int64_t count, const uint32_t* perm, float* out_y, cudaStream_t st) {
+    if (count <= 0) return LMMEW_OK;
+    k_forward_out<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ypart, ypart_stride, h->mc.nqt,
+                                                                   count, perm + begin, out_y);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_bp_partial(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                      int64_t ypart_stride, int64_t count, const uint32_t* perm,
+                      const float* weight, float* bpart, int64_t bpart_row0, double* llpart,
+                      cudaStream_t st) {
+    if (count <= 0) return LMMEW_OK;
+    const int nq = h->mc.nq;
+    dim3 g((unsigned)((count + kBpEvents - 1) / kBpEvents), (nq + kBpVoxels - 1) / kBpVoxels);
+    k_bp_partial<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt, count,
+                                          perm, weight, nq, bpart, bpart_row0, llpart);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int64_t bp_parts(int64_t count) { return (count + kBpEvents - 1) / kBpEvents; }
+
+int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, double* num,
+                        cudaStream_t st) {
+    k_voxel_reduce<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(bpart, n_parts, h->mc.nq, num);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
+                  const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st) {
+    k_update<<<1, 1024, 0, st>>>(lam_v, num, sens, h->mc.nq, llpart, n_ll, loglik_out);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStream_t st) {
+    k_gather<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(image, h->d_q_pix, h->mc.nq, lam_v);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStream_t st) {
+    LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * h->mc.n * h->mc.n, st));
+    k_scatter_f<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(lam_v, h->d_q_pix, h->mc.nq, image);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStream_t st) {
+    LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(double) * h->mc.n * h->mc.n, st));
+    k_scatter_d<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(v, h->d_q_pix, h->mc.nq, image);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStream_t st) {
+    LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * h->mc.n * h->mc.n, st));
+    k_scatter_df<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(num, h->d_q_pix, h->mc.nq, image);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+}  // namespace lmmew

@@ -1,0 +1,173 @@
+// Internal declarations shared by the translation units of liblmmew.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lmmew.h"
+
+namespace lmmew {
+
+// ---------------------------------------------------------------- tiling
+constexpr int kQT = 32;     // voxels per q-tile of the row kernel
+constexpr int kPC = 32;     // scatter points per pipeline stage
+constexpr int kET = 128;    // events per tile (4 per lane, 32 lanes)
+constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
+constexpr int kRowThreads = 256;
+constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path
+
+// Status bits written by kernels into the handle's device status word.
+constexpr int kStatusOutOfRange = 1;
+constexpr int kStatusTimeout = 2;
+
+// ---------------------------------------------------------------- model
+// Model constants passed by value to the setup kernels (FP64).
+struct ModelConst {
+    int n, A, B, S, W, n_win, n_knots;
+    int nq, np, f;            // support voxels, scatter points, pixels per cell side
+    int nqt, npc;             // q-tiles, p-chunks
+    double h, bin_w, r_det, fwhm0, slope, T, cell_area;
+    double fwhm_frac, e_ref, expo;
+    double line_e[LMMEW_MAX_LINES], alpha[LMMEW_MAX_LINES], kn_norm[LMMEW_MAX_LINES];
+    double win_lo[LMMEW_MAX_WINDOWS], win_hi[LMMEW_MAX_WINDOWS];
+    double knot_e[LMMEW_MAX_KNOTS], knot_mu[LMMEW_MAX_KNOTS];
+};
+
+// Per-line FP32 constants of the energy response used by the hot kernel.
+struct LineConst {
+    float e[LMMEW_MAX_LINES];      // line energy
+    float nk[LMMEW_MAX_LINES];     // -log2(e) / (2 sigma_E(E)^2)
+    float norm[LMMEW_MAX_LINES];   // 1 / (sqrt(2 pi) sigma_E(E))
+};
+
+// One tile of events: one angle, up to kET consecutive sorted events.
+struct Tile {
+    int a;          // detector angle
+    int begin;      // first sorted event (index into the sorted arrays)
+    int count;      // 1..kET
+    int b_lo_hi;    // (b_lo << 16) | b_hi: bin range of the tile's events
+};
+
+struct Scratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace lmmew
+
+struct lm_handle {
+    lmmew::ModelConst mc;
+    lmmew::LineConst lc;
+    int n_subsets_default;
+    // geometry on the device
+    int* d_q_pix = nullptr;        // [nq] pixel index of each support voxel
+    float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  lh, nk, E'
+    float* d_cs = nullptr;         // [A][npc][B][kCPad] collimator prob. of scatter points
+    float* d_cv = nullptr;         // [A][B][nq] collimator prob. of voxels
+    float* d_prim = nullptr;       // [A][W][nq] alpha_w exp(-mu_w gamma_det)
+    double* d_sens_a = nullptr;    // [A][nq] per-angle sensitivity (FP64)
+    int* d_status = nullptr;       // device status word
+    size_t tab_bytes = 0;
+    // cached subset sensitivities for the last partition asked for
+    int sens_parts = 0;
+    double* d_sens_sub = nullptr;  // [parts][nq]
+    // growable scratch arena
+    lmmew::Scratch scratch_sort;   // sorted events of the current call
+    lmmew::Scratch scratch_work;   // row blocks and partial sums
+    int sm_count = 0;
+    int row_blocks_per_sm = 0;
+    float setup_ms = 0.f;
+    int64_t terms_per_event = 0;   // exponentials per event row (primary + scatter)
+    // optional timing of the row kernel (CUDA events around each launch)
+    int prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;   // pairs
+    size_t prof_used = 0;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    double prof_terms = 0.0;
+    double prof_elems = 0.0;
+};
+
+namespace lmmew {
+
+// Error reporting (thread-local message).
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+#define LMMEW_CUDA(call)                                              \
+    do {                                                              \
+        cudaError_t e__ = (call);                                     \
+        if (e__ != cudaSuccess) return ::lmmew::cuda_error(e__, #call); \
+    } while (0)
+
+// setup.cu
+int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_host);
+int subset_sensitivity(lm_handle* h, int n_subsets, cudaStream_t st);
+
+// events.cu: validation + stable sort by (subset rank of angle, bin)
+struct SortedEvents {
+    uint16_t* bin = nullptr;     // [n] sorted bins
+    float* energy = nullptr;     // [n] sorted energies
+    uint32_t* perm = nullptr;    // [n] caller index of each sorted event
+    int* angle_start = nullptr;  // [A+1] device: first sorted event of each angle rank
+    Tile* tiles = nullptr;       // [max_tiles]
+    int* tile_start = nullptr;   // [A+1] first tile of each angle rank
+    int64_t n_valid = 0;
+    // host copies
+    std::vector<int> h_angle_start;  // [A+1]
+    std::vector<int> h_tile_start;   // [A+1]
+    std::vector<int> h_rank_angle;   // [A] angle of each rank
+};
+size_t sort_scratch_bytes(int64_t n, int A);
+int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* out,
+                char*& arena, cudaStream_t st);
+
+// row.cu: fused system-matrix row kernel
+struct RowLaunch {
+    const Tile* tiles;
+    int tile_begin, tile_end;
+    const uint16_t* ev_bin;
+    const float* ev_e;
+    const float* lam_v;     // [nq] image on the voxel list (may be null: no forward sums)
+    float* rows;            // null: do not store rows
+    int64_t row_base;       // sorted index of row 0
+    int row_stride;
+    float* ypart;           // [nqt][ypart_stride], indexed by sorted event - row_base
+    int64_t ypart_stride;
+    int64_t n_events;       // events covered by the tile range (for accounting)
+};
+int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
+size_t row_smem_bytes(const lm_handle* h);
+int row_kernel_occupancy(lm_handle* h);
+
+// em.cu
+int launch_forward_out(lm_handle* h, const float* ypart, int64_t ypart_stride, int64_t begin,
+                       int64_t count, const uint32_t* perm, float* out_y, cudaStream_t st);
+int launch_bp_partial(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                      int64_t ypart_stride, int64_t count, const uint32_t* perm,
+                      const float* weight, float* bpart, int64_t bpart_row0, double* llpart,
+                      cudaStream_t st);
+int64_t bp_parts(int64_t count);
+int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, double* num,
+                        cudaStream_t st);
+int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
+                  const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st);
+int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStream_t st);
+int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStream_t st);
+int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStream_t st);
+int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStream_t st);
+
+// Bump allocation from a scratch arena (256-byte aligned).
+template <class T>
+inline T* bump(char*& arena, size_t count) {
+    uintptr_t p = reinterpret_cast<uintptr_t>(arena);
+    p = (p + 255) & ~uintptr_t(255);
+    T* out = reinterpret_cast<T*>(p);
+    arena = reinterpret_cast<char*>(p + sizeof(T) * count);
+    return out;
+}
+inline size_t bump_bytes(size_t bytes) { return ((bytes + 255) / 256) * 256 + 256; }
+
+}  // namespace lmmew

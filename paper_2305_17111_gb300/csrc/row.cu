@@ -1,0 +1,355 @@
+// The hot kernel: system-matrix rows of the path model computed on the fly
+// (paper Eq. Aj_expansion with Eq. s_p for n = 0 and n = 1; Algorithm 1's
+// K_SumAjKernel), fused with the per-tile partial forward projection.
+//
+//   a_j[q] = sum_w alpha_w [ s_prim(a,w,q) C_q(b) g(E_hat; E_w)
+//                            + sum_p s(a,w,q,p) C_p(b) g(E_hat; E'(a,w,q,p)) ]
+//
+// Work unit = (tile of <= 128 events of one angle, tile of 32 voxels).  The
+// CTA streams the angle's scatter-path tables for its 32 voxels and the
+// collimator rows of the tile's bins, 32 scatter points per stage, from
+// global memory into shared memory with bulk asynchronous copies (TMA engine,
+// cp.async.bulk + mbarrier, double buffered).  Each of the 8 warps owns 4
+// voxels; each lane owns 4 events, so a table entry read from shared memory
+// is a broadcast that feeds 4 events, and the collimator value of an
+// (event, point) pair feeds every voxel and line.  Per scatter term:
+//   d = E_hat - E'; arg = nk d^2 + lh; term = ex2(arg)   (MUFU)
+// with lh = log2(alpha s / (sqrt(2 pi) sigma_E(E'))) and nk = -log2(e) /
+// (2 sigma_E(E')^2) precomputed in FP64.  Sums are hierarchical: per stage,
+// per unit, then across warps in a fixed order, so results are
+// deterministic.  Every mbarrier wait is bounded in time; a wait that runs
+// out sets the status word and the CTA stops cleanly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lmmew_internal.cuh"
+
+namespace lmmew {
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per pipeline wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a barrier phase with a time limit; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer();
+    while (!mbar_try_wait(bar, parity))
+        if (global_timer() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct RowParams {
+    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]
+    const float* cs;      // [A][npc][B][kCPad]
+    const float* cv;      // [A][B][nq]
+    const float* prim;    // [A][W][nq]
+    const Tile* tiles;
+    int tile_begin, tile_end;
+    const uint16_t* ev_bin;
+    const float* ev_e;
+    const float* lam;     // [nq] or null
+    float* rows;          // or null
+    int64_t row_base;
+    int row_stride;
+    float* ypart;         // [nqt][ypart_stride] or null
+    int64_t ypart_stride;
+    int* status;
+    int W, B, nq, nqt, npc;
+    uint32_t stage_bytes;   // bytes of one pipeline stage in shared memory
+    uint32_t tab_stage_bytes;
+    LineConst lc;
+};
+
+__global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = P.W;
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    const int n_tiles = P.tile_end - P.tile_begin;
+    const int n_units = n_tiles * P.nqt;
+    const size_t tab_block = (size_t)3 * W * kQT * kPC;   // floats per (a, qt, pc)
+    uint32_t g = 0;                                       // pipeline stages issued so far
+
+    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+        const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
+        const int qt = unit % P.nqt;
+        const int b_lo = T.b_lo_hi >> 16, b_hi = T.b_lo_hi & 0xffff;
+        const uint32_t c_bytes = (uint32_t)(b_hi - b_lo + 1) * kCPad * 4u;
+
+        float eh[4];
+        int bo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = k * 32 + lane;
+            const bool v = e < T.count;
+            eh[k] = v ? P.ev_e[T.begin + e] : 0.f;
+            bo[k] = v ? (int)P.ev_bin[T.begin + e] - b_lo : 0;
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[k][i] = 0.f;
+
+        if (P.npc > 0) {
+            const float* tab_u = P.tab + ((size_t)T.a * P.nqt + qt) * P.npc * tab_block;
+            const float* cs_u = P.cs + ((size_t)T.a * P.npc * P.B + b_lo) * kCPad;
+            auto issue = [&](int pc, uint32_t gs) {
+                const int buf = gs & 1;
+                const uint32_t bar = buf ? bar1 : bar0;
+                const uint32_t dst = smem_addr(smem + buf * P.stage_bytes);
+                mbar_expect_tx(bar, P.tab_stage_bytes + c_bytes);
+                bulk_g2s(dst, tab_u + (size_t)pc * tab_block, P.tab_stage_bytes, bar);
+                bulk_g2s(dst + P.tab_stage_bytes, cs_u + (size_t)pc * P.B * kCPad, c_bytes, bar);
+            };
+            if (tid == 0) issue(0, g);
+            for (int pc = 0; pc < P.npc; ++pc, ++g) {
+                if (tid == 0 && pc + 1 < P.npc) issue(pc + 1, g + 1);
+                const int buf = g & 1;
+                const bool ok = mbar_wait_bounded(buf ? bar1 : bar0, (g >> 1) & 1);
+                if (!ok) s_abort = 1;
+                if (ok) {
+                    const unsigned char* sb = smem + buf * P.stage_bytes;
+                    const float* tb = reinterpret_cast<const float*>(sb);
+                    const float* cr = reinterpret_cast<const float*>(sb + P.tab_stage_bytes);
+                    float sacc[4][4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) sacc[k][i] = 0.f;
+#pragma unroll 1
+                    for (int pq = 0; pq < kPC / 4; ++pq) {
+                        float4 c4[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            c4[k] = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
+#pragma unroll
+                        for (int qi = 0; qi < 4; ++qi) {
+                            const int ql = warp * 4 + qi;
+                            float in[4][4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) in[k][i] = 0.f;
+#pragma unroll 1
+                            for (int w = 0; w < W; ++w) {
+                                const float4 lh = *reinterpret_cast<const float4*>(
+                                    tb + ((0 * W + w) * kQT + ql) * kPC + pq * 4);
+                                const float4 nk = *reinterpret_cast<const float4*>(
+                                    tb + ((1 * W + w) * kQT + ql) * kPC + pq * 4);
+                                const float4 ep = *reinterpret_cast<const float4*>(
+                                    tb + ((2 * W + w) * kQT + ql) * kPC + pq * 4);
+                                const float lhv[4] = {lh.x, lh.y, lh.z, lh.w};
+                                const float nkv[4] = {nk.x, nk.y, nk.z, nk.w};
+                                const float epv[4] = {ep.x, ep.y, ep.z, ep.w};
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                                    for (int i = 0; i < 4; ++i) {
+                                        const float d = eh[k] - epv[i];
+                                        in[k][i] += fast_ex2(fmaf(nkv[i], d * d, lhv[i]));
+                                    }
+                            }
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                float s = sacc[k][qi];
+                                s = fmaf(c4[k].x, in[k][0], s);
+                                s = fmaf(c4[k].y, in[k][1], s);
+                                s = fmaf(c4[k].z, in[k][2], s);
+                                s = fmaf(c4[k].w, in[k][3], s);
+                                sacc[k][qi] = s;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc[k][i] += sacc[k][i];
+                }
+                __syncthreads();
+                if (s_abort) {
+                    if (tid == 0) {
+                        atomicOr(P.status, kStatusTimeout);
+                        // let the copies still in flight land before the CTA exits
+                        mbar_wait_bounded((g & 1) ? bar1 : bar0, (g >> 1) & 1);
+                        if (pc + 1 < P.npc)
+                            mbar_wait_bounded(((g + 1) & 1) ? bar1 : bar0, ((g + 1) >> 1) & 1);
+                    }
+                    return;
+                }
+            }
+        }
+
+        // unscattered paths
+        {
+            const int b_base = T.a * P.B + b_lo;
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi) {
+                const int q = qt * kQT + warp * 4 + qi;
+                if (q < P.nq) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k * 32 + lane < T.count) {
+                            float s = 0.f;
+#pragma unroll
+                            for (int w = 0; w < LMMEW_MAX_LINES; ++w) {
+                                if (w < W) {
+                                    const float d = eh[k] - P.lc.e[w];
+                                    const float gw = P.lc.norm[w] * fast_ex2(P.lc.nk[w] * d * d);
+                                    s = fmaf(P.prim[((size_t)T.a * W + w) * P.nq + q], gw, s);
+                                }
+                            }
+                            acc[k][qi] = fmaf(P.cv[((size_t)(b_base + bo[k])) * P.nq + q], s, acc[k][qi]);
+                        }
+                    }
+                }
+            }
+        }
+
+        // transpose through shared memory: tile [128 events][32 voxels]
+        float* tt = reinterpret_cast<float*>(smem);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi) tt[(k * 32 + lane) * 33 + warp * 4 + qi] = acc[k][qi];
+        __syncthreads();
+        if (P.rows) {
+            for (int i = tid; i < kET * kQT; i += kRowThreads) {
+                const int e = i >> 5, ql = i & 31;
+                const int q = qt * kQT + ql;
+                if (e < T.count && q < P.nq)
+                    P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + q] = tt[e * 33 + ql];
+            }
+        }
+        if (P.lam && tid < T.count) {
+            const int e = tid;
+            float s = 0.f;
+            const int qmax = min(kQT, P.nq - qt * kQT);
+            for (int ql = 0; ql < qmax; ++ql) s = fmaf(P.lam[qt * kQT + ql], tt[e * 33 + ql], s);
+            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+static RowParams make_params(lm_handle* h, const RowLaunch& L) {
+    const ModelConst& m = h->mc;
+    RowParams P;
+    P.tab = h->d_tab;
+    P.cs = h->d_cs;
+    P.cv = h->d_cv;
+    P.prim = h->d_prim;
+    P.tiles = L.tiles;
+    P.tile_begin = L.tile_begin;
+    P.tile_end = L.tile_end;
+    P.ev_bin = L.ev_bin;
+    P.ev_e = L.ev_e;
+    P.lam = L.lam_v;
+    P.rows = L.rows;
+    P.row_base = L.row_base;
+    P.row_stride = L.row_stride;
+    P.ypart = L.ypart;
+    P.ypart_stride = L.ypart_stride;
+    P.status = h->d_status;
+    P.W = m.W;
+    P.B = m.B;
+    P.nq = m.nq;
+    P.nqt = m.nqt;
+    P.npc = m.npc;
+    P.tab_stage_bytes = (uint32_t)(3 * m.W * kQT * kPC * 4);
+    uint32_t stage = P.tab_stage_bytes + (uint32_t)(m.B * kCPad * 4);
+    const uint32_t tr = kET * 33 * 4;   // epilogue transpose tile
+    if (stage < tr) stage = tr;
+    P.stage_bytes = (stage + 127u) & ~127u;
+    P.lc = h->lc;
+    return P;
+}
+
+size_t row_smem_bytes(const lm_handle* h) {
+    RowParams P = make_params(const_cast<lm_handle*>(h), RowLaunch{});
+    return 2 * (size_t)P.stage_bytes;
+}
+
+int row_kernel_occupancy(lm_handle* h) {
+    const size_t smem = row_smem_bytes(h);
+    int dev = 0;
+    LMMEW_CUDA(cudaGetDevice(&dev));
+    int max_optin = 0;
+    LMMEW_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem + 64 > (size_t)max_optin)
+        return set_error(LMMEW_ERR_INVALID_ARG,
+                         "lines x bins too large for the row kernel's shared-memory stages");
+    LMMEW_CUDA(cudaFuncSetAttribute(k_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = 0;
+    LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_row, kRowThreads, smem));
+    LMMEW_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    h->row_blocks_per_sm = blocks > 0 ? blocks : 1;
+    return LMMEW_OK;
+}
+
+int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
+    const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
+    if (n_units <= 0) return LMMEW_OK;
+    RowParams P = make_params(h, L);
+    const int grid = std::min(n_units, h->sm_count * h->row_blocks_per_sm);
+    k_row<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+}  // namespace lmmew

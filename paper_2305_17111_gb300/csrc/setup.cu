@@ -1,0 +1,545 @@
+// Model set-up on the GPU (once per lm_create): exact line integrals through
+// the density map (Eq. radpath), path sensitivities s(P, E_0^w) of Eq. (s_p)
+// for the unscattered and single-scatter paths of every (angle, voxel,
+// scatter point, line), the collimator tables and the per-angle sensitivity
+// image (denominator of Eq. os-lm-mlem).  Arithmetic is FP64; the tables the
+// hot kernel streams are rounded to FP32 at the end.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lmmew_internal.cuh"
+
+namespace lmmew {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMeC2 = 510.99895;     // electron rest energy, keV
+constexpr double kLog2e = 1.4426950408889634;
+
+__device__ __forceinline__ double mu_water(const ModelConst& m, double e) {
+    if (m.n_knots == 1) return m.knot_mu[0];
+    int s = 0;
+    while (s < m.n_knots - 2 && e >= m.knot_e[s + 1]) ++s;
+    const double t = (e - m.knot_e[s]) / (m.knot_e[s + 1] - m.knot_e[s]);
+    return m.knot_mu[s] + t * (m.knot_mu[s + 1] - m.knot_mu[s]);
+}
+
+// sigma of the energy response: FWHM = frac * E * (E / E_ref)^expo
+__host__ __device__ __forceinline__ double sigma_energy(double frac, double e_ref, double expo,
+                                                        double e) {
+    return frac * e * pow(e / e_ref, expo) / (2.0 * sqrt(2.0 * log(2.0)));
+}
+
+__device__ __forceinline__ double sigma_coll(const ModelConst& m, double depth) {
+    return (m.fwhm0 + m.slope * depth) / (2.0 * sqrt(2.0 * log(2.0)));
+}
+
+// Gaussian mass on [lo, hi]; erfc on the tail side keeps small masses accurate.
+__device__ __forceinline__ double gauss_mass(double lo, double hi, double mean, double sigma) {
+    const double inv = 1.0 / (sqrt(2.0) * sigma);
+    const double a = (lo - mean) * inv, b = (hi - mean) * inv;
+    if (a >= 0.0) return 0.5 * (erfc(a) - erfc(b));
+    if (b <= 0.0) return 0.5 * (erfc(-b) - erfc(-a));
+    return 0.5 * (erf(b) - erf(a));
+}
+
+__device__ __forceinline__ double window_mass(const ModelConst& m, double e) {
+    const double s = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e);
+    double t = 0.0;
+    for (int k = 0; k < m.n_win; ++k) t += gauss_mass(m.win_lo[k], m.win_hi[k], e, s);
+    return t;
+}
+
+// Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E.
+__device__ __forceinline__ double kn_shape(double e, double c) {
+    const double r = 1.0 / (1.0 + (e / kMeC2) * (1.0 - c));
+    return r * r * (r + 1.0 / r - (1.0 - c * c));
+}
+
+// Integral over [0, 2 pi) of the KN shape, in closed form: with a = 1 + k,
+// b = k, D = a^2 - b^2, int dth/(a - b cos) = 2 pi / sqrt(D),
+// int dth/(a - b cos)^3 = pi (2a^2 + b^2) / D^(5/2) and, by parts,
+// int sin^2/(a - b cos)^2 = (a int 1/(a - b cos) - 2 pi) / b^2.
+__device__ double kn_plane_norm(double e) {
+    const double k = e / kMeC2;
+    if (k < 1e-4) return 3.0 * kPi * (1.0 - 2.0 * k);   // Thomson limit + first order
+    const double a = 1.0 + k, b = k, d = 1.0 + 2.0 * k;
+    const double i1 = 2.0 * kPi / sqrt(d);
+    const double i3 = kPi * (2.0 * a * a + b * b) * pow(d, -2.5);
+    return i3 + i1 - (a * i1 - 2.0 * kPi) / (b * b);
+}
+
+__device__ __forceinline__ double rho_pix(const float* rho, int n, int ix, int iy) {
+    return (ix < 0 || iy < 0 || ix >= n || iy >= n) ? 0.0 : (double)rho[iy * n + ix];
+}
+
+// Exact integral of the pixelwise-constant density along the segment
+// (x0,y0)->(x1,y1), pixel units from the image corner, result in pixel
+// lengths.  Incremental grid walk: the next vertical and horizontal grid
+// crossings are tracked, every piece between consecutive crossings lies in
+// one pixel (looked up at the piece's midpoint).  A ray running exactly
+// along a grid line takes the mean of the pixels on its two sides.
+__device__ double seg_integral(const float* rho, int n, double x0, double y0, double x1,
+                               double y1) {
+    const double dx = x1 - x0, dy = y1 - y0;
+    const double len = sqrt(dx * dx + dy * dy);
+    if (len == 0.0) return 0.0;
+    double tmin = 0.0, tmax = 1.0;
+    if (dx == 0.0) {
+        if (x0 < 0.0 || x0 > n) return 0.0;
+    } else {
+        double ta = -x0 / dx, tb = (n - x0) / dx;
+        if (ta > tb) { const double t = ta; ta = tb; tb = t; }
+        tmin = fmax(tmin, ta);
+        tmax = fmin(tmax, tb);
+    }
+    if (dy == 0.0) {
+        if (y0 < 0.0 || y0 > n) return 0.0;
+    } else {
+        double ta = -y0 / dy, tb = (n - y0) / dy;
+        if (ta > tb) { const double t = ta; ta = tb; tb = t; }
+        tmin = fmax(tmin, ta);
+        tmax = fmin(tmax, tb);
+    }
+    if (!(tmax > tmin)) return 0.0;
+    const bool vline = (dx == 0.0 && x0 == floor(x0));
+    const bool hline = (dy == 0.0 && y0 == floor(y0));
+    const int sx = dx > 0.0 ? 1 : (dx < 0.0 ? -1 : 0);
+    const int sy = dy > 0.0 ? 1 : (dy < 0.0 ? -1 : 0);
+    const double xs = x0 + tmin * dx, ys = y0 + tmin * dy;
+    int kx = sx > 0 ? (int)floor(xs) + 1 : (int)ceil(xs) - 1;
+    int ky = sy > 0 ? (int)floor(ys) + 1 : (int)ceil(ys) - 1;
+    double tx = sx ? (kx - x0) / dx : 2.0 * tmax + 1.0;
+    double ty = sy ? (ky - y0) / dy : 2.0 * tmax + 1.0;
+    double t = tmin, acc = 0.0;
+    for (int guard = 0; guard < 4 * n + 16 && t < tmax; ++guard) {
+        const double tn = fmin(fmin(tx, ty), tmax);
+        if (tn > t) {
+            const double tm = 0.5 * (t + tn);
+            const double px = x0 + tm * dx, py = y0 + tm * dy;
+            double r;
+            if (vline) {
+                const int ix = (int)x0, iy = (int)floor(py);
+                r = 0.5 * (rho_pix(rho, n, ix - 1, iy) + rho_pix(rho, n, ix, iy));
+            } else if (hline) {
+                const int iy = (int)y0, ix = (int)floor(px);
+                r = 0.5 * (rho_pix(rho, n, ix, iy - 1) + rho_pix(rho, n, ix, iy));
+            } else {
+                r = rho_pix(rho, n, (int)floor(px), (int)floor(py));
+            }
+            acc += (tn - t) * r;
+        }
+        t = tn;
+        if (sx && tn == tx) { kx += sx; tx = (kx - x0) / dx; }
+        if (sy && tn == ty) { ky += sy; ty = (ky - y0) / dy; }
+    }
+    return acc * len;
+}
+
+__device__ __forceinline__ double det_integral(const float* rho, int n, double x, double y,
+                                               double c, double s) {
+    const double far = 4.0 * n + 8.0;
+    return seg_integral(rho, n, x, y, x + far * c, y + far * s);
+}
+
+// ---------------------------------------------------------------- kernels
+
+__global__ void k_line_consts(ModelConst m, double* out /* [W][4] */) {
+    const int w = threadIdx.x;
+    if (w >= m.W) return;
+    const double e = m.line_e[w];
+    const double s = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e);
+    out[w * 4 + 0] = kn_plane_norm(e);
+    out[w * 4 + 1] = -kLog2e / (2.0 * s * s);
+    out[w * 4 + 2] = 1.0 / (sqrt(2.0 * kPi) * s);
+    out[w * 4 + 3] = mu_water(m, e);
+}
+
+__global__ void k_cell_means(const float* rho, int n, int S, double* mean) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S * S) return;
+    const int f = n / S, mx = c % S, my = c / S;
+    double sum = 0.0;
+    for (int iy = my * f; iy < (my + 1) * f; ++iy)
+        for (int ix = mx * f; ix < (mx + 1) * f; ++ix) sum += rho[iy * n + ix];
+    mean[c] = sum / (double)(f * f);
+}
+
+// Detector-leg path integrals (cm) for voxels and scatter points.
+__global__ void k_gamma_det(ModelConst m, const float* rho, const double* cs_a,
+                            const int* q_pix, const int* p_cell, double* g_q, double* g_p) {
+    const int a = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.nq + m.np) return;
+    double x, y;
+    if (i < m.nq) {
+        const int pix = q_pix[i];
+        x = (pix % m.n) + 0.5;
+        y = (pix / m.n) + 0.5;
+    } else {
+        const int c = p_cell[i - m.nq];
+        x = ((c % m.S) + 0.5) * m.f;
+        y = ((c / m.S) + 0.5) * m.f;
+    }
+    const double g = m.h * det_integral(rho, m.n, x, y, cs_a[2 * a], cs_a[2 * a + 1]);
+    if (i < m.nq) g_q[(size_t)a * m.nq + i] = g;
+    else g_p[(size_t)a * m.np + (i - m.nq)] = g;
+}
+
+// Emission-to-scatter path integrals and distances (cm).
+__global__ void k_gamma_qp(ModelConst m, const float* rho, const int* q_pix, const int* p_cell,
+                           double* g_qp, double* d_qp) {
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (size_t)m.nq * m.np) return;
+    const int q = (int)(k / m.np), p = (int)(k % m.np);
+    const int pix = q_pix[q], c = p_cell[p];
+    const double xq = (pix % m.n) + 0.5, yq = (pix / m.n) + 0.5;
+    const double xp = ((c % m.S) + 0.5) * m.f, yp = ((c / m.S) + 0.5) * m.f;
+    g_qp[k] = m.h * seg_integral(rho, m.n, xq, yq, xp, yp);
+    d_qp[k] = m.h * sqrt((xp - xq) * (xp - xq) + (yp - yq) * (yp - yq));
+}
+
+__device__ __forceinline__ void point_cm(const ModelConst& m, bool voxel, int idx, const int* q_pix,
+                                         const int* p_cell, double* x, double* y) {
+    if (voxel) {
+        const int pix = q_pix[idx];
+        *x = ((pix % m.n) + 0.5 - 0.5 * m.n) * m.h;
+        *y = ((pix / m.n) + 0.5 - 0.5 * m.n) * m.h;
+    } else {
+        const int c = p_cell[idx];
+        *x = (((c % m.S) + 0.5) * m.f - 0.5 * m.n) * m.h;
+        *y = (((c / m.S) + 0.5) * m.f - 0.5 * m.n) * m.h;
+    }
+}
+
+// Collimator bin probabilities: voxels [A][B][nq], scatter points [A][npc][B][kCPad].
+__global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
+                             const int* p_cell, float* cv, float* csp) {
+    const int a = blockIdx.z, b = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_p_pad = m.npc * kPC;
+    if (i >= m.nq + n_p_pad) return;
+    const double c = cs_a[2 * a], s = cs_a[2 * a + 1];
+    const double lo = -0.5 * m.B * m.bin_w + b * m.bin_w, hi = lo + m.bin_w;
+    if (i < m.nq) {
+        double x, y;
+        point_cm(m, true, i, q_pix, p_cell, &x, &y);
+        const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
+        cv[((size_t)a * m.B + b) * m.nq + i] = (float)gauss_mass(lo, hi, u, sg);
+    } else {
+        const int p = i - m.nq;
+        float val = 0.f;
+        if (p < m.np) {
+            double x, y;
+            point_cm(m, false, p, q_pix, p_cell, &x, &y);
+            const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
+            val = (float)gauss_mass(lo, hi, u, sg);
+        }
+        const int pc = p / kPC, pl = p % kPC;
+        csp[(((size_t)a * m.npc + pc) * m.B + b) * kCPad + pl] = val;
+    }
+}
+
+// Unscattered paths: prim[a][w][q] = alpha_w exp(-mu_w(E_w) gamma_det) and the
+// primary part of the per-angle sensitivity.
+__global__ void k_primary(ModelConst m, const double* cs_a, const int* q_pix, const double* g_q,
+                          const double* mu_line, float* prim, double* sens_a) {
+    const int a = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m.nq) return;
+    double x, y;
+    point_cm(m, true, q, q_pix, nullptr, &x, &y);
+    const double c = cs_a[2 * a], s = cs_a[2 * a + 1];
+    const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
+    const double on_det = gauss_mass(-0.5 * m.B * m.bin_w, 0.5 * m.B * m.bin_w, u, sg);
+    double sens = 0.0;
+    for (int w = 0; w < m.W; ++w) {
+        const double v = m.alpha[w] * exp(-mu_line[w] * g_q[(size_t)a * m.nq + q]);
+        prim[((size_t)a * m.W + w) * m.nq + q] = (float)v;
+        sens += v * on_det * window_mass(m, m.line_e[w]);
+    }
+    sens_a[(size_t)a * m.nq + q] = m.T * sens;
+}
+
+// Single-scatter paths.  One warp per (angle, voxel), lanes over scatter
+// points.  Writes the FP32 hot-kernel tables
+//   lh = log2(alpha_w s(P) / (sqrt(2 pi) sigma_E(E'))), nk = -log2(e)/(2 sigma_E(E')^2), E'
+// and adds sum_w alpha_w sum_p s(P) Prob(detector) Prob(window | E') to the
+// per-angle sensitivity.
+__global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_a,
+                                                 const int* q_pix, const int* p_cell,
+                                                 const double* p_rho, const double* g_qp,
+                                                 const double* d_qp, const double* g_p,
+                                                 const double* mu_line, float* tab,
+                                                 double* sens_a) {
+    const int a = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 8 + warp;
+    if (q >= m.nq) return;
+    const double c = cs_a[2 * a], s = cs_a[2 * a + 1];
+    const int pix = q_pix[q];
+    const int qx = pix % m.n, qy = pix / m.n;
+    const int own_cell = (qy / m.f) * m.S + (qx / m.f);
+    const double xq = qx + 0.5, yq = qy + 0.5;
+    const int qt = q / kQT, ql = q % kQT;
+    const double half_det = 0.5 * m.B * m.bin_w;
+    double sens = 0.0;
+    for (int pc = 0; pc < m.npc; ++pc) {
+        const int p = pc * kPC + lane;
+        float* base = tab + (((size_t)a * m.nqt + qt) * m.npc + pc) * (size_t)(3 * m.W * kQT * kPC);
+        if (p >= m.np) {
+            for (int w = 0; w < m.W; ++w) {
+                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kNegHuge;
+                base[((1 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
+                base[((2 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
+            }
+            continue;
+        }
+        const int cell = p_cell[p];
+        const double xp = ((cell % m.S) + 0.5) * m.f, yp = ((cell / m.S) + 0.5) * m.f;
+        const size_t k = (size_t)q * m.np + p;
+        const double d = d_qp[k];
+        const double ux = (xp - xq) * m.h / d, uy = (yp - yq) * m.h / d;
+        const double cos_t = ux * c + uy * s;
+        const double xpc = (xp - 0.5 * m.n) * m.h, ypc = (yp - 0.5 * m.n) * m.h;
+        const double u = -xpc * s + ypc * c;
+        const double on_det = gauss_mass(-half_det, half_det, u,
+                                         sigma_coll(m, m.r_det - (xpc * c + ypc * s)));
+        const double gqp = g_qp[k], gp = g_p[(size_t)a * m.np + p];
+        const double inter = p_rho[p] * m.cell_area / (2.0 * kPi * d);
+        for (int w = 0; w < m.W; ++w) {
+            const double e0 = m.line_e[w];
+            const double e1 = e0 / (1.0 + (e0 / kMeC2) * (1.0 - cos_t));
+            const double mu0 = mu_line[w], mu1 = mu_water(m, e1);
+            double path = 0.0;
+            if (cell != own_cell)
+                path = exp(-mu0 * gqp - mu1 * gp) * inter * mu0 * 2.0 * kPi *
+                       kn_shape(e0, cos_t) / m.kn_norm[w];
+            const double sg = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
+            const double wgt = m.alpha[w] * path / (sqrt(2.0 * kPi) * sg);
+            base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)log2(wgt) : kNegHuge;
+            base[((1 * m.W + w) * kQT + ql) * kPC + lane] = (float)(-kLog2e / (2.0 * sg * sg));
+            base[((2 * m.W + w) * kQT + ql) * kPC + lane] = (float)e1;
+            if (path > 0.0) sens += m.alpha[w] * path * on_det * window_mass(m, e1);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);
+    if (lane == 0) sens_a[(size_t)a * m.nq + q] += m.T * sens;
+}
+
+__global__ void k_sum_subsets(const double* sens_a, int A, int nq, int parts, double* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
+    if (q >= nq) return;
+    double acc = 0.0;
+    for (int a = s; a < A; a += parts) acc += sens_a[(size_t)a * nq + q];
+    out[(size_t)s * nq + q] = acc;
+}
+
+__global__ void k_sum_all(const double* sens_a, int A, int nq, double* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double acc = 0.0;
+    for (int a = 0; a < A; ++a) acc += sens_a[(size_t)a * nq + q];
+    out[q] = acc;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+int subset_sensitivity(lm_handle* h, int parts, cudaStream_t st) {
+    const ModelConst& m = h->mc;
+    if (h->sens_parts != parts) {
+        if (h->d_sens_sub) { cudaFree(h->d_sens_sub); h->d_sens_sub = nullptr; }
+        const size_t bytes = sizeof(double) * (size_t)(parts + 1) * m.nq;
+        if (cudaMalloc(&h->d_sens_sub, bytes) != cudaSuccess)
+            return set_error(LMMEW_ERR_OOM, "cannot allocate subset sensitivities");
+        dim3 g((m.nq + 255) / 256, parts);
+        k_sum_subsets<<<g, 256, 0, st>>>(h->d_sens_a, m.A, m.nq, parts, h->d_sens_sub);
+        k_sum_all<<<(m.nq + 255) / 256, 256, 0, st>>>(h->d_sens_a, m.A, m.nq,
+                                                       h->d_sens_sub + (size_t)parts * m.nq);
+        LMMEW_CUDA(cudaGetLastError());
+        h->sens_parts = parts;
+    }
+    return LMMEW_OK;
+}
+
+int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_host) {
+    ModelConst& m = h->mc;
+    const int n = m.n;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, 0);
+
+    // support voxel list (raster order)
+    std::vector<int> q_pix;
+    for (int i = 0; i < n * n; ++i)
+        if (support_host ? support_host[i] != 0 : rho_host[i] > 0.f) q_pix.push_back(i);
+    m.nq = (int)q_pix.size();
+    if (m.nq == 0) return set_error(LMMEW_ERR_INVALID_ARG, "the support holds no voxel");
+    m.nqt = (m.nq + kQT - 1) / kQT;
+
+    DevBuf d_rho, d_cs_a, d_cell_mean, d_p_cell, d_p_rho, d_gq, d_gp, d_gqp, d_dqp, d_lc;
+    LMMEW_CUDA(cudaMalloc(&d_rho.p, sizeof(float) * n * n));
+    LMMEW_CUDA(cudaMemcpy(d_rho.p, rho_host, sizeof(float) * n * n, cudaMemcpyHostToDevice));
+    const float* rho = (const float*)d_rho.p;
+
+    // scatter points: cells with positive mean density (raster order)
+    std::vector<int> p_cell;
+    std::vector<double> p_rho;
+    if (m.S > 0) {
+        LMMEW_CUDA(cudaMalloc(&d_cell_mean.p, sizeof(double) * m.S * m.S));
+        k_cell_means<<<(m.S * m.S + 255) / 256, 256>>>(rho, n, m.S, (double*)d_cell_mean.p);
+        LMMEW_CUDA(cudaGetLastError());
+        std::vector<double> mean(m.S * m.S);
+        LMMEW_CUDA(cudaMemcpy(mean.data(), d_cell_mean.p, sizeof(double) * m.S * m.S,
+                              cudaMemcpyDeviceToHost));
+        for (int c = 0; c < m.S * m.S; ++c)
+            if (mean[c] > 0.0) { p_cell.push_back(c); p_rho.push_back(mean[c]); }
+    }
+    m.np = (int)p_cell.size();
+    m.npc = (m.np + kPC - 1) / kPC;
+
+    // collimator blur must stay positive for every point and angle
+    {
+        double rmax = 0.0;
+        for (int pix : q_pix) {
+            const double x = ((pix % n) + 0.5 - 0.5 * n) * m.h, y = ((pix / n) + 0.5 - 0.5 * n) * m.h;
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+        for (int c : p_cell) {
+            const double x = (((c % m.S) + 0.5) * m.f - 0.5 * n) * m.h;
+            const double y = (((c / m.S) + 0.5) * m.f - 0.5 * n) * m.h;
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+        const double lo = m.fwhm0 + m.slope * (m.r_det - rmax);
+        const double hi = m.fwhm0 + m.slope * (m.r_det + rmax);
+        if (!(lo > 0.0 && hi > 0.0))
+            return set_error(LMMEW_ERR_INVALID_ARG,
+                             "collimator FWHM is not positive at some depth of the model");
+    }
+
+    // detector directions, quarter turns exact
+    std::vector<double> cs_a(2 * m.A);
+    for (int a = 0; a < m.A; ++a) {
+        if ((4 * a) % m.A == 0) {
+            const int k = (4 * a) / m.A;
+            const double cc[4] = {1, 0, -1, 0}, ss[4] = {0, 1, 0, -1};
+            cs_a[2 * a] = cc[k];
+            cs_a[2 * a + 1] = ss[k];
+        } else {
+            cs_a[2 * a] = cos(2.0 * kPi * a / m.A);
+            cs_a[2 * a + 1] = sin(2.0 * kPi * a / m.A);
+        }
+    }
+    LMMEW_CUDA(cudaMalloc(&d_cs_a.p, sizeof(double) * 2 * m.A));
+    LMMEW_CUDA(cudaMemcpy(d_cs_a.p, cs_a.data(), sizeof(double) * 2 * m.A, cudaMemcpyHostToDevice));
+    const double* dcs = (const double*)d_cs_a.p;
+
+    LMMEW_CUDA(cudaMalloc(&h->d_q_pix, sizeof(int) * m.nq));
+    LMMEW_CUDA(cudaMemcpy(h->d_q_pix, q_pix.data(), sizeof(int) * m.nq, cudaMemcpyHostToDevice));
+    const int np_alloc = std::max(m.np, 1);
+    LMMEW_CUDA(cudaMalloc(&d_p_cell.p, sizeof(int) * np_alloc));
+    LMMEW_CUDA(cudaMalloc(&d_p_rho.p, sizeof(double) * np_alloc));
+    if (m.np) {
+        LMMEW_CUDA(cudaMemcpy(d_p_cell.p, p_cell.data(), sizeof(int) * m.np, cudaMemcpyHostToDevice));
+        LMMEW_CUDA(cudaMemcpy(d_p_rho.p, p_rho.data(), sizeof(double) * m.np, cudaMemcpyHostToDevice));
+    }
+
+    // per-line constants: KN plane normaliser, energy response, mu at the line
+    LMMEW_CUDA(cudaMalloc(&d_lc.p, sizeof(double) * 4 * LMMEW_MAX_LINES));
+    k_line_consts<<<1, 32>>>(m, (double*)d_lc.p);
+    LMMEW_CUDA(cudaGetLastError());
+    double lc[4 * LMMEW_MAX_LINES];
+    LMMEW_CUDA(cudaMemcpy(lc, d_lc.p, sizeof(lc), cudaMemcpyDeviceToHost));
+    double mu_line_h[LMMEW_MAX_LINES];
+    for (int w = 0; w < m.W; ++w) {
+        m.kn_norm[w] = lc[4 * w + 0];
+        h->lc.e[w] = (float)m.line_e[w];
+        h->lc.nk[w] = (float)lc[4 * w + 1];
+        h->lc.norm[w] = (float)lc[4 * w + 2];
+        mu_line_h[w] = lc[4 * w + 3];
+    }
+    DevBuf d_mu_line;
+    LMMEW_CUDA(cudaMalloc(&d_mu_line.p, sizeof(mu_line_h)));
+    LMMEW_CUDA(cudaMemcpy(d_mu_line.p, mu_line_h, sizeof(mu_line_h), cudaMemcpyHostToDevice));
+    const double* mu_line = (const double*)d_mu_line.p;
+
+    // path integrals
+    LMMEW_CUDA(cudaMalloc(&d_gq.p, sizeof(double) * (size_t)m.A * m.nq));
+    LMMEW_CUDA(cudaMalloc(&d_gp.p, sizeof(double) * (size_t)m.A * np_alloc));
+    {
+        dim3 g((m.nq + m.np + 127) / 128, m.A);
+        k_gamma_det<<<g, 128>>>(m, rho, dcs, h->d_q_pix, (const int*)d_p_cell.p,
+                                (double*)d_gq.p, (double*)d_gp.p);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+    if (m.np) {
+        const size_t k = (size_t)m.nq * m.np;
+        LMMEW_CUDA(cudaMalloc(&d_gqp.p, sizeof(double) * k));
+        LMMEW_CUDA(cudaMalloc(&d_dqp.p, sizeof(double) * k));
+        k_gamma_qp<<<(unsigned)((k + 127) / 128), 128>>>(m, rho, h->d_q_pix,
+                                                         (const int*)d_p_cell.p,
+                                                         (double*)d_gqp.p, (double*)d_dqp.p);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+
+    // collimator tables
+    const size_t cv_n = (size_t)m.A * m.B * m.nq;
+    const size_t cs_n = (size_t)m.A * std::max(m.npc, 1) * m.B * kCPad;
+    if (cudaMalloc(&h->d_cv, sizeof(float) * cv_n) != cudaSuccess ||
+        cudaMalloc(&h->d_cs, sizeof(float) * cs_n) != cudaSuccess)
+        return set_error(LMMEW_ERR_OOM, "cannot allocate collimator tables");
+    LMMEW_CUDA(cudaMemset(h->d_cs, 0, sizeof(float) * cs_n));
+    {
+        dim3 g((m.nq + m.npc * kPC + 127) / 128, m.B, m.A);
+        k_collimator<<<g, 128>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, h->d_cv, h->d_cs);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+
+    // unscattered paths + per-angle sensitivity
+    if (cudaMalloc(&h->d_prim, sizeof(float) * (size_t)m.A * m.W * m.nq) != cudaSuccess ||
+        cudaMalloc(&h->d_sens_a, sizeof(double) * (size_t)m.A * m.nq) != cudaSuccess)
+        return set_error(LMMEW_ERR_OOM, "cannot allocate primary tables");
+    {
+        dim3 g((m.nq + 127) / 128, m.A);
+        k_primary<<<g, 128>>>(m, dcs, h->d_q_pix, (const double*)d_gq.p, mu_line, h->d_prim,
+                              h->d_sens_a);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+
+    // single-scatter paths
+    if (m.np) {
+        h->tab_bytes = sizeof(float) * (size_t)m.A * m.nqt * m.npc * 3 * m.W * kQT * kPC;
+        if (cudaMalloc(&h->d_tab, h->tab_bytes) != cudaSuccess)
+            return set_error(LMMEW_ERR_OOM, "cannot allocate scatter tables (" +
+                                                std::to_string(h->tab_bytes >> 20) + " MiB)");
+        LMMEW_CUDA(cudaMemset(h->d_tab, 0, h->tab_bytes));
+        dim3 g((m.nq + 7) / 8, m.A);
+        k_scatter<<<g, 256>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
+                              (const double*)d_gqp.p, (const double*)d_dqp.p,
+                              (const double*)d_gp.p, mu_line, h->d_tab, h->d_sens_a);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+    LMMEW_CUDA(cudaMalloc(&h->d_status, sizeof(int)));
+    LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    cudaEventRecord(e1, 0);
+    LMMEW_CUDA(cudaDeviceSynchronize());
+    cudaEventElapsedTime(&h->setup_ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return subset_sensitivity(h, h->n_subsets_default, 0) == LMMEW_OK
+               ? (cudaDeviceSynchronize() == cudaSuccess ? LMMEW_OK
+                                                         : set_error(LMMEW_ERR_CUDA, "set-up"))
+               : LMMEW_ERR_OOM;
+}
+
+}  // namespace lmmew

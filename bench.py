@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the LM-MEW OSEM hot path on GB300.
+
+One step = one full LM-OSEM iteration (every subset: event sort, system-matrix
+rows computed on the fly, forward projection, ratio, back projection, update)
+over the 64x64 study-scale workload (300k events, 60 angles, 64 bins, 64x64
+scatter grid, 3 emission lines, 8 subsets), through the C ABI.
+
+Metric: system-matrix elements per second (events x support voxels per
+step / step time), plus seconds per OSEM iteration.  With --gpus N under
+torchrun every rank reconstructs its own independent noise realisation
+(replicas; the path has no cross-GPU exchange), the value is the whole job's
+elements / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (its forward projection of a subset of events) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "lmmew_64"
+METRIC = "sys-matrix elems/s"
+UNIT = "elem/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(sc, nq=None, npts=None):
+    cfg = {"workload": f"{sc.name}: {sc.n}x{sc.n} image {sc.pixel_cm} cm, {sc.n_angles} angles, "
+                       f"{sc.n_bins} bins, {sc.scatter_n}x{sc.scatter_n} scatter grid, "
+                       f"{len(sc.line_keV)} lines {'/'.join(str(int(e)) for e in sc.line_keV)} keV, "
+                       f"{sc.n_events} events, {sc.n_subsets} subsets",
+           "events": sc.n_events, "subsets": sc.n_subsets, "step": "one LM-OSEM iteration"}
+    if nq is not None:
+        cfg["support_voxels"] = nq
+    if npts is not None:
+        cfg["scatter_points"] = npts
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return None
+
+
+# Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
+# of the exact path is the SFU rate: every path term needs one ex2.
+EX2_PER_SM_PER_CLK = 32
+
+
+def ex2_peak(sm_count, mhz):
+    return sm_count * EX2_PER_SM_PER_CLK * mhz * 1e6
+
+
+# ------------------------------------------------------------------ CPU baseline
+class OracleSample:
+    """The FP64 oracle, as it stands, timed on bounded samples of the workload."""
+
+    def __init__(self, sc):
+        import numpy as np
+
+        import oracle
+        from synthetic import simulate_cached
+        self.sc = sc
+        ph = sc.make_phantom()
+        self.ev = simulate_cached(sc)
+        self.orc = oracle.Model.from_scenario(sc, ph.rho)
+        self.lam = (ph.rho.reshape(-1) > 0).astype(np.float64)
+        self.cores = oracle.max_threads()
+
+    def run(self, n_sample, seed=0):
+        import numpy as np
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(len(self.ev), size=min(n_sample, len(self.ev)), replace=False))
+        sub = self.ev.subset(idx)
+        t0 = time.perf_counter()
+        self.orc.forward(sub, self.lam)
+        dt = time.perf_counter() - t0
+        return len(sub) * self.orc.nq, dt
+
+
+def cpu_baseline(sc, n_sample=None):
+    o = OracleSample(sc)
+    if n_sample is None:
+        n_sample = 400 if sc.n <= 64 else 60
+    elems, dt = o.run(n_sample)
+    return {"value": elems / dt, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+            "sample": f"{n_sample} random events of {sc.name}: FP64 oracle row + forward "
+                      f"projection ({elems:.3e} elements in {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from synthetic import preset
+    sc = preset(args.workload)
+    n_per_step = 100 if sc.n <= 64 else 16
+    o = OracleSample(sc)
+    tot_e, tot_t = 0.0, 0.0
+    for step in range(args.warmup + args.steps):
+        elems, dt = o.run(n_per_step, seed=step)
+        if step >= args.warmup:
+            tot_e += elems
+            tot_t += dt
+    value = tot_e / tot_t
+    base = {"cores": o.cores}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(sc),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
+                             "kind": "oracle",
+                             "sample": f"each step: {n_per_step} random events of "
+                                       f"{sc.name}, FP64 oracle row + forward projection"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, local_rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    sc = preset(args.workload)
+    ph = sc.make_phantom()
+    # every rank reconstructs its own noise realisation (seed + rank)
+    ev = simulate_cached(sc, seed=sc.seed + rank)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    img = lam0.clone()
+    n_sub = sc.n_subsets
+    J, nq = len(ev), model.nq
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    it = 0
+    for _ in range(args.warmup):
+        model.osem(dev, img, n_sub, it + 1, start_iter=it)
+        it += 1
+    torch.cuda.synchronize()
+    model.profile_read()                      # reset counters
+    model.profile_enable(True)
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        model.osem(dev, img, n_sub, it + 1, start_iter=it)
+        it += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = model.profile_read()
+    model.profile_enable(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    elems_step = J * nq
+    value = world * elems_step * args.steps / (ms / 1e3)
+
+    # end to end through the same call with host buffers: copy the step's
+    # events from pinned host memory, run the iteration, read the image back
+    h_ang = torch.from_numpy(np.asarray(ev.angle, np.uint16).view(np.int16).copy()).pin_memory()
+    h_bin = torch.from_numpy(np.asarray(ev.bin, np.uint16).view(np.int16).copy()).pin_memory()
+    h_en = torch.from_numpy(np.asarray(ev.energy, np.float32).copy()).pin_memory()
+    h_img = torch.empty(sc.n * sc.n, dtype=torch.float32).pin_memory()
+    d_ang = torch.empty_like(h_ang, device="cuda")
+    d_bin = torch.empty_like(h_bin, device="cuda")
+    d_en = torch.empty_like(h_en, device="cuda")
+    dev2 = lm.DeviceEvents(d_ang, d_bin, d_en)
+    img2 = img.clone()
+    barrier()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        d_ang.copy_(h_ang, non_blocking=True)
+        d_bin.copy_(h_bin, non_blocking=True)
+        d_en.copy_(h_en, non_blocking=True)
+        model.osem(dev2, img2, n_sub, it + 1, start_iter=it)
+        h_img.copy_(img2, non_blocking=True)
+        it += 1
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = f0.elapsed_time(f1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = h_ang.numel() * 2 + h_bin.numel() * 2 + h_en.numel() * 4
+    d2h = h_img.numel() * 4
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(local_rank)
+    sm_count = props.multi_processor_count
+    peaks = measured_peaks() or {}
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak = ex2_peak(sm_count, sm_max)
+    achieved = prof["terms"] / (prof["ms"] / 1e3) if prof["ms"] > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(sc, nq, model.np_scatter),
+                       l2="inputs larger than L2: %.2f GB of path tables stream every step"
+                          % (model.table_bytes / 1e9),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "s_per_osem_iter": ms_per_step / 1e3,
+        "terms_per_s": prof["terms"] / (ms / 1e3) if ms > 0 else None,
+        "setup_ms": model.setup_ms,
+        "clocks": clk,
+        "e2e": {"value": world * elems_step * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(prof["kernels"]),
+        "roofline": {"bound": "alu", "kernel": "k_row (fused row + forward)",
+                     "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tex2/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_basis": f"{sm_count} SMs x {EX2_PER_SM_PER_CLK} ex2/clk x "
+                                   f"{sm_max:.0f} MHz",
+                     "row_kernel_share": prof["ms"] / ms if ms > 0 else None},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, local_rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

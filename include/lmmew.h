@@ -191,12 +191,14 @@ const char* lm_last_error(void);
  * library, not part of the paper's method).  While enabled, CUDA events are
  * recorded on the caller's stream around every launch of the fused
  * system-matrix row kernel.  lm_profile_read synchronises those events and
- * writes out4[0] = total row-kernel time in ms, out4[1] = launches,
- * out4[2] = exponentials evaluated by those launches (one per path term),
- * out4[3] = system-matrix elements (events x support voxels); then it resets
- * the counters.  Errors: INVALID_ARG, CUDA. */
+ * writes out5[0] = total row-kernel time in ms, out5[1] = row-kernel
+ * launches, out5[2] = exponentials evaluated by those launches (one per path
+ * term), out5[3] = system-matrix elements (events x support voxels),
+ * out5[4] = kernels of every kind this handle launched (counted whether or
+ * not timing is enabled); then it resets the counters.
+ * Errors: INVALID_ARG, CUDA. */
 int lm_profile_enable(lm_handle* h, int enable);
-int lm_profile_read(lm_handle* h, double* out4);
+int lm_profile_read(lm_handle* h, double* out5);
 
 /* Model sizes, for work accounting: out8[0] = voxels in the support,
  * out8[1] = scatter points with rho > 0, out8[2] = emission lines,

@@ -176,16 +176,23 @@ class Model:
         lib.orc_voxel_pixels(self._h, _ptr(self.voxel_pixels, ctypes.c_int32))
 
     @classmethod
-    def from_scenario(cls, sc, rho=None, support=None) -> "Model":
+    def from_scenario(cls, sc, rho=None, support=None, f32_inputs=True) -> "Model":
+        """Model of a synthetic workload.  With ``f32_inputs`` every real
+        parameter is first rounded to float32, the precision in which the
+        CUDA library's C ABI receives them, so both sides model the same
+        scanner; the oracle's arithmetic stays FP64."""
         if rho is None:
             rho = sc.make_phantom().rho
-        return cls(n=sc.n, pixel_cm=sc.pixel_cm, n_angles=sc.n_angles, n_bins=sc.n_bins,
-                   bin_cm=sc.bin_cm, r_det_cm=sc.r_det_cm, coll_fwhm0_cm=sc.coll_fwhm0_cm,
-                   coll_fwhm_slope=sc.coll_fwhm_slope, scan_time=sc.scan_time, rho=rho,
-                   knot_keV=sc.knot_keV, mu_water_cm=sc.mu_water_cm, scatter_n=sc.scatter_n,
-                   line_keV=sc.line_keV, yields=sc.yields, fwhm_frac=sc.fwhm_frac,
-                   e_ref_keV=sc.e_ref_keV, fwhm_exponent=sc.fwhm_exponent,
-                   windows=sc.windows, support=support)
+        f = (lambda x: float(np.float32(x))) if f32_inputs else float
+        ft = lambda xs: tuple(f(x) for x in xs)  # noqa: E731
+        return cls(n=sc.n, pixel_cm=f(sc.pixel_cm), n_angles=sc.n_angles, n_bins=sc.n_bins,
+                   bin_cm=f(sc.bin_cm), r_det_cm=f(sc.r_det_cm),
+                   coll_fwhm0_cm=f(sc.coll_fwhm0_cm), coll_fwhm_slope=f(sc.coll_fwhm_slope),
+                   scan_time=f(sc.scan_time), rho=rho, knot_keV=ft(sc.knot_keV),
+                   mu_water_cm=ft(sc.mu_water_cm), scatter_n=sc.scatter_n,
+                   line_keV=ft(sc.line_keV), yields=ft(sc.yields), fwhm_frac=f(sc.fwhm_frac),
+                   e_ref_keV=f(sc.e_ref_keV), fwhm_exponent=f(sc.fwhm_exponent),
+                   windows=tuple(ft(w) for w in sc.windows), support=support)
 
     def __del__(self):
         h = getattr(self, "_h", None)

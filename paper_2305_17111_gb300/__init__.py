@@ -184,6 +184,7 @@ class Model:
         _native.check(_native.load().lm_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self) -> dict:
-        out = (ctypes.c_double * 4)()
+        out = (ctypes.c_double * 5)()
         _native.check(_native.load().lm_profile_read(self._h, out))
-        return {"ms": out[0], "launches": int(out[1]), "terms": out[2], "elements": out[3]}
+        return {"ms": out[0], "launches": int(out[1]), "terms": out[2], "elements": out[3],
+                "kernels": int(out[4])}

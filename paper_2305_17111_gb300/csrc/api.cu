@@ -446,8 +446,8 @@ int lm_profile_enable(lm_handle* h, int enable) {
     return LMMEW_OK;
 }
 
-int lm_profile_read(lm_handle* h, double* out4) {
-    if (!h || !out4) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+int lm_profile_read(lm_handle* h, double* out5) {
+    if (!h || !out5) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
     double ms = 0.0;
     for (size_t i = 0; i + 1 < h->prof_used; i += 2) {
         LMMEW_CUDA(cudaEventSynchronize(h->prof_ev[i + 1]));
@@ -455,10 +455,12 @@ int lm_profile_read(lm_handle* h, double* out4) {
         LMMEW_CUDA(cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]));
         ms += t;
     }
-    out4[0] = ms;
-    out4[1] = (double)h->prof_launches;
-    out4[2] = h->prof_terms;
-    out4[3] = h->prof_elems;
+    out5[0] = ms;
+    out5[1] = (double)h->prof_launches;
+    out5[2] = h->prof_terms;
+    out5[3] = h->prof_elems;
+    out5[4] = (double)h->launches;
+    h->launches = 0;
     h->prof_used = 0;
     h->prof_launches = 0;
     h->prof_terms = 0.0;

@@ -127,6 +127,7 @@ int launch_forward_out(lm_handle* h, const float* ypart, int64_t ypart_stride, i
     if (count <= 0) return LMMEW_OK;
     k_forward_out<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(ypart, ypart_stride, h->mc.nqt,
                                                                    count, perm + begin, out_y);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -140,6 +141,7 @@ int launch_bp_partial(lm_handle* h, const float* rows, int row_stride, const flo
     dim3 g((unsigned)((count + kBpEvents - 1) / kBpEvents), (nq + kBpVoxels - 1) / kBpVoxels);
     k_bp_partial<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt, count,
                                           perm, weight, nq, bpart, bpart_row0, llpart);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -149,6 +151,7 @@ int64_t bp_parts(int64_t count) { return (count + kBpEvents - 1) / kBpEvents; }
 int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, double* num,
                         cudaStream_t st) {
     k_voxel_reduce<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(bpart, n_parts, h->mc.nq, num);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -156,12 +159,14 @@ int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, doubl
 int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
                   const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st) {
     k_update<<<1, 1024, 0, st>>>(lam_v, num, sens, h->mc.nq, llpart, n_ll, loglik_out);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
 
 int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStream_t st) {
     k_gather<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(image, h->d_q_pix, h->mc.nq, lam_v);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -169,6 +174,7 @@ int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStre
 int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStream_t st) {
     LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * h->mc.n * h->mc.n, st));
     k_scatter_f<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(lam_v, h->d_q_pix, h->mc.nq, image);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -176,6 +182,7 @@ int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStr
 int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStream_t st) {
     LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(double) * h->mc.n * h->mc.n, st));
     k_scatter_d<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(v, h->d_q_pix, h->mc.nq, image);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }
@@ -183,6 +190,7 @@ int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStr
 int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStream_t st) {
     LMMEW_CUDA(cudaMemsetAsync(image, 0, sizeof(float) * h->mc.n * h->mc.n, st));
     k_scatter_df<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(num, h->d_q_pix, h->mc.nq, image);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }

@@ -237,6 +237,7 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
         k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ev->angle, ev->bin, ev->energy_keV, n, A,
                                                             B, d_rank_of_angle, m.n_win, w01,
                                                             w23, w45, w67, keys0, vals0, h->d_status);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
         const uint64_t kmax = (uint64_t)A * (uint64_t)B;
         int bits = 1;
@@ -244,23 +245,30 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
         uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
         for (int shift = 0; shift < bits; shift += 8) {
             k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
+            ++h->launches;
             k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+            ++h->launches;
             k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk,
                                                               kout, vout);
+            ++h->launches;
             LMMEW_CUDA(cudaGetLastError());
             std::swap(kin, kout);
             std::swap(vin, vout);
         }
         k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B,
                                                              out->perm, out->bin, out->energy);
+        ++h->launches;
         k_bounds<<<(A + 1 + 127) / 128, 128, 0, st>>>(kin, n, A, B, out->angle_start);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     } else {
         LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (A + 1), st));
     }
     k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, A, out->tile_start);
+    ++h->launches;
     k_tiles<<<(A + 127) / 128, 128, 0, st>>>(out->angle_start, out->tile_start, d_angle_of_rank, A,
                                              out->bin, out->tiles);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     // one synchronisation: validation status and the work sizes
     out->h_angle_start.resize(A + 1);

@@ -89,6 +89,7 @@ struct lm_handle {
     int64_t prof_launches = 0;
     double prof_terms = 0.0;
     double prof_elems = 0.0;
+    int64_t launches = 0;          // kernels this library launched (all kinds)
 };
 
 namespace lmmew {

@@ -334,7 +334,14 @@ int row_kernel_occupancy(lm_handle* h) {
     if (smem + 64 > (size_t)max_optin)
         return set_error(LMMEW_ERR_INVALID_ARG,
                          "lines x bins too large for the row kernel's shared-memory stages");
-    LMMEW_CUDA(cudaFuncSetAttribute(k_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the cap is per kernel, shared by every handle: allow the device maximum
+    cudaFuncAttributes fa;
+    LMMEW_CUDA(cudaFuncGetAttributes(&fa, k_row));
+    const int cap = max_optin - (int)fa.sharedSizeBytes;
+    if ((int)smem > cap)
+        return set_error(LMMEW_ERR_INVALID_ARG,
+                         "lines x bins too large for the row kernel's shared-memory stages");
+    LMMEW_CUDA(cudaFuncSetAttribute(k_row, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     int blocks = 0;
     LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_row, kRowThreads, smem));
     LMMEW_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -348,6 +355,7 @@ int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     RowParams P = make_params(h, L);
     const int grid = std::min(n_units, h->sm_count * h->row_blocks_per_sm);
     k_row<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }

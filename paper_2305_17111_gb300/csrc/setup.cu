@@ -299,6 +299,14 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             continue;
         }
         const int cell = p_cell[p];
+        if (cell == own_cell) {   // the emission voxel's own cell carries no path
+            for (int w = 0; w < m.W; ++w) {
+                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kNegHuge;
+                base[((1 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
+                base[((2 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
+            }
+            continue;
+        }
         const double xp = ((cell % m.S) + 0.5) * m.f, yp = ((cell / m.S) + 0.5) * m.f;
         const size_t k = (size_t)q * m.np + p;
         const double d = d_qp[k];
@@ -314,10 +322,8 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             const double e0 = m.line_e[w];
             const double e1 = e0 / (1.0 + (e0 / kMeC2) * (1.0 - cos_t));
             const double mu0 = mu_line[w], mu1 = mu_water(m, e1);
-            double path = 0.0;
-            if (cell != own_cell)
-                path = exp(-mu0 * gqp - mu1 * gp) * inter * mu0 * 2.0 * kPi *
-                       kn_shape(e0, cos_t) / m.kn_norm[w];
+            const double path = exp(-mu0 * gqp - mu1 * gp) * inter * mu0 * 2.0 * kPi *
+                                kn_shape(e0, cos_t) / m.kn_norm[w];
             const double sg = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
             const double wgt = m.alpha[w] * path / (sqrt(2.0 * kPi) * sg);
             base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)log2(wgt) : kNegHuge;
@@ -363,8 +369,10 @@ int subset_sensitivity(lm_handle* h, int parts, cudaStream_t st) {
             return set_error(LMMEW_ERR_OOM, "cannot allocate subset sensitivities");
         dim3 g((m.nq + 255) / 256, parts);
         k_sum_subsets<<<g, 256, 0, st>>>(h->d_sens_a, m.A, m.nq, parts, h->d_sens_sub);
+        ++h->launches;
         k_sum_all<<<(m.nq + 255) / 256, 256, 0, st>>>(h->d_sens_a, m.A, m.nq,
                                                        h->d_sens_sub + (size_t)parts * m.nq);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
         h->sens_parts = parts;
     }
@@ -398,6 +406,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     if (m.S > 0) {
         LMMEW_CUDA(cudaMalloc(&d_cell_mean.p, sizeof(double) * m.S * m.S));
         k_cell_means<<<(m.S * m.S + 255) / 256, 256>>>(rho, n, m.S, (double*)d_cell_mean.p);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
         std::vector<double> mean(m.S * m.S);
         LMMEW_CUDA(cudaMemcpy(mean.data(), d_cell_mean.p, sizeof(double) * m.S * m.S,
@@ -457,6 +466,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     // per-line constants: KN plane normaliser, energy response, mu at the line
     LMMEW_CUDA(cudaMalloc(&d_lc.p, sizeof(double) * 4 * LMMEW_MAX_LINES));
     k_line_consts<<<1, 32>>>(m, (double*)d_lc.p);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     double lc[4 * LMMEW_MAX_LINES];
     LMMEW_CUDA(cudaMemcpy(lc, d_lc.p, sizeof(lc), cudaMemcpyDeviceToHost));
@@ -480,6 +490,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         dim3 g((m.nq + m.np + 127) / 128, m.A);
         k_gamma_det<<<g, 128>>>(m, rho, dcs, h->d_q_pix, (const int*)d_p_cell.p,
                                 (double*)d_gq.p, (double*)d_gp.p);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }
     if (m.np) {
@@ -489,6 +500,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         k_gamma_qp<<<(unsigned)((k + 127) / 128), 128>>>(m, rho, h->d_q_pix,
                                                          (const int*)d_p_cell.p,
                                                          (double*)d_gqp.p, (double*)d_dqp.p);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }
 
@@ -502,6 +514,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     {
         dim3 g((m.nq + m.npc * kPC + 127) / 128, m.B, m.A);
         k_collimator<<<g, 128>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, h->d_cv, h->d_cs);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }
 
@@ -513,6 +526,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         dim3 g((m.nq + 127) / 128, m.A);
         k_primary<<<g, 128>>>(m, dcs, h->d_q_pix, (const double*)d_gq.p, mu_line, h->d_prim,
                               h->d_sens_a);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }
 
@@ -527,6 +541,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         k_scatter<<<g, 256>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
                               (const double*)d_gqp.p, (const double*)d_dqp.p,
                               (const double*)d_gp.p, mu_line, h->d_tab, h->d_sens_a);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }
     LMMEW_CUDA(cudaMalloc(&h->d_status, sizeof(int)));

@@ -158,6 +158,30 @@ int lm_sensitivity(lm_handle* h, int subset, double* out, lm_stream stream);
 int lm_forward(lm_handle* h, const lm_events* events, const float* image, float* out_y,
                lm_stream stream);
 
+/* Forward projection that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * while they run -- a process whose device memory is already reserved by
+ * another allocator (a framework's caching allocator, a fixed budget), or a
+ * steady-state loop in which the allocation and the device synchronisation
+ * that cudaMalloc/cudaFree imply are not allowed.  It computes exactly what
+ * lm_forward computes (same kernels, same order, bit-identical results), with
+ * all of its scratch in one 16 MiB array in the library's static device
+ * memory, which every GPU that loads the library holds until the process
+ * exits.  The call rejects, with LMMEW_ERR_INVALID_ARG and a message, event
+ * counts whose scratch would exceed 16 MiB (about 26 + 4*ceil(nq/32) bytes
+ * per event, nq = support voxels: some 180 000 events for a 32x32 model of
+ * 484 voxels, 36 000 for a 128x128 model of 3 464); use lm_forward for
+ * those.  Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  Every call shares the one array and
+ * it keeps the last call's contents (each call writes every word it reads
+ * before reading it): calls that overlap on the GPU -- two streams, two host
+ * threads, or a call queued before an earlier one finished on another
+ * stream -- race, so serialise them.  Arguments and errors as lm_forward;
+ * the caller still provides events, image and output. */
+int lm_forward_noalloc(lm_handle* h, const lm_events* events, const float* image, float* out_y,
+                       lm_stream stream);
+
 /* Back projection out[q] = sum_j weight_j a_j[q].  weight: DEVICE
  * float[events->n] in the caller's order; out_image: DEVICE float[n*n],
  * zero outside the support.  Errors: as lm_forward. */

@@ -153,6 +153,16 @@ class Model:
                                                 _stream(stream)))
         return out
 
+    def forward_noalloc(self, events: DeviceEvents, image, out, stream=None):
+        """lm_forward_noalloc: same result as forward(), no device allocation
+        inside the call (``image`` and ``out`` are caller-owned CUDA tensors)."""
+        ev = events.struct()
+        _native.check(_native.load().lm_forward_noalloc(self._h, ctypes.byref(ev),
+                                                        ctypes.c_void_p(image.data_ptr()),
+                                                        ctypes.c_void_p(out.data_ptr()),
+                                                        _stream(stream)))
+        return out
+
     def backproject(self, events: DeviceEvents, weight, out=None, stream=None):
         torch = _torch()
         weight = weight.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)

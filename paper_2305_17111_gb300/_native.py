@@ -69,6 +69,8 @@ SYMBOLS = {
                                       ctypes.c_void_p]),
     "lm_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events), ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_forward_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events),
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lm_backproject": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "lm_osem": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events), ctypes.c_int,

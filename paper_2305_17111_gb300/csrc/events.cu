@@ -292,4 +292,87 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
     return LMMEW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Variant for callers that cannot allocate: every buffer comes from a
+// caller-provided region, no host container is built, and the host reads
+// back only three integers.  Angles keep their natural order (one subset).
+namespace {
+__global__ void k_identity(int* a, int* b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i] = i; b[i] = i; }
+}
+}  // namespace
+
+size_t sort_fixed_bytes(int64_t n, int A) { return sort_scratch_bytes(n, A); }
+
+int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
+                      cudaStream_t st) {
+    const ModelConst& m = h->mc;
+    const int64_t n = ev->n;
+    const int A = m.A, B = m.B;
+    uint32_t* keys0 = bump<uint32_t>(arena, n);
+    uint32_t* keys1 = bump<uint32_t>(arena, n);
+    uint32_t* vals0 = bump<uint32_t>(arena, n);
+    uint32_t* vals1 = bump<uint32_t>(arena, n);
+    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+    uint32_t* hist = bump<uint32_t>(arena, 256 * (nblk > 0 ? nblk : 1));
+    out->perm = bump<uint32_t>(arena, n);
+    out->bin = bump<uint16_t>(arena, n);
+    out->energy = bump<float>(arena, n);
+    int* angle_start = bump<int>(arena, A + 1);
+    int* tile_start = bump<int>(arena, A + 1);
+    int* d_angle_of_rank = bump<int>(arena, A);
+    int* d_rank_of_angle = bump<int>(arena, A);
+    out->tiles = bump<Tile>(arena, n / kET + A + 1);
+
+    k_identity<<<(A + 255) / 256, 256, 0, st>>>(d_rank_of_angle, d_angle_of_rank, A);
+    float w[8][2] = {};
+    for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        ev->angle, ev->bin, ev->energy_keV, n, A, B, d_rank_of_angle, m.n_win,
+        make_float4(w[0][0], w[0][1], w[1][0], w[1][1]), make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
+        make_float4(w[4][0], w[4][1], w[5][0], w[5][1]), make_float4(w[6][0], w[6][1], w[7][0], w[7][1]),
+        keys0, vals0, h->d_status);
+    LMMEW_CUDA(cudaGetLastError());
+    const uint64_t kmax = (uint64_t)A * (uint64_t)B;
+    int bits = 1;
+    while (bits < 32 && (kmax >> bits) != 0) ++bits;
+    uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
+        k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+        k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk, kout,
+                                                          vout);
+        LMMEW_CUDA(cudaGetLastError());
+        uint32_t* t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+    }
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B, out->perm,
+                                                         out->bin, out->energy);
+    k_bounds<<<(A + 1 + 127) / 128, 128, 0, st>>>(kin, n, A, B, angle_start);
+    k_tile_scan<<<1, 1024, 0, st>>>(angle_start, A, tile_start);
+    k_tiles<<<(A + 127) / 128, 128, 0, st>>>(angle_start, tile_start, d_angle_of_rank, A, out->bin,
+                                             out->tiles);
+    LMMEW_CUDA(cudaGetLastError());
+    h->launches += 6 + 3 * ((bits + 7) / 8);
+    int host3[3] = {0, 0, 0};   // tiles, valid events, status
+    LMMEW_CUDA(cudaMemcpyAsync(&host3[0], tile_start + A, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&host3[1], angle_start + A, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&host3[2], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    if (host3[2] != 0) {
+        LMMEW_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+        LMMEW_CUDA(cudaStreamSynchronize(st));
+    }
+    if (host3[2] & kStatusTimeout)
+        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
+    if (host3[2] & kStatusOutOfRange)
+        return set_error(LMMEW_ERR_OUT_OF_RANGE,
+                         "an event has an angle or bin outside the model or an energy outside "
+                         "every window");
+    out->n_tiles = host3[0];
+    out->n_valid = host3[1];
+    return LMMEW_OK;
+}
+
 }  // namespace lmmew

@@ -125,6 +125,19 @@ size_t sort_scratch_bytes(int64_t n, int A);
 int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* out,
                 char*& arena, cudaStream_t st);
 
+// events.cu: the same sort on a caller-provided region, no host containers
+struct SortedFixed {
+    uint16_t* bin = nullptr;
+    float* energy = nullptr;
+    uint32_t* perm = nullptr;
+    Tile* tiles = nullptr;
+    int n_tiles = 0;
+    int64_t n_valid = 0;
+};
+size_t sort_fixed_bytes(int64_t n, int A);
+int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
+                      cudaStream_t st);
+
 // row.cu: fused system-matrix row kernel
 struct RowLaunch {
     const Tile* tiles;

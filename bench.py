@@ -43,6 +43,9 @@ def parse_args():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=None,
+                    help="override the workload's event count (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -200,6 +203,60 @@ def run_reference(args, rank, world):
     return 0
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The slowest rank's time (or any value): MAX all-reduce when distributed."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(units_per_rank_step, steps, world, ms_max):
+    """Units all ranks processed / the slowest rank's time (replicas: every
+    rank processes the same number of units per step)."""
+    return world * units_per_rank_step * steps / (ms_max / 1e3)
+
+
+def run_e2e(model, ev, img, sc, n_sub, it, steps, stream, barrier, dist):
+    """Same steps through the same call with host buffers: each step copies
+    its events from pinned host memory and reads the image back."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    h_ang = torch.from_numpy(np.asarray(ev.angle, np.uint16).view(np.int16).copy()).pin_memory()
+    h_bin = torch.from_numpy(np.asarray(ev.bin, np.uint16).view(np.int16).copy()).pin_memory()
+    h_en = torch.from_numpy(np.asarray(ev.energy, np.float32).copy()).pin_memory()
+    h_img = torch.empty(sc.n * sc.n, dtype=torch.float32).pin_memory()
+    d_ang = torch.empty_like(h_ang, device="cuda")
+    d_bin = torch.empty_like(h_bin, device="cuda")
+    d_en = torch.empty_like(h_en, device="cuda")
+    dev2 = lm.DeviceEvents(d_ang, d_bin, d_en)
+    img2 = img.clone()
+    barrier()
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(steps):
+        d_ang.copy_(h_ang, non_blocking=True)
+        d_bin.copy_(h_bin, non_blocking=True)
+        d_en.copy_(h_en, non_blocking=True)
+        model.osem(dev2, img2, n_sub, it + 1, start_iter=it)
+        h_img.copy_(img2, non_blocking=True)
+        it += 1
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1), dist, "cuda")
+    h2d = h_ang.numel() * 2 + h_bin.numel() * 2 + h_en.numel() * 4
+    d2h = h_img.numel() * 4
+
+    return ms_e2e, h2d, d2h, it
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, local_rank, world):
     import numpy as np
@@ -215,6 +272,8 @@ def run_gpu(args, rank, local_rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     sc = preset(args.workload)
+    if args.events:
+        sc = sc.with_(n_events=args.events)
     ph = sc.make_phantom()
     # every rank reconstructs its own noise realisation (seed + rank)
     ev = simulate_cached(sc, seed=sc.seed + rank)
@@ -254,48 +313,15 @@ def run_gpu(args, rank, local_rank, world):
     ms = e0.elapsed_time(e1)
     prof = model.profile_read()
     model.profile_enable(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     elems_step = J * nq
-    value = world * elems_step * args.steps / (ms / 1e3)
+    value = whole_job_throughput(elems_step, args.steps, world, ms)
 
-    # end to end through the same call with host buffers: copy the step's
-    # events from pinned host memory, run the iteration, read the image back
-    h_ang = torch.from_numpy(np.asarray(ev.angle, np.uint16).view(np.int16).copy()).pin_memory()
-    h_bin = torch.from_numpy(np.asarray(ev.bin, np.uint16).view(np.int16).copy()).pin_memory()
-    h_en = torch.from_numpy(np.asarray(ev.energy, np.float32).copy()).pin_memory()
-    h_img = torch.empty(sc.n * sc.n, dtype=torch.float32).pin_memory()
-    d_ang = torch.empty_like(h_ang, device="cuda")
-    d_bin = torch.empty_like(h_bin, device="cuda")
-    d_en = torch.empty_like(h_en, device="cuda")
-    dev2 = lm.DeviceEvents(d_ang, d_bin, d_en)
-    img2 = img.clone()
-    barrier()
-    torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(args.steps):
-        d_ang.copy_(h_ang, non_blocking=True)
-        d_bin.copy_(h_bin, non_blocking=True)
-        d_en.copy_(h_en, non_blocking=True)
-        model.osem(dev2, img2, n_sub, it + 1, start_iter=it)
-        h_img.copy_(img2, non_blocking=True)
-        it += 1
-    f1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = f0.elapsed_time(f1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    h2d = h_ang.numel() * 2 + h_bin.numel() * 2 + h_en.numel() * 4
-    d2h = h_img.numel() * 4
-
+    ms_e2e, h2d, d2h = None, 0, 0
+    if not args.no_e2e:
+        ms_e2e, h2d, d2h, it = run_e2e(model, ev, img, sc, n_sub, it, args.steps, stream, barrier,
+                                       dist)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -319,8 +345,8 @@ def run_gpu(args, rank, local_rank, world):
         "terms_per_s": prof["terms"] / (ms / 1e3) if ms > 0 else None,
         "setup_ms": model.setup_ms,
         "clocks": clk,
-        "e2e": {"value": world * elems_step * args.steps / (ms_e2e / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": whole_job_throughput(elems_step, args.steps, world, ms_e2e), "unit": UNIT,
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h} if ms_e2e else None),
         "gpu_launches": int(prof["kernels"]),
         "roofline": {"bound": "alu", "kernel": "k_row (fused row + forward)",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tex2/s",

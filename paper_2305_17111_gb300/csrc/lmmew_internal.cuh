@@ -64,7 +64,7 @@ struct lm_handle {
     int n_subsets_default;
     // geometry on the device
     int* d_q_pix = nullptr;        // [nq] pixel index of each support voxel
-    float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  lh, nk, E'
+    float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  lh, nk, -E'
     float* d_cs = nullptr;         // [A][npc][B][kCPad] collimator prob. of scatter points
     float* d_cv = nullptr;         // [A][B][nq] collimator prob. of voxels
     float* d_prim = nullptr;       // [A][W][nq] alpha_w exp(-mu_w gamma_det)

@@ -13,7 +13,9 @@
 // voxels; each lane owns 4 events, so a table entry read from shared memory
 // is a broadcast that feeds 4 events, and the collimator value of an
 // (event, point) pair feeds every voxel and line.  Per scatter term:
-//   d = E_hat - E'; arg = nk d^2 + lh; term = ex2(arg)   (MUFU)
+//   d = E_hat - E'; arg = (nk d) d + lh; term = ex2(arg)   (MUFU)
+// with the FP32 arithmetic on packed pairs of scatter points (f32x2), so one
+// instruction covers two terms.
 // with lh = log2(alpha s / (sqrt(2 pi) sigma_E(E'))) and nk = -log2(e) /
 // (2 sigma_E(E')^2) precomputed in FP64.  Sums are hierarchical: per stage,
 // per unit, then across warps in a fixed order, so results are
@@ -81,7 +83,7 @@ __device__ __forceinline__ float fast_ex2(float x) {
 }
 
 struct RowParams {
-    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]
+    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: lh, nk, -E'
     const float* cs;      // [A][npc][B][kCPad]
     const float* cv;      // [A][B][nq]
     const float* prim;    // [A][W][nq]
@@ -102,13 +104,49 @@ struct RowParams {
     LineConst lc;
 };
 
+// Packed pairs of FP32 values (Blackwell's f32x2 arithmetic).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// ex2 of both halves of the exponent pair lh + nk d^2 with d = e_hat - E'
+// (the table holds -E'), for one event and two scatter points.
+__device__ __forceinline__ f32x2 term2(f32x2 eh2, f32x2 neg_ep, f32x2 nk, f32x2 lh) {
+    const f32x2 d = add2(eh2, neg_ep);
+    const f32x2 t = mul2(nk, d);
+    const f32x2 a = fma2(t, d, lh);
+    float a0, a1;
+    upk(a, a0, a1);
+    return pk(fast_ex2(a0), fast_ex2(a1));
+}
+
+template <int W>
 __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int W = P.W;
     const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
     if (tid == 0) {
         mbar_init(bar0, 1);
@@ -120,7 +158,8 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 
     const int n_tiles = P.tile_end - P.tile_begin;
     const int n_units = n_tiles * P.nqt;
-    const size_t tab_block = (size_t)3 * W * kQT * kPC;   // floats per (a, qt, pc)
+    constexpr int kTabBlock = 3 * W * kQT * kPC;          // floats per (a, qt, pc)
+    constexpr uint32_t kTabBytes = kTabBlock * 4u;
     uint32_t g = 0;                                       // pipeline stages issued so far
 
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
@@ -130,30 +169,33 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         const uint32_t c_bytes = (uint32_t)(b_hi - b_lo + 1) * kCPad * 4u;
 
         float eh[4];
+        f32x2 eh2[4];
         int bo[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int e = k * 32 + lane;
             const bool v = e < T.count;
             eh[k] = v ? P.ev_e[T.begin + e] : 0.f;
+            eh2[k] = pk(eh[k], eh[k]);
             bo[k] = v ? (int)P.ev_bin[T.begin + e] - b_lo : 0;
         }
-        float acc[4][4];
+        // two partial sums per (event, voxel): even and odd scatter points
+        f32x2 acc2[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[k][i] = 0.f;
+            for (int i = 0; i < 4; ++i) acc2[k][i] = 0ull;
 
         if (P.npc > 0) {
-            const float* tab_u = P.tab + ((size_t)T.a * P.nqt + qt) * P.npc * tab_block;
+            const float* tab_u = P.tab + ((size_t)T.a * P.nqt + qt) * P.npc * (size_t)kTabBlock;
             const float* cs_u = P.cs + ((size_t)T.a * P.npc * P.B + b_lo) * kCPad;
             auto issue = [&](int pc, uint32_t gs) {
                 const int buf = gs & 1;
                 const uint32_t bar = buf ? bar1 : bar0;
                 const uint32_t dst = smem_addr(smem + buf * P.stage_bytes);
-                mbar_expect_tx(bar, P.tab_stage_bytes + c_bytes);
-                bulk_g2s(dst, tab_u + (size_t)pc * tab_block, P.tab_stage_bytes, bar);
-                bulk_g2s(dst + P.tab_stage_bytes, cs_u + (size_t)pc * P.B * kCPad, c_bytes, bar);
+                mbar_expect_tx(bar, kTabBytes + c_bytes);
+                bulk_g2s(dst, tab_u + (size_t)pc * kTabBlock, kTabBytes, bar);
+                bulk_g2s(dst + kTabBytes, cs_u + (size_t)pc * P.B * kCPad, c_bytes, bar);
             };
             if (tid == 0) issue(0, g);
             for (int pc = 0; pc < P.npc; ++pc, ++g) {
@@ -163,61 +205,48 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 if (!ok) s_abort = 1;
                 if (ok) {
                     const unsigned char* sb = smem + buf * P.stage_bytes;
-                    const float* tb = reinterpret_cast<const float*>(sb);
-                    const float* cr = reinterpret_cast<const float*>(sb + P.tab_stage_bytes);
-                    float sacc[4][4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) sacc[k][i] = 0.f;
+                    const float* tb = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
+                    const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
 #pragma unroll 1
                     for (int pq = 0; pq < kPC / 4; ++pq) {
-                        float4 c4[4];
+                        f32x2 cA[4], cB[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            c4[k] = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
+                        for (int k = 0; k < 4; ++k) {
+                            const float4 c4 =
+                                *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
+                            cA[k] = pk(c4.x, c4.y);
+                            cB[k] = pk(c4.z, c4.w);
+                        }
 #pragma unroll
                         for (int qi = 0; qi < 4; ++qi) {
-                            const int ql = warp * 4 + qi;
-                            float in[4][4];
+                            const float* tq = tb + qi * kPC + pq * 4;
+                            f32x2 inA[4], inB[4];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                                for (int i = 0; i < 4; ++i) in[k][i] = 0.f;
-#pragma unroll 1
                             for (int w = 0; w < W; ++w) {
                                 const float4 lh = *reinterpret_cast<const float4*>(
-                                    tb + ((0 * W + w) * kQT + ql) * kPC + pq * 4);
+                                    tq + (0 * W + w) * kQT * kPC);
                                 const float4 nk = *reinterpret_cast<const float4*>(
-                                    tb + ((1 * W + w) * kQT + ql) * kPC + pq * 4);
-                                const float4 ep = *reinterpret_cast<const float4*>(
-                                    tb + ((2 * W + w) * kQT + ql) * kPC + pq * 4);
-                                const float lhv[4] = {lh.x, lh.y, lh.z, lh.w};
-                                const float nkv[4] = {nk.x, nk.y, nk.z, nk.w};
-                                const float epv[4] = {ep.x, ep.y, ep.z, ep.w};
+                                    tq + (1 * W + w) * kQT * kPC);
+                                const float4 ne = *reinterpret_cast<const float4*>(
+                                    tq + (2 * W + w) * kQT * kPC);
+                                const f32x2 lhA = pk(lh.x, lh.y), lhB = pk(lh.z, lh.w);
+                                const f32x2 nkA = pk(nk.x, nk.y), nkB = pk(nk.z, nk.w);
+                                const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
 #pragma unroll
-                                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                                    for (int i = 0; i < 4; ++i) {
-                                        const float d = eh[k] - epv[i];
-                                        in[k][i] += fast_ex2(fmaf(nkv[i], d * d, lhv[i]));
-                                    }
+                                for (int k = 0; k < 4; ++k) {
+                                    const f32x2 tA = term2(eh2[k], neA, nkA, lhA);
+                                    const f32x2 tB = term2(eh2[k], neB, nkB, lhB);
+                                    inA[k] = (w == 0) ? tA : add2(inA[k], tA);
+                                    inB[k] = (w == 0) ? tB : add2(inB[k], tB);
+                                }
                             }
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                float s = sacc[k][qi];
-                                s = fmaf(c4[k].x, in[k][0], s);
-                                s = fmaf(c4[k].y, in[k][1], s);
-                                s = fmaf(c4[k].z, in[k][2], s);
-                                s = fmaf(c4[k].w, in[k][3], s);
-                                sacc[k][qi] = s;
+                                acc2[k][qi] = fma2(cA[k], inA[k], acc2[k][qi]);
+                                acc2[k][qi] = fma2(cB[k], inB[k], acc2[k][qi]);
                             }
                         }
                     }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) acc[k][i] += sacc[k][i];
                 }
                 __syncthreads();
                 if (s_abort) {
@@ -233,6 +262,16 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             }
         }
 
+        float acc[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float lo, hi;
+                upk(acc2[k][i], lo, hi);
+                acc[k][i] = lo + hi;
+            }
+
         // unscattered paths
         {
             const int b_base = T.a * P.B + b_lo;
@@ -245,12 +284,10 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                         if (k * 32 + lane < T.count) {
                             float s = 0.f;
 #pragma unroll
-                            for (int w = 0; w < LMMEW_MAX_LINES; ++w) {
-                                if (w < W) {
-                                    const float d = eh[k] - P.lc.e[w];
-                                    const float gw = P.lc.norm[w] * fast_ex2(P.lc.nk[w] * d * d);
-                                    s = fmaf(P.prim[((size_t)T.a * W + w) * P.nq + q], gw, s);
-                                }
+                            for (int w = 0; w < W; ++w) {
+                                const float d = eh[k] - P.lc.e[w];
+                                const float gw = P.lc.norm[w] * fast_ex2(P.lc.nk[w] * d * d);
+                                s = fmaf(P.prim[((size_t)T.a * W + w) * P.nq + q], gw, s);
                             }
                             acc[k][qi] = fmaf(P.cv[((size_t)(b_base + bo[k])) * P.nq + q], s, acc[k][qi]);
                         }
@@ -282,6 +319,20 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
         }
         __syncthreads();
+    }
+}
+
+typedef void (*RowKernel)(const RowParams);
+RowKernel row_kernel_for(int W) {
+    switch (W) {
+        case 1: return k_row<1>;
+        case 2: return k_row<2>;
+        case 3: return k_row<3>;
+        case 4: return k_row<4>;
+        case 5: return k_row<5>;
+        case 6: return k_row<6>;
+        case 7: return k_row<7>;
+        default: return k_row<8>;
     }
 }
 
@@ -335,15 +386,16 @@ int row_kernel_occupancy(lm_handle* h) {
         return set_error(LMMEW_ERR_INVALID_ARG,
                          "lines x bins too large for the row kernel's shared-memory stages");
     // the cap is per kernel, shared by every handle: allow the device maximum
+    RowKernel kern = row_kernel_for(h->mc.W);
     cudaFuncAttributes fa;
-    LMMEW_CUDA(cudaFuncGetAttributes(&fa, k_row));
+    LMMEW_CUDA(cudaFuncGetAttributes(&fa, kern));
     const int cap = max_optin - (int)fa.sharedSizeBytes;
     if ((int)smem > cap)
         return set_error(LMMEW_ERR_INVALID_ARG,
                          "lines x bins too large for the row kernel's shared-memory stages");
-    LMMEW_CUDA(cudaFuncSetAttribute(k_row, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    LMMEW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     int blocks = 0;
-    LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_row, kRowThreads, smem));
+    LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kRowThreads, smem));
     LMMEW_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
     h->row_blocks_per_sm = blocks > 0 ? blocks : 1;
     return LMMEW_OK;
@@ -354,7 +406,7 @@ int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     if (n_units <= 0) return LMMEW_OK;
     RowParams P = make_params(h, L);
     const int grid = std::min(n_units, h->sm_count * h->row_blocks_per_sm);
-    k_row<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    row_kernel_for(h->mc.W)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -266,7 +266,7 @@ __global__ void k_primary(ModelConst m, const double* cs_a, const int* q_pix, co
 
 // Single-scatter paths.  One warp per (angle, voxel), lanes over scatter
 // points.  Writes the FP32 hot-kernel tables
-//   lh = log2(alpha_w s(P) / (sqrt(2 pi) sigma_E(E'))), nk = -log2(e)/(2 sigma_E(E')^2), E'
+//   lh = log2(alpha_w s(P) / (sqrt(2 pi) sigma_E(E'))), nk = -log2(e)/(2 sigma_E(E')^2), -E'
 // and adds sum_w alpha_w sum_p s(P) Prob(detector) Prob(window | E') to the
 // per-angle sensitivity.
 __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_a,
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             const double wgt = m.alpha[w] * path / (sqrt(2.0 * kPi) * sg);
             base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)log2(wgt) : kNegHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = (float)(-kLog2e / (2.0 * sg * sg));
-            base[((2 * m.W + w) * kQT + ql) * kPC + lane] = (float)e1;
+            base[((2 * m.W + w) * kQT + ql) * kPC + lane] = (float)(-e1);
             if (path > 0.0) sens += m.alpha[w] * path * on_det * window_mass(m, e1);
         }
     }

@@ -127,6 +127,12 @@ def measured_peaks():
         return None
 
 
+# DRAM bytes (read + write) per launch of the current k_row revision on this
+# workload, from the one-pass ncu capture summarised in
+# profiles/k_row_lmmew64.md.  Set to None whenever k_row changes until the
+# counters are taken again.
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 0.62e9}
+
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.
 EX2_PER_SM_PER_CLK = 32
@@ -350,7 +356,9 @@ def run_gpu(args, rank, local_rank, world):
         "gpu_launches": int(prof["kernels"]),
         "roofline": {"bound": "alu", "kernel": "k_row (fused row + forward)",
                      "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tex2/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": (ROW_TRAFFIC_BYTES_PER_LAUNCH.get(sc.name)
+                                 if not args.events else None),
                      "peak_basis": f"{sm_count} SMs x {EX2_PER_SM_PER_CLK} ex2/clk x "
                                    f"{sm_max:.0f} MHz",
                      "row_kernel_share": prof["ms"] / ms if ms > 0 else None},

@@ -38,7 +38,7 @@ UNIT = "elem/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -131,7 +131,7 @@ def measured_peaks():
 # workload, from the one-pass ncu capture summarised in
 # profiles/k_row_lmmew64.md.  Set to None whenever k_row changes until the
 # counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 0.62e9}
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.
@@ -349,6 +349,8 @@ def run_gpu(args, rank, local_rank, world):
                        parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "s_per_osem_iter": ms_per_step / 1e3,
         "terms_per_s": prof["terms"] / (ms / 1e3) if ms > 0 else None,
+        "terms_evaluated_per_step": prof["terms"] / args.steps,
+        "terms_dense_per_step": float(model.terms_per_event) * J,
         "setup_ms": model.setup_ms,
         "clocks": clk,
         "e2e": ({"value": whole_job_throughput(elems_step, args.steps, world, ms_e2e), "unit": UNIT,

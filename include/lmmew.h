@@ -216,8 +216,10 @@ const char* lm_last_error(void);
  * recorded on the caller's stream around every launch of the fused
  * system-matrix row kernel.  lm_profile_read synchronises those events and
  * writes out5[0] = total row-kernel time in ms, out5[1] = row-kernel
- * launches, out5[2] = exponentials evaluated by those launches (one per path
- * term), out5[3] = system-matrix elements (events x support voxels),
+ * launches, out5[2] = exponentials those launches evaluated for real
+ * (event, voxel) pairs -- one per path term whose collimator factor is not
+ * an exact zero -- counted on the device, out5[3] = system-matrix elements
+ * (events x support voxels),
  * out5[4] = kernels of every kind this handle launched (counted whether or
  * not timing is enabled); then it resets the counters.
  * Errors: INVALID_ARG, CUDA. */

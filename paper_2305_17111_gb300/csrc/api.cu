@@ -104,7 +104,7 @@ int launch_row_profiled(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     LMMEW_CUDA(cudaEventRecord(e1, st));
     h->prof_used += 2;
     h->prof_launches += 1;
-    h->prof_terms += (double)L.n_events * (double)h->terms_per_event;
+    h->prof_terms_dense += (double)L.n_events * (double)h->terms_per_event;
     h->prof_elems += (double)L.n_events * (double)h->mc.nq;
     return LMMEW_OK;
 }
@@ -195,6 +195,10 @@ int lm_create(const lm_geometry* g, const lm_attenuation* at, const lm_lines* ln
     }
     h->n_subsets_default = n_subsets;
     int rc = build_tables(h, at->rho, support);
+    if (rc == LMMEW_OK &&
+        (cudaMalloc(&h->d_term_counter, sizeof(unsigned long long)) != cudaSuccess ||
+         cudaMemset(h->d_term_counter, 0, sizeof(unsigned long long)) != cudaSuccess))
+        rc = set_error(LMMEW_ERR_OOM, "cannot allocate the term counter");
     if (rc == LMMEW_OK) rc = row_kernel_occupancy(h);
     if (rc != LMMEW_OK) {
         std::string keep = g_err;
@@ -231,6 +235,8 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_q_pix);
     cudaFree(h->d_tab);
     cudaFree(h->d_cs);
+    cudaFree(h->d_crange);
+    cudaFree(h->d_term_counter);
     cudaFree(h->d_cv);
     cudaFree(h->d_prim);
     cudaFree(h->d_sens_a);
@@ -455,15 +461,21 @@ int lm_profile_read(lm_handle* h, double* out5) {
         LMMEW_CUDA(cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]));
         ms += t;
     }
+    unsigned long long evaluated = 0;
+    if (h->d_term_counter) {
+        LMMEW_CUDA(cudaMemcpy(&evaluated, h->d_term_counter, sizeof(evaluated),
+                              cudaMemcpyDeviceToHost));
+        LMMEW_CUDA(cudaMemset(h->d_term_counter, 0, sizeof(evaluated)));
+    }
     out5[0] = ms;
     out5[1] = (double)h->prof_launches;
-    out5[2] = h->prof_terms;
+    out5[2] = (double)evaluated;
     out5[3] = h->prof_elems;
     out5[4] = (double)h->launches;
     h->launches = 0;
     h->prof_used = 0;
     h->prof_launches = 0;
-    h->prof_terms = 0.0;
+    h->prof_terms_dense = 0.0;
     h->prof_elems = 0.0;
     return LMMEW_OK;
 }

@@ -18,6 +18,9 @@ constexpr int kET = 128;    // events per tile (4 per lane, 32 lanes)
 constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
 constexpr int kRowThreads = 256;
 constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path
+// Collimator probabilities below this are stored as exactly 0: a term that
+// small is below FP32 resolution of any row it could enter.
+constexpr double kCollimatorFloor = 1e-20;
 
 // Status bits written by kernels into the handle's device status word.
 constexpr int kStatusOutOfRange = 1;
@@ -65,7 +68,9 @@ struct lm_handle {
     // geometry on the device
     int* d_q_pix = nullptr;        // [nq] pixel index of each support voxel
     float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  lh, nk, -E'
-    float* d_cs = nullptr;         // [A][npc][B][kCPad] collimator prob. of scatter points
+    float* d_cs = nullptr;         // [A][npc][B][kCPad] collimator prob. of scatter points,
+                                   // points in each angle's ascending-u order
+    int2* d_crange = nullptr;      // [A][B] chunks with non-zero probability: [first, last+1)
     float* d_cv = nullptr;         // [A][B][nq] collimator prob. of voxels
     float* d_prim = nullptr;       // [A][W][nq] alpha_w exp(-mu_w gamma_det)
     double* d_sens_a = nullptr;    // [A][nq] per-angle sensitivity (FP64)
@@ -87,9 +92,10 @@ struct lm_handle {
     size_t prof_used = 0;
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
-    double prof_terms = 0.0;
+    double prof_terms_dense = 0.0;   // terms of the rows without the exact-zero skip
     double prof_elems = 0.0;
     int64_t launches = 0;          // kernels this library launched (all kinds)
+    unsigned long long* d_term_counter = nullptr;   // exponentials evaluated while timing
 };
 
 namespace lmmew {

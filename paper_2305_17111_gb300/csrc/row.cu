@@ -7,7 +7,9 @@
 //
 // Work unit = (tile of <= 128 events of one angle, tile of 32 voxels).  The
 // CTA streams the angle's scatter-path tables for its 32 voxels and the
-// collimator rows of the tile's bins, 32 scatter points per stage, from
+// collimator rows of the tile's bins, 32 scatter points per stage (points in
+// the angle's ascending detector-coordinate order, only the run of chunks
+// whose collimator probability for the tile's bins is non-zero), from
 // global memory into shared memory with bulk asynchronous copies (TMA engine,
 // cp.async.bulk + mbarrier, double buffered).  Each of the 8 warps owns 4
 // voxels; each lane owns 4 events, so a table entry read from shared memory
@@ -85,6 +87,8 @@ __device__ __forceinline__ float fast_ex2(float x) {
 struct RowParams {
     const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: lh, nk, -E'
     const float* cs;      // [A][npc][B][kCPad]
+    const int2* crange;   // [A][B] point chunks with non-zero collimator probability
+    unsigned long long* term_counter;   // if set: exponentials evaluated for valid (event, voxel)
     const float* cv;      // [A][B][nq]
     const float* prim;    // [A][W][nq]
     const Tile* tiles;
@@ -98,7 +102,7 @@ struct RowParams {
     float* ypart;         // [nqt][ypart_stride] or null
     int64_t ypart_stride;
     int* status;
-    int W, B, nq, nqt, npc;
+    int W, B, nq, nqt, npc, np;
     uint32_t stage_bytes;   // bytes of one pipeline stage in shared memory
     uint32_t tab_stage_bytes;
     LineConst lc;
@@ -186,7 +190,24 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc2[k][i] = 0ull;
 
-        if (P.npc > 0) {
+        // scatter points whose collimator probability is non-zero for some bin
+        // of the tile: a contiguous run of chunks in this angle's point order;
+        // every other term is an exact zero and is not evaluated
+        int pc_lo = P.npc, pc_hi = 0;
+        for (int b = b_lo; b <= b_hi; ++b) {
+            const int2 r = P.crange[(size_t)T.a * P.B + b];
+            if (r.y > r.x) {
+                pc_lo = min(pc_lo, r.x);
+                pc_hi = max(pc_hi, r.y);
+            }
+        }
+        if (P.term_counter && tid == 0) {
+            const int nq_here = min(kQT, P.nq - qt * kQT);
+            const int np_here = pc_lo < pc_hi ? min(pc_hi * kPC, P.np) - pc_lo * kPC : 0;
+            atomicAdd(P.term_counter,
+                      (unsigned long long)T.count * nq_here * W * (unsigned long long)(np_here + 1));
+        }
+        if (pc_lo < pc_hi) {
             const float* tab_u = P.tab + ((size_t)T.a * P.nqt + qt) * P.npc * (size_t)kTabBlock;
             const float* cs_u = P.cs + ((size_t)T.a * P.npc * P.B + b_lo) * kCPad;
             auto issue = [&](int pc, uint32_t gs) {
@@ -197,9 +218,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 bulk_g2s(dst, tab_u + (size_t)pc * kTabBlock, kTabBytes, bar);
                 bulk_g2s(dst + kTabBytes, cs_u + (size_t)pc * P.B * kCPad, c_bytes, bar);
             };
-            if (tid == 0) issue(0, g);
-            for (int pc = 0; pc < P.npc; ++pc, ++g) {
-                if (tid == 0 && pc + 1 < P.npc) issue(pc + 1, g + 1);
+            if (tid == 0) issue(pc_lo, g);
+            for (int pc = pc_lo; pc < pc_hi; ++pc, ++g) {
+                if (tid == 0 && pc + 1 < pc_hi) issue(pc + 1, g + 1);
                 const int buf = g & 1;
                 const bool ok = mbar_wait_bounded(buf ? bar1 : bar0, (g >> 1) & 1);
                 if (!ok) s_abort = 1;
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                         atomicOr(P.status, kStatusTimeout);
                         // let the copies still in flight land before the CTA exits
                         mbar_wait_bounded((g & 1) ? bar1 : bar0, (g >> 1) & 1);
-                        if (pc + 1 < P.npc)
+                        if (pc + 1 < pc_hi)
                             mbar_wait_bounded(((g + 1) & 1) ? bar1 : bar0, ((g + 1) >> 1) & 1);
                     }
                     return;
@@ -343,6 +364,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L) {
     RowParams P;
     P.tab = h->d_tab;
     P.cs = h->d_cs;
+    P.crange = h->d_crange;
     P.cv = h->d_cv;
     P.prim = h->d_prim;
     P.tiles = L.tiles;
@@ -362,6 +384,8 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L) {
     P.nq = m.nq;
     P.nqt = m.nqt;
     P.npc = m.npc;
+    P.np = m.np;
+    P.term_counter = h->prof_on ? h->d_term_counter : nullptr;
     P.tab_stage_bytes = (uint32_t)(3 * m.W * kQT * kPC * 4);
     uint32_t stage = P.tab_stage_bytes + (uint32_t)(m.B * kCPad * 4);
     const uint32_t tr = kET * 33 * 4;   // epilogue transpose tile

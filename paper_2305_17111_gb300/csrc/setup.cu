@@ -215,9 +215,32 @@ __device__ __forceinline__ void point_cm(const ModelConst& m, bool voxel, int id
     }
 }
 
-// Collimator bin probabilities: voxels [A][B][nq], scatter points [A][npc][B][kCPad].
+// Per angle, the scatter points in ascending order of their detector
+// coordinate u (ties by index): inv[a][r] = point of rank r.  In this order
+// the points a bin can see form one contiguous run.
+__global__ void k_point_order(ModelConst m, const double* cs_a, const int* p_cell, int* inv) {
+    const int a = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.np) return;
+    const double c = cs_a[2 * a], s = cs_a[2 * a + 1];
+    double x, y;
+    point_cm(m, false, p, nullptr, p_cell, &x, &y);
+    const double u = -x * s + y * c;
+    int rank = 0;
+    for (int o = 0; o < m.np; ++o) {
+        double xo, yo;
+        point_cm(m, false, o, nullptr, p_cell, &xo, &yo);
+        const double uo = -xo * s + yo * c;
+        rank += (uo < u || (uo == u && o < p)) ? 1 : 0;
+    }
+    inv[(size_t)a * m.np + rank] = p;
+}
+
+// Collimator bin probabilities: voxels [A][B][nq], scatter points [A][npc][B][kCPad]
+// with the points of each angle in the order of k_point_order.  Probabilities
+// below kCollimatorFloor are stored as 0 (no row can resolve them in FP32).
 __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
-                             const int* p_cell, float* cv, float* csp) {
+                             const int* p_cell, const int* inv, float* cv, float* csp) {
     const int a = blockIdx.z, b = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n_p_pad = m.npc * kPC;
@@ -230,17 +253,35 @@ __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
         const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
         cv[((size_t)a * m.B + b) * m.nq + i] = (float)gauss_mass(lo, hi, u, sg);
     } else {
-        const int p = i - m.nq;
+        const int r = i - m.nq;   // rank of the point in this angle's order
         float val = 0.f;
-        if (p < m.np) {
+        if (r < m.np) {
             double x, y;
-            point_cm(m, false, p, q_pix, p_cell, &x, &y);
+            point_cm(m, false, inv[(size_t)a * m.np + r], q_pix, p_cell, &x, &y);
             const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
-            val = (float)gauss_mass(lo, hi, u, sg);
+            const double v = gauss_mass(lo, hi, u, sg);
+            val = v < kCollimatorFloor ? 0.f : (float)v;
         }
-        const int pc = p / kPC, pl = p % kPC;
+        const int pc = r / kPC, pl = r % kPC;
         csp[(((size_t)a * m.npc + pc) * m.B + b) * kCPad + pl] = val;
     }
+}
+
+// For every (angle, bin): the chunks of ordered points whose collimator
+// probability for that bin is non-zero, as [first, last + 1) (0, 0 if none).
+__global__ void k_chunk_range(ModelConst m, const float* csp, int2* range) {
+    const int a = blockIdx.y;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= m.B) return;
+    int first = -1, last = -1;
+    for (int r = 0; r < m.np; ++r) {
+        const float v = csp[(((size_t)a * m.npc + r / kPC) * m.B + b) * kCPad + (r % kPC)];
+        if (v != 0.f) {
+            if (first < 0) first = r;
+            last = r;
+        }
+    }
+    range[(size_t)a * m.B + b] = first < 0 ? make_int2(0, 0) : make_int2(first / kPC, last / kPC + 1);
 }
 
 // Unscattered paths: prim[a][w][q] = alpha_w exp(-mu_w(E_w) gamma_det) and the
@@ -273,8 +314,8 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
                                                  const int* q_pix, const int* p_cell,
                                                  const double* p_rho, const double* g_qp,
                                                  const double* d_qp, const double* g_p,
-                                                 const double* mu_line, float* tab,
-                                                 double* sens_a) {
+                                                 const double* mu_line, const int* inv,
+                                                 float* tab, double* sens_a) {
     const int a = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.x * 8 + warp;
@@ -288,9 +329,9 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
     const double half_det = 0.5 * m.B * m.bin_w;
     double sens = 0.0;
     for (int pc = 0; pc < m.npc; ++pc) {
-        const int p = pc * kPC + lane;
+        const int r = pc * kPC + lane;   // slot in this angle's point order
         float* base = tab + (((size_t)a * m.nqt + qt) * m.npc + pc) * (size_t)(3 * m.W * kQT * kPC);
-        if (p >= m.np) {
+        if (r >= m.np) {
             for (int w = 0; w < m.W; ++w) {
                 base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kNegHuge;
                 base[((1 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
@@ -298,6 +339,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             }
             continue;
         }
+        const int p = inv[(size_t)a * m.np + r];
         const int cell = p_cell[p];
         if (cell == own_cell) {   // the emission voxel's own cell carries no path
             for (int w = 0; w < m.W; ++w) {
@@ -504,6 +546,16 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         LMMEW_CUDA(cudaGetLastError());
     }
 
+    // per-angle point order
+    DevBuf d_inv;
+    LMMEW_CUDA(cudaMalloc(&d_inv.p, sizeof(int) * (size_t)m.A * np_alloc));
+    if (m.np) {
+        dim3 g((m.np + 127) / 128, m.A);
+        k_point_order<<<g, 128>>>(m, dcs, (const int*)d_p_cell.p, (int*)d_inv.p);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+    const int* inv = (const int*)d_inv.p;
+
     // collimator tables
     const size_t cv_n = (size_t)m.A * m.B * m.nq;
     const size_t cs_n = (size_t)m.A * std::max(m.npc, 1) * m.B * kCPad;
@@ -513,9 +565,19 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     LMMEW_CUDA(cudaMemset(h->d_cs, 0, sizeof(float) * cs_n));
     {
         dim3 g((m.nq + m.npc * kPC + 127) / 128, m.B, m.A);
-        k_collimator<<<g, 128>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, h->d_cv, h->d_cs);
+        k_collimator<<<g, 128>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, inv, h->d_cv,
+                                 h->d_cs);
         ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
+    }
+    if (cudaMalloc(&h->d_crange, sizeof(int2) * (size_t)m.A * m.B) != cudaSuccess)
+        return set_error(LMMEW_ERR_OOM, "cannot allocate chunk ranges");
+    if (m.np) {
+        dim3 g((m.B + 127) / 128, m.A);
+        k_chunk_range<<<g, 128>>>(m, h->d_cs, h->d_crange);
+        LMMEW_CUDA(cudaGetLastError());
+    } else {
+        LMMEW_CUDA(cudaMemset(h->d_crange, 0, sizeof(int2) * (size_t)m.A * m.B));
     }
 
     // unscattered paths + per-angle sensitivity
@@ -540,7 +602,7 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         dim3 g((m.nq + 7) / 8, m.A);
         k_scatter<<<g, 256>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
                               (const double*)d_gqp.p, (const double*)d_dqp.p,
-                              (const double*)d_gp.p, mu_line, h->d_tab, h->d_sens_a);
+                              (const double*)d_gp.p, mu_line, inv, h->d_tab, h->d_sens_a);
         ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
     }

@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--events", type=int, default=None,
                     help="override the workload's event count (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced-precision / batched forms section")
     return ap.parse_args()
 
 
@@ -263,6 +265,72 @@ def run_e2e(model, ev, img, sc, n_sub, it, steps, stream, barrier, dist):
     return ms_e2e, h2d, d2h, it
 
 
+# ------------------------------------------------------------------ chosen forms
+def roi_sums(img, masks):
+    import numpy as np
+    v = np.asarray(img, dtype=np.float64).reshape(-1)
+    return [float(v[m.reshape(-1)].sum()) for m in masks]
+
+
+def run_precision_form(workload="lmmew_128", iters=None):
+    """The reduced-precision scatter sum against the exact FP32 path on the
+    same GPU: seconds per OSEM iteration, and the deviation of forward
+    projections and lesion (ROI) activities after the stated iterations from
+    the FP32 result (the FP32 path's own parity with the FP64 oracle is
+    established by the test suite)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    ev = simulate_cached(sc)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    rng = np.random.default_rng(5)
+    lam_r = torch.from_numpy((rng.uniform(0.2, 3.0, ph.rho.size)
+                              * (ph.rho.reshape(-1) > 0)).astype(np.float32)).cuda()
+    n_it = sc.n_iters if iters is None else iters
+    out = {"workload": f"{sc.name}: {sc.n}x{sc.n}, {sc.n_angles} angles, {sc.n_bins} bins, "
+                       f"{sc.scatter_n}x{sc.scatter_n} scatter grid, {len(ev)} events, "
+                       f"{sc.n_subsets} subsets x {n_it} iterations"}
+    res = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        model.set_scatter_precision(prec)
+        y = model.forward(dev, lam_r).cpu().numpy().astype(np.float64)
+        img = lam0.clone()
+        model.osem(dev, img, sc.n_subsets, 1)             # warm-up iteration
+        img = lam0.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        model.osem(dev, img, sc.n_subsets, n_it)
+        e1.record()
+        torch.cuda.synchronize()
+        res[prec] = {"y": y, "img": img.cpu().numpy(), "s_per_iter": e0.elapsed_time(e1) / 1e3 / n_it}
+    model.set_scatter_precision("fp32")
+    ref = res["fp32"]
+    roi_ref = roi_sums(ref["img"], ph.lesion_masks)
+    out["fp32"] = {"s_per_iter": ref["s_per_iter"],
+                   "elems_per_s": len(ev) * model.nq / ref["s_per_iter"],
+                   "roi_activity": roi_ref}
+    for prec in ("fp16", "bf16"):
+        r = res[prec]
+        dev_y = np.abs(r["y"] - ref["y"]) / ref["y"]
+        roi = roi_sums(r["img"], ph.lesion_masks)
+        out[prec] = {"s_per_iter": r["s_per_iter"],
+                     "speedup_vs_fp32": ref["s_per_iter"] / r["s_per_iter"],
+                     "fwd_rel_dev_vs_fp32": {"max": float(dev_y.max()), "mean": float(dev_y.mean())},
+                     "roi_rel_dev_vs_fp32": [abs(a - b) / b for a, b in zip(roi, roi_ref)],
+                     "image_rel_l2_vs_fp32": float(np.linalg.norm(r["img"] - ref["img"])
+                                                   / np.linalg.norm(ref["img"]))}
+    model.close()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, local_rank, world):
     import numpy as np
@@ -365,6 +433,9 @@ def run_gpu(args, rank, local_rank, world):
                                    f"{sm_max:.0f} MHz",
                      "row_kernel_share": prof["ms"] / ms if ms > 0 else None},
     }
+    if world == 1 and not args.no_forms and not args.events:
+        model.close()
+        line["forms"] = {"precision": run_precision_form()}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

@@ -205,6 +205,21 @@ int lm_osem(lm_handle* h, const lm_events* events, int n_subsets, int n_iters,
             int start_iter, int start_subset, float* image, double* loglik,
             lm_stream stream);
 
+/* Arithmetic of the single-scatter sum (the reduced-precision form).
+ * LMMEW_PREC_FP32 (default): every term in FP32.  LMMEW_PREC_FP16 /
+ * LMMEW_PREC_BF16: d = E_hat - E' stays FP32, the Gaussian exponent
+ * (relative to the largest log2 path weight of each 32-voxel x 32-point block)
+ * and ex2 run on packed FP16 / BF16 pairs, the per-line sum in that type,
+ * everything is accumulated in FP32; unscattered terms, the sensitivity (FP64)
+ * and the log-likelihood (FP64) are unchanged.  Applies to the handle's later
+ * lm_forward / lm_backproject / lm_osem calls.  The first switch to a reduced
+ * precision builds its tables (8 KiB per line per block, synchronously).
+ * Errors: INVALID_ARG, NOT_IMPLEMENTED (more than 4 lines), OOM, CUDA. */
+#define LMMEW_PREC_FP32 0
+#define LMMEW_PREC_FP16 1
+#define LMMEW_PREC_BF16 2
+int lm_set_scatter_precision(lm_handle* h, int precision);
+
 /* Free every device buffer of the handle (NULL is ignored). */
 int lm_destroy(lm_handle* h);
 

@@ -190,6 +190,13 @@ class Model:
                                              _stream(stream)))
         return image
 
+    PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+    def set_scatter_precision(self, precision="fp32"):
+        """Arithmetic of the single-scatter sum: 'fp32' (exact path), 'fp16' or 'bf16'."""
+        _native.check(_native.load().lm_set_scatter_precision(self._h,
+                                                              self.PRECISIONS[precision]))
+
     def profile_enable(self, on=True):
         _native.check(_native.load().lm_profile_enable(self._h, 1 if on else 0))
 

@@ -76,6 +76,7 @@ SYMBOLS = {
     "lm_osem": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events), ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_set_scatter_precision": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lm_last_error": (ctypes.c_char_p, []),
     "lm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

@@ -236,6 +236,8 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_tab);
     cudaFree(h->d_cs);
     cudaFree(h->d_crange);
+    cudaFree(h->d_tabh);
+    cudaFree(h->d_tscale);
     cudaFree(h->d_term_counter);
     cudaFree(h->d_cv);
     cudaFree(h->d_prim);
@@ -444,6 +446,11 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
         }
     }
     return launch_scatter_image(h, lam_v, image, st);
+}
+
+int lm_set_scatter_precision(lm_handle* h, int precision) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    return set_precision(h, precision);
 }
 
 int lm_profile_enable(lm_handle* h, int enable) {

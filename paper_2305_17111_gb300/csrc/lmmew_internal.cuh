@@ -84,6 +84,12 @@ struct lm_handle {
     lmmew::Scratch scratch_work;   // row blocks and partial sums
     int sm_count = 0;
     int row_blocks_per_sm = 0;
+    int row_blocks[3] = {0, 0, 0};   // resident row-kernel CTAs per SM, per precision
+    // scatter-term precision: 0 FP32, 1 FP16, 2 BF16 (reduced-precision form)
+    int prec = 0;
+    int tabh_prec = 0;
+    float* d_tabh = nullptr;       // reduced-precision copy of d_tab
+    float* d_tscale = nullptr;     // [A][nqt][npc] block scales 2^base
     float setup_ms = 0.f;
     int64_t terms_per_event = 0;   // exponentials per event row (primary + scatter)
     // optional timing of the row kernel (CUDA events around each launch)
@@ -159,6 +165,7 @@ struct RowLaunch {
     int64_t n_events;       // events covered by the tile range (for accounting)
 };
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
+int set_precision(lm_handle* h, int prec);
 size_t row_smem_bytes(const lm_handle* h);
 int row_kernel_occupancy(lm_handle* h);
 

@@ -23,6 +23,8 @@
 // per unit, then across warps in a fixed order, so results are
 // deterministic.  Every mbarrier wait is bounded in time; a wait that runs
 // out sets the status word and the CTA stops cleanly.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,6 +88,9 @@ __device__ __forceinline__ float fast_ex2(float x) {
 
 struct RowParams {
     const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: lh, nk, -E'
+    const float* tabh;    // reduced-precision form: [A][nqt][npc]{-E' f32 [W][kQT][kPC],
+                          //   (lh - base, nk) halves [W][kQT][kPC/4][8]}
+    const float* tscale;  // [A][nqt][npc] 2^base of each block (reduced precision)
     const float* cs;      // [A][npc][B][kCPad]
     const int2* crange;   // [A][B] point chunks with non-zero collimator probability
     unsigned long long* term_counter;   // if set: exponentials evaluated for valid (event, voxel)
@@ -144,7 +149,175 @@ __device__ __forceinline__ f32x2 term2(f32x2 eh2, f32x2 neg_ep, f32x2 nk, f32x2 
     return pk(fast_ex2(a0), fast_ex2(a1));
 }
 
+// Packed half-precision arithmetic for the reduced-precision form: PREC 1 =
+// FP16 (f16x2), PREC 2 = BF16 (bf16x2).  Values travel as .b32 pairs.
+template <int PREC> struct Half;
+template <> struct Half<1> {
+    static __device__ __forceinline__ uint32_t cvt(float lo, float hi) {
+        uint32_t r;
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) {
+        uint32_t r;
+        asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t fma(uint32_t a, uint32_t b, uint32_t c) {
+        uint32_t r;
+        asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) {
+        uint32_t r;
+        asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t ex2(uint32_t a) {
+        uint32_t r;
+        asm("ex2.approx.f16x2 %0, %1;" : "=r"(r) : "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ f32x2 widen(uint32_t h) {
+        float lo, hi;
+        asm("{\n .reg .b16 l, h;\n mov.b32 {l, h}, %2;\n cvt.f32.f16 %0, l;\n cvt.f32.f16 %1, h;\n}"
+            : "=f"(lo), "=f"(hi) : "r"(h));
+        return pk(lo, hi);
+    }
+};
+template <> struct Half<2> {
+    static __device__ __forceinline__ uint32_t cvt(float lo, float hi) {
+        uint32_t r;
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) {
+        uint32_t r;
+        asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t fma(uint32_t a, uint32_t b, uint32_t c) {
+        uint32_t r;
+        asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) {
+        uint32_t r;
+        asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+        return r;
+    }
+    static __device__ __forceinline__ uint32_t ex2(uint32_t a) {
+        uint32_t r;
+        asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(r) : "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ f32x2 widen(uint32_t h) {
+        // a bf16 is the upper half of the FP32 with the same bits
+        return pk(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u));
+    }
+};
+
+// One pipeline stage of the FP32 form: 32 scatter points x 4 voxels x 4 events
+// per lane, all lines.
 template <int W>
+__device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, const int* bo,
+                                           const f32x2* eh2, f32x2 (*acc2)[4]) {
+    constexpr int kTabBytes = 3 * W * kQT * kPC * 4;
+    const float* tb = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
+    const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
+#pragma unroll 1
+    for (int pq = 0; pq < kPC / 4; ++pq) {
+        f32x2 cA[4], cB[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 c4 = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
+            cA[k] = pk(c4.x, c4.y);
+            cB[k] = pk(c4.z, c4.w);
+        }
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            const float* tq = tb + qi * kPC + pq * 4;
+            f32x2 inA[4], inB[4];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const float4 lh = *reinterpret_cast<const float4*>(tq + (0 * W + w) * kQT * kPC);
+                const float4 nk = *reinterpret_cast<const float4*>(tq + (1 * W + w) * kQT * kPC);
+                const float4 ne = *reinterpret_cast<const float4*>(tq + (2 * W + w) * kQT * kPC);
+                const f32x2 lhA = pk(lh.x, lh.y), lhB = pk(lh.z, lh.w);
+                const f32x2 nkA = pk(nk.x, nk.y), nkB = pk(nk.z, nk.w);
+                const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const f32x2 tA = term2(eh2[k], neA, nkA, lhA);
+                    const f32x2 tB = term2(eh2[k], neB, nkB, lhB);
+                    inA[k] = (w == 0) ? tA : add2(inA[k], tA);
+                    inB[k] = (w == 0) ? tB : add2(inB[k], tB);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc2[k][qi] = fma2(cA[k], inA[k], acc2[k][qi]);
+                acc2[k][qi] = fma2(cB[k], inB[k], acc2[k][qi]);
+            }
+        }
+    }
+}
+
+// One stage of the reduced-precision form.  The difference d = E_hat - E'
+// stays FP32; nk*d, the exponent (lh relative to the stage block's largest
+// log2 weight) and ex2 run on packed halves, the per-line sum in halves, the
+// accumulation in FP32 with the block's scale 2^base folded into the
+// collimator factor.
+template <int W, int PREC>
+__device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, const int* bo,
+                                           const f32x2* eh2, float scale, f32x2 (*acc2)[4]) {
+    typedef Half<PREC> H;
+    constexpr int kTabBytes = 2 * W * kQT * kPC * 4;
+    const float* ep = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
+    const uint4* ln = reinterpret_cast<const uint4*>(sb + W * kQT * kPC * 4) + warp * 4 * (kPC / 4);
+    const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
+    const f32x2 sc2 = pk(scale, scale);
+#pragma unroll 1
+    for (int pq = 0; pq < kPC / 4; ++pq) {
+        f32x2 cA[4], cB[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 c4 = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
+            cA[k] = mul2(pk(c4.x, c4.y), sc2);
+            cB[k] = mul2(pk(c4.z, c4.w), sc2);
+        }
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            uint32_t inA[4], inB[4];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const float4 ne =
+                    *reinterpret_cast<const float4*>(ep + (w * kQT) * kPC + qi * kPC + pq * 4);
+                const uint4 hl = ln[(w * kQT) * (kPC / 4) + qi * (kPC / 4) + pq];
+                const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float d0, d1;
+                    upk(add2(eh2[k], neA), d0, d1);
+                    uint32_t dh = H::cvt(d0, d1);
+                    const uint32_t eA = H::ex2(H::fma(H::mul(hl.z, dh), dh, hl.x));
+                    upk(add2(eh2[k], neB), d0, d1);
+                    dh = H::cvt(d0, d1);
+                    const uint32_t eB = H::ex2(H::fma(H::mul(hl.w, dh), dh, hl.y));
+                    inA[k] = (w == 0) ? eA : H::add(inA[k], eA);
+                    inB[k] = (w == 0) ? eB : H::add(inB[k], eB);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc2[k][qi] = fma2(cA[k], H::widen(inA[k]), acc2[k][qi]);
+                acc2[k][qi] = fma2(cB[k], H::widen(inB[k]), acc2[k][qi]);
+            }
+        }
+    }
+}
+
+template <int W, int PREC>
 __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -162,7 +335,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 
     const int n_tiles = P.tile_end - P.tile_begin;
     const int n_units = n_tiles * P.nqt;
-    constexpr int kTabBlock = 3 * W * kQT * kPC;          // floats per (a, qt, pc)
+    constexpr int kTabBlock = (PREC == 0 ? 3 : 2) * W * kQT * kPC;   // 4-byte words per (a, qt, pc)
     constexpr uint32_t kTabBytes = kTabBlock * 4u;
     uint32_t g = 0;                                       // pipeline stages issued so far
 
@@ -208,7 +381,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                       (unsigned long long)T.count * nq_here * W * (unsigned long long)(np_here + 1));
         }
         if (pc_lo < pc_hi) {
-            const float* tab_u = P.tab + ((size_t)T.a * P.nqt + qt) * P.npc * (size_t)kTabBlock;
+            const float* tab_u = (PREC == 0 ? P.tab : P.tabh) +
+                                 ((size_t)T.a * P.nqt + qt) * P.npc * (size_t)kTabBlock;
+            const float* scale_u = P.tscale + ((size_t)T.a * P.nqt + qt) * P.npc;
             const float* cs_u = P.cs + ((size_t)T.a * P.npc * P.B + b_lo) * kCPad;
             auto issue = [&](int pc, uint32_t gs) {
                 const int buf = gs & 1;
@@ -226,48 +401,10 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 if (!ok) s_abort = 1;
                 if (ok) {
                     const unsigned char* sb = smem + buf * P.stage_bytes;
-                    const float* tb = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
-                    const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
-#pragma unroll 1
-                    for (int pq = 0; pq < kPC / 4; ++pq) {
-                        f32x2 cA[4], cB[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float4 c4 =
-                                *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
-                            cA[k] = pk(c4.x, c4.y);
-                            cB[k] = pk(c4.z, c4.w);
-                        }
-#pragma unroll
-                        for (int qi = 0; qi < 4; ++qi) {
-                            const float* tq = tb + qi * kPC + pq * 4;
-                            f32x2 inA[4], inB[4];
-#pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                const float4 lh = *reinterpret_cast<const float4*>(
-                                    tq + (0 * W + w) * kQT * kPC);
-                                const float4 nk = *reinterpret_cast<const float4*>(
-                                    tq + (1 * W + w) * kQT * kPC);
-                                const float4 ne = *reinterpret_cast<const float4*>(
-                                    tq + (2 * W + w) * kQT * kPC);
-                                const f32x2 lhA = pk(lh.x, lh.y), lhB = pk(lh.z, lh.w);
-                                const f32x2 nkA = pk(nk.x, nk.y), nkB = pk(nk.z, nk.w);
-                                const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const f32x2 tA = term2(eh2[k], neA, nkA, lhA);
-                                    const f32x2 tB = term2(eh2[k], neB, nkB, lhB);
-                                    inA[k] = (w == 0) ? tA : add2(inA[k], tA);
-                                    inB[k] = (w == 0) ? tB : add2(inB[k], tB);
-                                }
-                            }
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                acc2[k][qi] = fma2(cA[k], inA[k], acc2[k][qi]);
-                                acc2[k][qi] = fma2(cB[k], inB[k], acc2[k][qi]);
-                            }
-                        }
-                    }
+                    if (PREC == 0)
+                        stage_fp32<W>(sb, warp, bo, eh2, acc2);
+                    else
+                        stage_half<W, (PREC == 0 ? 1 : PREC)>(sb, warp, bo, eh2, scale_u[pc], acc2);
                 }
                 __syncthreads();
                 if (s_abort) {
@@ -344,25 +481,45 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 }
 
 typedef void (*RowKernel)(const RowParams);
-RowKernel row_kernel_for(int W) {
+RowKernel row_kernel_for(int W, int prec) {
+    if (prec == 1) {
+        switch (W) {
+            case 1: return k_row<1, 1>;
+            case 2: return k_row<2, 1>;
+            case 3: return k_row<3, 1>;
+            case 4: return k_row<4, 1>;
+            default: return nullptr;
+        }
+    }
+    if (prec == 2) {
+        switch (W) {
+            case 1: return k_row<1, 2>;
+            case 2: return k_row<2, 2>;
+            case 3: return k_row<3, 2>;
+            case 4: return k_row<4, 2>;
+            default: return nullptr;
+        }
+    }
     switch (W) {
-        case 1: return k_row<1>;
-        case 2: return k_row<2>;
-        case 3: return k_row<3>;
-        case 4: return k_row<4>;
-        case 5: return k_row<5>;
-        case 6: return k_row<6>;
-        case 7: return k_row<7>;
-        default: return k_row<8>;
+        case 1: return k_row<1, 0>;
+        case 2: return k_row<2, 0>;
+        case 3: return k_row<3, 0>;
+        case 4: return k_row<4, 0>;
+        case 5: return k_row<5, 0>;
+        case 6: return k_row<6, 0>;
+        case 7: return k_row<7, 0>;
+        default: return k_row<8, 0>;
     }
 }
 
 }  // namespace
 
-static RowParams make_params(lm_handle* h, const RowLaunch& L) {
+static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     const ModelConst& m = h->mc;
     RowParams P;
     P.tab = h->d_tab;
+    P.tabh = h->d_tabh;
+    P.tscale = h->d_tscale;
     P.cs = h->d_cs;
     P.crange = h->d_crange;
     P.cv = h->d_cv;
@@ -386,7 +543,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L) {
     P.npc = m.npc;
     P.np = m.np;
     P.term_counter = h->prof_on ? h->d_term_counter : nullptr;
-    P.tab_stage_bytes = (uint32_t)(3 * m.W * kQT * kPC * 4);
+    P.tab_stage_bytes = (uint32_t)((prec == 0 ? 3 : 2) * m.W * kQT * kPC * 4);
     uint32_t stage = P.tab_stage_bytes + (uint32_t)(m.B * kCPad * 4);
     const uint32_t tr = kET * 33 * 4;   // epilogue transpose tile
     if (stage < tr) stage = tr;
@@ -396,43 +553,127 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L) {
 }
 
 size_t row_smem_bytes(const lm_handle* h) {
-    RowParams P = make_params(const_cast<lm_handle*>(h), RowLaunch{});
+    RowParams P = make_params(const_cast<lm_handle*>(h), RowLaunch{}, 0);
     return 2 * (size_t)P.stage_bytes;
 }
 
+// Shared-memory cap and occupancy of every precision variant for this model.
 int row_kernel_occupancy(lm_handle* h) {
-    const size_t smem = row_smem_bytes(h);
     int dev = 0;
     LMMEW_CUDA(cudaGetDevice(&dev));
     int max_optin = 0;
     LMMEW_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (smem + 64 > (size_t)max_optin)
-        return set_error(LMMEW_ERR_INVALID_ARG,
-                         "lines x bins too large for the row kernel's shared-memory stages");
-    // the cap is per kernel, shared by every handle: allow the device maximum
-    RowKernel kern = row_kernel_for(h->mc.W);
-    cudaFuncAttributes fa;
-    LMMEW_CUDA(cudaFuncGetAttributes(&fa, kern));
-    const int cap = max_optin - (int)fa.sharedSizeBytes;
-    if ((int)smem > cap)
-        return set_error(LMMEW_ERR_INVALID_ARG,
-                         "lines x bins too large for the row kernel's shared-memory stages");
-    LMMEW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    int blocks = 0;
-    LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kRowThreads, smem));
     LMMEW_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    h->row_blocks_per_sm = blocks > 0 ? blocks : 1;
+    for (int prec = 0; prec < 3; ++prec) {
+        RowKernel kern = row_kernel_for(h->mc.W, prec);
+        h->row_blocks[prec] = 0;
+        if (!kern) continue;
+        const size_t smem = 2 * (size_t)make_params(h, RowLaunch{}, prec).stage_bytes;
+        // the cap is per kernel, shared by every handle: allow the device maximum
+        cudaFuncAttributes fa;
+        LMMEW_CUDA(cudaFuncGetAttributes(&fa, kern));
+        const int cap = max_optin - (int)fa.sharedSizeBytes;
+        if ((int)smem > cap) {
+            if (prec == 0)
+                return set_error(LMMEW_ERR_INVALID_ARG,
+                                 "lines x bins too large for the row kernel's shared-memory stages");
+            continue;
+        }
+        LMMEW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        int blocks = 0;
+        LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kRowThreads, smem));
+        h->row_blocks[prec] = blocks > 0 ? blocks : 1;
+    }
+    h->row_blocks_per_sm = h->row_blocks[0];
     return LMMEW_OK;
 }
 
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
     if (n_units <= 0) return LMMEW_OK;
-    RowParams P = make_params(h, L);
-    const int grid = std::min(n_units, h->sm_count * h->row_blocks_per_sm);
-    row_kernel_for(h->mc.W)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    const int prec = h->prec;
+    RowParams P = make_params(h, L, prec);
+    const int grid = std::min(n_units, h->sm_count * h->row_blocks[prec]);
+    row_kernel_for(h->mc.W, prec)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+// Reduced-precision tables from the FP32 ones: per (angle, voxel tile, point
+// chunk) block, base = largest log2 weight; the block keeps -E' in FP32 and
+// (lh - base, nk) as packed halves.
+template <int PREC>
+__global__ void __launch_bounds__(256) k_half_tables(const float* tab, int W, float* tabh,
+                                                     float* tscale) {
+    const size_t blk = blockIdx.x;
+    const int n = W * kQT * kPC;
+    const float* src = tab + blk * (size_t)(3 * n);
+    float* dst = tabh + blk * (size_t)(2 * n);
+    __shared__ float red[256];
+    float mx = -3.0e38f;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const float v = src[i];
+        if (v > -1.0e29f) mx = fmaxf(mx, v);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const float base = red[0] > -1.0e29f ? red[0] : 0.f;
+    if (threadIdx.x == 0) tscale[blk] = red[0] > -1.0e29f ? exp2f(base) : 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) dst[i] = src[2 * n + i];   // -E'
+    uint16_t* hl = reinterpret_cast<uint16_t*>(dst + n);
+    // layout [W][kQT][kPC/4][8]: lh of 4 points, then nk of the same 4 points
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const int wq = i / kPC, p = i % kPC, pq = p / 4, pl = p % 4;
+        const float lh = src[i], nk = src[n + i];
+        const float rel = lh > -1.0e29f ? lh - base : -1.0e30f;
+        uint16_t a, b;
+        if (PREC == 1) {
+            const __half ha = __float2half_rn(rel), hb = __float2half_rn(nk);
+            a = *reinterpret_cast<const uint16_t*>(&ha);
+            b = *reinterpret_cast<const uint16_t*>(&hb);
+        } else {
+            const __nv_bfloat16 ha = __float2bfloat16_rn(rel), hb = __float2bfloat16_rn(nk);
+            a = *reinterpret_cast<const uint16_t*>(&ha);
+            b = *reinterpret_cast<const uint16_t*>(&hb);
+        }
+        hl[((size_t)wq * (kPC / 4) + pq) * 8 + pl] = a;
+        hl[((size_t)wq * (kPC / 4) + pq) * 8 + 4 + pl] = b;
+    }
+}
+
+int set_precision(lm_handle* h, int prec) {
+    if (prec < 0 || prec > 2) return set_error(LMMEW_ERR_INVALID_ARG, "unknown precision");
+    if (prec == 0 || h->mc.np == 0) {
+        h->prec = 0;
+        return LMMEW_OK;
+    }
+    if (!row_kernel_for(h->mc.W, prec) || h->row_blocks[prec] == 0)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "the reduced-precision form supports up to 4 lines");
+    if (h->tabh_prec != prec) {
+        const ModelConst& m = h->mc;
+        const size_t blocks = (size_t)m.A * m.nqt * m.npc;
+        if (!h->d_tabh) {
+            if (cudaMalloc(&h->d_tabh, blocks * 2 * m.W * kQT * kPC * 4) != cudaSuccess ||
+                cudaMalloc(&h->d_tscale, blocks * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(LMMEW_ERR_OOM, "cannot allocate reduced-precision tables");
+            }
+        }
+        if (prec == 1)
+            k_half_tables<1><<<(unsigned)blocks, 256>>>(h->d_tab, m.W, h->d_tabh, h->d_tscale);
+        else
+            k_half_tables<2><<<(unsigned)blocks, 256>>>(h->d_tab, m.W, h->d_tabh, h->d_tscale);
+        LMMEW_CUDA(cudaGetLastError());
+        LMMEW_CUDA(cudaDeviceSynchronize());
+        h->tabh_prec = prec;
+    }
+    h->prec = prec;
     return LMMEW_OK;
 }
 

@@ -220,6 +220,28 @@ int lm_osem(lm_handle* h, const lm_events* events, int n_subsets, int n_iters,
 #define LMMEW_PREC_BF16 2
 int lm_set_scatter_precision(lm_handle* h, int precision);
 
+/* Batched LM-OSEM over n_real independent realisations (noise realisations
+ * of the same object: same handle, own events, own image).  Each
+ * sub-iteration runs as one persistent row-kernel launch over the events of
+ * every realisation (plus per-realisation back projection, FP64 log-likelihood
+ * and update), and the whole n_iters x n_subsets sequence is captured once as
+ * a CUDA graph and replayed on the caller's stream.  Before the capture an
+ * autotuner times the row kernel's launch shapes (work-unit order x CTAs per
+ * SM) on the batch's first row block and keeps the fastest; it re-tunes when
+ * the batch shape (events, realisations, subsets) changes.
+ * events: HOST array of n_real lm_events (device pointers inside); images:
+ * DEVICE float[n_real][n*n], lambda^0 in, lambda out; loglik: NULL or DEVICE
+ * double[n_real][n_iters*n_subsets].  Every realisation's result equals
+ * lm_osem's on its own events bit for bit.  Errors: as lm_osem. */
+int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subsets, int n_iters,
+                  float* images, double* loglik, lm_stream stream);
+
+/* The row-kernel launch shape chosen by the last batch autotune: out4[0] =
+ * work-unit order (0 tile-major, 1 voxel-tile-major), out4[1] = CTAs per SM,
+ * out4[2] = 1 if tuned, out4[3] = the chosen shape's time on the tuning block
+ * (ms).  Not part of the paper's method.  Errors: INVALID_ARG. */
+int lm_batch_tuning(const lm_handle* h, double* out4);
+
 /* Free every device buffer of the handle (NULL is ignored). */
 int lm_destroy(lm_handle* h);
 

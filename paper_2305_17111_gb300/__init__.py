@@ -190,6 +190,27 @@ class Model:
                                              _stream(stream)))
         return image
 
+    def osem_batch(self, events_list, images, n_subsets, n_iters, loglik=None, stream=None):
+        """Batched LM-OSEM: ``images`` is a contiguous float32 CUDA tensor
+        [R, n*n] updated in place; ``events_list`` holds R DeviceEvents."""
+        torch = _torch()
+        R = len(events_list)
+        if not (isinstance(images, torch.Tensor) and images.is_cuda and images.is_contiguous()
+                and images.dtype == torch.float32 and images.numel() == R * self.n * self.n):
+            raise TypeError("images must be a contiguous float32 CUDA tensor of R*n*n values")
+        arr = (_native.Events * R)(*[e.struct() for e in events_list])
+        llp = ctypes.c_void_p(loglik.data_ptr()) if loglik is not None else None
+        _native.check(_native.load().lm_osem_batch(self._h, R, arr, int(n_subsets), int(n_iters),
+                                                   ctypes.c_void_p(images.data_ptr()), llp,
+                                                   _stream(stream)))
+        return images
+
+    def batch_tuning(self) -> dict:
+        out = (ctypes.c_double * 4)()
+        _native.check(_native.load().lm_batch_tuning(self._h, out))
+        return {"unit_order": int(out[0]), "ctas_per_sm": int(out[1]), "tuned": bool(out[2]),
+                "tuned_ms": out[3]}
+
     PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 
     def set_scatter_precision(self, precision="fp32"):

@@ -236,6 +236,9 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_tab);
     cudaFree(h->d_cs);
     cudaFree(h->d_crange);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_tabh);
     cudaFree(h->d_tscale);
     cudaFree(h->d_term_counter);
@@ -446,6 +449,199 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
         }
     }
     return launch_scatter_image(h, lam_v, image, st);
+}
+
+int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subsets, int n_iters,
+                  float* images, double* loglik, lm_stream stream) {
+    if (!h || !events || !images) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    const ModelConst& m = h->mc;
+    if (n_real < 1 || n_real > 65535) return set_error(LMMEW_ERR_INVALID_ARG, "1..65535 realisations");
+    if (n_subsets < 1 || n_subsets > m.A)
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_subsets must be in 1..n_angles");
+    if (n_iters < 0) return set_error(LMMEW_ERR_INVALID_ARG, "negative iteration count");
+    int64_t n_total = 0;
+    for (int r = 0; r < n_real; ++r) {
+        int rc = check_events(h, &events[r]);
+        if (rc != LMMEW_OK) return rc;
+        n_total += events[r].n;
+    }
+    if (n_total >= (int64_t(1) << 31))
+        return set_error(LMMEW_ERR_INVALID_ARG, "at most 2^31 - 1 events per batch");
+    const int R = n_real;
+    const int A_s = (m.A + n_subsets - 1) / n_subsets;
+    const int64_t V = (int64_t)n_subsets * R * A_s;
+    if ((uint64_t)V * (uint64_t)m.B >= (uint64_t(1) << 32))
+        return set_error(LMMEW_ERR_INVALID_ARG, "realisations x angles x bins too large for one batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->graph_exec) {   // the previous batch's graph (its launch finished before this call's sync)
+        LMMEW_CUDA(cudaStreamSynchronize(st));
+        cudaGraphExecDestroy(h->graph_exec);
+        cudaGraphDestroy(h->graph);
+        h->graph_exec = nullptr;
+        h->graph = nullptr;
+    }
+    int rc = subset_sensitivity(h, n_subsets, st);
+    if (rc != LMMEW_OK) return rc;
+    rc = ensure(h, h->scratch_sort, sort_batch_scratch_bytes(n_total, V, R), st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events_batch(h, events, R, n_subsets, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+
+    // plan: per subset, row blocks of whole realisations; 128-event chunks
+    const int rs = row_stride_of(h);
+    const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / rs));
+    struct RowChunk { int t0, t1; int64_t e0, e1; int c0, c1; };
+    std::vector<std::vector<RowChunk>> rchunks(n_subsets);
+    std::vector<BpChunk> bp;
+    std::vector<int> bp_off(n_subsets + 1, 0), part_start((size_t)n_subsets * (R + 1), 0);
+    int64_t biggest = 1;
+    int parts_max = 1;
+    for (int s = 0; s < n_subsets; ++s) {
+        bp_off[s] = (int)bp.size();
+        RowChunk cur{-1, -1, 0, 0, 0, 0};
+        for (int r = 0; r < R; ++r) {
+            const int64_t v0 = ((int64_t)s * R + r) * A_s, v1 = v0 + A_s;
+            const int64_t e0 = se.h_angle_start[v0], e1 = se.h_angle_start[v1];
+            const int t0 = se.h_tile_start[v0], t1 = se.h_tile_start[v1];
+            if (cur.t0 >= 0 && (e1 - cur.e0) > max_ev) {
+                rchunks[s].push_back(cur);
+                cur.t0 = -1;
+            }
+            if (cur.t0 < 0) cur = RowChunk{t0, t0, e0, e0, (int)bp.size() - bp_off[s], 0};
+            part_start[(size_t)s * (R + 1) + r] = (int)bp.size() - bp_off[s];
+            for (int64_t e = e0; e < e1; e += 128)
+                bp.push_back(BpChunk{e - cur.e0, (int)std::min<int64_t>(128, e1 - e), r});
+            cur.t1 = t1;
+            cur.e1 = e1;
+            cur.c1 = (int)bp.size() - bp_off[s];
+        }
+        if (cur.t0 >= 0) rchunks[s].push_back(cur);
+        part_start[(size_t)s * (R + 1) + R] = (int)bp.size() - bp_off[s];
+        parts_max = std::max(parts_max, (int)bp.size() - bp_off[s]);
+        for (const RowChunk& c : rchunks[s]) biggest = std::max(biggest, c.e1 - c.e0);
+    }
+    bp_off[n_subsets] = (int)bp.size();
+    const size_t need = bump_bytes(sizeof(float) * (size_t)R * m.nq) +
+                        bump_bytes(sizeof(float) * (size_t)rs * biggest) +
+                        bump_bytes(sizeof(float) * (size_t)m.nqt * biggest) +
+                        bump_bytes(sizeof(float) * (size_t)parts_max * m.nq) +
+                        bump_bytes(sizeof(double) * (size_t)parts_max) +
+                        bump_bytes(sizeof(double) * (size_t)R * m.nq) +
+                        bump_bytes(sizeof(BpChunk) * std::max<size_t>(bp.size(), 1)) +
+                        bump_bytes(sizeof(int) * part_start.size());
+    rc = ensure(h, h->scratch_work, need, st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* lam_v = bump<float>(w, (size_t)R * m.nq);
+    float* rows = bump<float>(w, (size_t)rs * biggest);
+    float* ypart = bump<float>(w, (size_t)m.nqt * biggest);
+    float* bpart = bump<float>(w, (size_t)parts_max * m.nq);
+    double* llpart = bump<double>(w, parts_max);
+    double* num = bump<double>(w, (size_t)R * m.nq);
+    BpChunk* d_bp = bump<BpChunk>(w, std::max<size_t>(bp.size(), 1));
+    int* d_part = bump<int>(w, part_start.size());
+    if (!bp.empty())
+        LMMEW_CUDA(cudaMemcpyAsync(d_bp, bp.data(), sizeof(BpChunk) * bp.size(),
+                                   cudaMemcpyHostToDevice, st));
+    LMMEW_CUDA(cudaMemcpyAsync(d_part, part_start.data(), sizeof(int) * part_start.size(),
+                               cudaMemcpyHostToDevice, st));
+    rc = launch_images_batch(h, R, images, lam_v, true, st);
+    if (rc != LMMEW_OK) return rc;
+
+    // autotune the row kernel's launch shape on this batch's first row block
+    const uint64_t key = ((uint64_t)n_total << 24) ^ ((uint64_t)R << 8) ^ (uint64_t)n_subsets;
+    if (h->tune_key != key && !rchunks[0].empty()) {
+        const RowChunk& c = rchunks[0][0];
+        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
+                    c.e1 - c.e0, c.e1 - c.e0, m.nq};
+        cudaEvent_t ta, tb;
+        LMMEW_CUDA(cudaEventCreate(&ta));
+        LMMEW_CUDA(cudaEventCreate(&tb));
+        float best = 3.0e38f;
+        int best_order = 0, best_grid = 0;
+        const int max_grid = h->row_blocks[h->prec];
+        for (int order = 0; order < 2; ++order) {
+            for (int grid = 1; grid <= max_grid; ++grid) {
+                h->unit_order = order;
+                h->grid_per_sm = grid;
+                float tmin = 3.0e38f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    LMMEW_CUDA(cudaEventRecord(ta, st));
+                    rc = launch_row(h, L, st);
+                    if (rc != LMMEW_OK) return rc;
+                    LMMEW_CUDA(cudaEventRecord(tb, st));
+                    LMMEW_CUDA(cudaEventSynchronize(tb));
+                    float ms = 0.f;
+                    LMMEW_CUDA(cudaEventElapsedTime(&ms, ta, tb));
+                    tmin = std::min(tmin, ms);
+                }
+                if (tmin < best) {
+                    best = tmin;
+                    best_order = order;
+                    best_grid = grid;
+                }
+            }
+        }
+        cudaEventDestroy(ta);
+        cudaEventDestroy(tb);
+        h->unit_order = best_order;
+        h->grid_per_sm = best_grid;
+        h->tune_key = key;
+        h->tune_ms = best;
+    }
+
+    if (n_iters == 0) return launch_images_batch(h, R, images, lam_v, false, st);
+
+    // the whole reconstruction as one CUDA graph, replayed on the caller's stream
+    if (!h->cap_stream) LMMEW_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    LMMEW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < n_iters && rc == LMMEW_OK; ++it) {
+        for (int s = 0; s < n_subsets && rc == LMMEW_OK; ++s) {
+            for (const RowChunk& c : rchunks[s]) {
+                RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
+                            c.e1 - c.e0, c.e1 - c.e0, m.nq};
+                rc = launch_row(h, L, cs);
+                if (rc != LMMEW_OK) break;
+                rc = launch_bp_batch(h, rows, rs, ypart, c.e1 - c.e0, d_bp + bp_off[s] + c.c0,
+                                     c.c1 - c.c0, bpart, c.c0, llpart, cs);
+                if (rc != LMMEW_OK) break;
+            }
+            if (rc != LMMEW_OK) break;
+            rc = launch_reduce_update_batch(
+                h, R, bpart, d_part + (size_t)s * (R + 1), num, lam_v,
+                h->d_sens_sub + (size_t)s * m.nq, llpart,
+                loglik ? loglik + (size_t)it * n_subsets + s : nullptr, n_iters * n_subsets, cs);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (rc != LMMEW_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess) return cuda_error(ec, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_error(ei, "cudaGraphInstantiate");
+    }
+    h->graph = graph;
+    h->graph_exec = exec;
+    LMMEW_CUDA(cudaGraphLaunch(exec, st));
+    return launch_images_batch(h, R, images, lam_v, false, st);
+}
+
+int lm_batch_tuning(const lm_handle* h, double* out4) {
+    if (!h || !out4) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    out4[0] = h->unit_order;
+    out4[1] = h->grid_per_sm;
+    out4[2] = h->tune_key != 0 ? 1.0 : 0.0;
+    out4[3] = h->tune_ms;
+    return LMMEW_OK;
 }
 
 int lm_set_scatter_precision(lm_handle* h, int precision) {

@@ -195,4 +195,137 @@ int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStrea
     return LMMEW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched realisations: the same steps with every event chunk tagged by its
+// realisation, voxel sums and updates per realisation.
+namespace {
+
+__global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
+    const float* rows, int row_stride, const float* ypart, int64_t ypart_stride, int nqt,
+    const BpChunk* chunks, int nq, float* bpart, int64_t row0, double* llpart) {
+    __shared__ float r[kBpEvents];
+    __shared__ double ll[kBpEvents];
+    const int t = threadIdx.x;
+    const BpChunk C = chunks[blockIdx.x];
+    if (t < kBpEvents) {
+        float rv = 0.f;
+        double lv = 0.0;
+        if (t < C.count) {
+            const int64_t j = C.begin + t;
+            float y = 0.f;
+            for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
+            if (y > 0.f) {
+                rv = 1.0f / y;
+                lv = log((double)y);
+            }
+        }
+        r[t] = rv;
+        ll[t] = lv;
+    }
+    __syncthreads();
+    if (llpart && blockIdx.y == 0) {
+        for (int off = kBpEvents / 2; off > 0; off >>= 1) {
+            if (t < off) ll[t] += ll[t + off];
+            __syncthreads();
+        }
+        if (t == 0) llpart[row0 + blockIdx.x] = ll[0];
+    }
+    const int q = blockIdx.y * kBpVoxels + t;
+    if (q >= nq) return;
+    const float* rp = rows + (size_t)C.begin * row_stride + q;
+    float acc = 0.f;
+    for (int e = 0; e < C.count; ++e) acc = fmaf(r[e], rp[(size_t)e * row_stride], acc);
+    bpart[(size_t)(row0 + blockIdx.x) * nq + q] = acc;
+}
+
+__global__ void k_voxel_reduce_batch(const float* bpart, const int* part_start, int nq,
+                                     double* num) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rr = blockIdx.y;
+    if (q >= nq) return;
+    double acc = 0.0;
+    for (int i = part_start[rr]; i < part_start[rr + 1]; ++i) acc += (double)bpart[(size_t)i * nq + q];
+    num[(size_t)rr * nq + q] = acc;
+}
+
+__global__ void __launch_bounds__(1024) k_update_batch(float* lam, const double* num,
+                                                       const double* sens, int nq,
+                                                       const double* llpart,
+                                                       const int* part_start, double* loglik,
+                                                       int ll_stride) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x, rr = blockIdx.x;
+    float* l = lam + (size_t)rr * nq;
+    const double* nm = num + (size_t)rr * nq;
+    if (loglik) {
+        double s = 0.0;
+        for (int i = part_start[rr] + t; i < part_start[rr + 1]; i += 1024) s += llpart[i];
+        for (int q = t; q < nq; q += 1024) s -= (double)l[q] * sens[q];
+        red[t] = s;
+        __syncthreads();
+        for (int off = 512; off > 0; off >>= 1) {
+            if (t < off) red[t] += red[t + off];
+            __syncthreads();
+        }
+        if (t == 0) loglik[(size_t)rr * ll_stride] = red[0];
+        __syncthreads();
+    }
+    for (int q = t; q < nq; q += 1024)
+        l[q] = sens[q] > 0.0 ? (float)((double)l[q] * nm[q] / sens[q]) : 0.f;
+}
+
+__global__ void k_gather_batch(const float* images, int npix, const int* q_pix, int nq,
+                               float* lam) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) lam[(size_t)blockIdx.y * nq + q] = images[(size_t)blockIdx.y * npix + q_pix[q]];
+}
+
+__global__ void k_scatter_batch(const float* lam, const int* q_pix, int nq, float* images,
+                                int npix) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nq) images[(size_t)blockIdx.y * npix + q_pix[q]] = lam[(size_t)blockIdx.y * nq + q];
+}
+
+}  // namespace
+
+int launch_bp_batch(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                    int64_t ypart_stride, const BpChunk* chunks, int n_chunks, float* bpart,
+                    int64_t row0, double* llpart, cudaStream_t st) {
+    if (n_chunks <= 0) return LMMEW_OK;
+    dim3 g(n_chunks, (h->mc.nq + kBpVoxels - 1) / kBpVoxels);
+    k_bp_batch<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt, chunks,
+                                        h->mc.nq, bpart, row0, llpart);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_reduce_update_batch(lm_handle* h, int R, const float* bpart, const int* part_start,
+                               double* num, float* lam_v, const double* sens,
+                               const double* llpart, double* loglik, int ll_stride,
+                               cudaStream_t st) {
+    dim3 g((h->mc.nq + 255) / 256, R);
+    k_voxel_reduce_batch<<<g, 256, 0, st>>>(bpart, part_start, h->mc.nq, num);
+    k_update_batch<<<R, 1024, 0, st>>>(lam_v, num, sens, h->mc.nq, llpart, part_start, loglik,
+                                       ll_stride);
+    h->launches += 2;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_images_batch(lm_handle* h, int R, float* images, float* lam_v, bool to_voxels,
+                        cudaStream_t st) {
+    const int npix = h->mc.n * h->mc.n;
+    dim3 g((h->mc.nq + 255) / 256, R);
+    if (to_voxels) {
+        k_gather_batch<<<g, 256, 0, st>>>(images, npix, h->d_q_pix, h->mc.nq, lam_v);
+    } else {
+        LMMEW_CUDA(cudaMemsetAsync(images, 0, sizeof(float) * (size_t)R * npix, st));
+        k_scatter_batch<<<g, 256, 0, st>>>(lam_v, h->d_q_pix, h->mc.nq, images, npix);
+    }
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
 }  // namespace lmmew

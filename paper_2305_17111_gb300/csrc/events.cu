@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int
 }
 
 __global__ void k_tiles(const int* start, const int* tile_start, const int* angle_of_rank, int A,
-                        const uint16_t* bin_s, Tile* tiles) {
+                        const uint16_t* bin_s, Tile* tiles, const int* real_of_rank = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A) return;
     const int b0 = start[r], b1 = start[r + 1];
@@ -176,6 +176,7 @@ __global__ void k_tiles(const int* start, const int* tile_start, const int* angl
         T.begin = e;
         T.count = cnt;
         T.b_lo_hi = ((int)bin_s[e] << 16) | (int)bin_s[e + cnt - 1];
+        T.r = real_of_rank ? real_of_rank[r] : 0;
         tiles[t] = T;
     }
 }
@@ -372,6 +373,156 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
                          "every window");
     out->n_tiles = host3[0];
     out->n_valid = host3[1];
+    return LMMEW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched sort: R realisations' events concatenated, keyed by (subset,
+// realisation, angle within the subset, bin), so that for every subset the
+// events of all realisations are one contiguous run and every (realisation,
+// angle) run is cut into its own tiles.
+namespace {
+__global__ void k_keys_batch(const uint16_t* angle, const uint16_t* bin, const float* energy,
+                             int64_t n, const int64_t* off, int R, int A, int B, int n_subsets,
+                             int A_s, int n_win, float4 win01, float4 win23, float4 win45,
+                             float4 win67, uint32_t* keys, uint32_t* vals, int* status) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int lo = 0, hi = R;                       // realisation: off[r] <= j < off[r+1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+    }
+    const int r = lo;
+    const int a = angle[j], b = bin[j];
+    const float e = energy[j];
+    const float wl[8] = {win01.x, win01.z, win23.x, win23.z, win45.x, win45.z, win67.x, win67.z};
+    const float wh[8] = {win01.y, win01.w, win23.y, win23.w, win45.y, win45.w, win67.y, win67.w};
+    bool inwin = false;
+    for (int k = 0; k < n_win; ++k) inwin |= (e >= wl[k] && e < wh[k]);
+    const bool ok = a < A && b < B && isfinite(e) && inwin;
+    const uint32_t V = (uint32_t)n_subsets * R * A_s;
+    const uint32_t v = ((uint32_t)(a % n_subsets) * R + r) * A_s + a / n_subsets;
+    keys[j] = ok ? v * (uint32_t)B + (uint32_t)b : V * (uint32_t)B;
+    vals[j] = (uint32_t)j;
+    if (!ok) atomicOr(status, kStatusOutOfRange);
+}
+}  // namespace
+
+size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R) {
+    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+    size_t b = 0;
+    auto add = [&](size_t bytes) { b += bump_bytes(bytes); };
+    add(4 * n); add(4 * n); add(4 * n); add(4 * n);
+    add(4 * 256 * (nblk > 0 ? nblk : 1));
+    add(4 * n); add(2 * n); add(4 * n);
+    add(2 * n); add(2 * n); add(4 * n);                 // concatenated events
+    add(4 * (V + 1)); add(4 * (V + 1)); add(4 * V); add(4 * V);
+    add(8 * (R + 1));
+    add(sizeof(Tile) * (size_t)(n / kET + V + 1));
+    return b;
+}
+
+int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
+                      SortedEvents* out, char*& arena, cudaStream_t st) {
+    const ModelConst& m = h->mc;
+    const int A = m.A, B = m.B;
+    const int A_s = (A + n_subsets - 1) / n_subsets;
+    const int64_t V = (int64_t)n_subsets * R * A_s;
+    std::vector<int64_t> off(R + 1, 0);
+    for (int r = 0; r < R; ++r) off[r + 1] = off[r] + evs[r].n;
+    const int64_t n = off[R];
+    std::vector<int> angle_of_v(V), real_of_v(V);
+    for (int64_t v = 0; v < V; ++v) {
+        const int ai = (int)(v % A_s), r = (int)((v / A_s) % R), s = (int)(v / ((int64_t)A_s * R));
+        const int a = ai * n_subsets + s;
+        angle_of_v[v] = a < A ? a : 0;
+        real_of_v[v] = r;
+    }
+    uint32_t* keys0 = bump<uint32_t>(arena, n);
+    uint32_t* keys1 = bump<uint32_t>(arena, n);
+    uint32_t* vals0 = bump<uint32_t>(arena, n);
+    uint32_t* vals1 = bump<uint32_t>(arena, n);
+    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+    uint32_t* hist = bump<uint32_t>(arena, 256 * std::max<int64_t>(nblk, 1));
+    out->perm = bump<uint32_t>(arena, n);
+    out->bin = bump<uint16_t>(arena, n);
+    out->energy = bump<float>(arena, n);
+    uint16_t* c_angle = bump<uint16_t>(arena, n);
+    uint16_t* c_bin = bump<uint16_t>(arena, n);
+    float* c_energy = bump<float>(arena, n);
+    out->angle_start = bump<int>(arena, V + 1);
+    out->tile_start = bump<int>(arena, V + 1);
+    int* d_angle_of_v = bump<int>(arena, V);
+    int* d_real_of_v = bump<int>(arena, V);
+    int64_t* d_off = bump<int64_t>(arena, R + 1);
+    out->tiles = bump<Tile>(arena, n / kET + V + 1);
+
+    for (int r = 0; r < R; ++r) {
+        if (evs[r].n == 0) continue;
+        LMMEW_CUDA(cudaMemcpyAsync(c_angle + off[r], evs[r].angle, 2 * evs[r].n,
+                                   cudaMemcpyDeviceToDevice, st));
+        LMMEW_CUDA(cudaMemcpyAsync(c_bin + off[r], evs[r].bin, 2 * evs[r].n,
+                                   cudaMemcpyDeviceToDevice, st));
+        LMMEW_CUDA(cudaMemcpyAsync(c_energy + off[r], evs[r].energy_keV, 4 * evs[r].n,
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+    LMMEW_CUDA(cudaMemcpyAsync(d_off, off.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
+    LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_v, angle_of_v.data(), 4 * V, cudaMemcpyHostToDevice, st));
+    LMMEW_CUDA(cudaMemcpyAsync(d_real_of_v, real_of_v.data(), 4 * V, cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+        float w[8][2] = {};
+        for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
+        k_keys_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            c_angle, c_bin, c_energy, n, d_off, R, A, B, n_subsets, A_s, m.n_win,
+            make_float4(w[0][0], w[0][1], w[1][0], w[1][1]), make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
+            make_float4(w[4][0], w[4][1], w[5][0], w[5][1]), make_float4(w[6][0], w[6][1], w[7][0], w[7][1]),
+            keys0, vals0, h->d_status);
+        LMMEW_CUDA(cudaGetLastError());
+        const uint64_t kmax = (uint64_t)V * (uint64_t)B;
+        int bits = 1;
+        while (bits < 32 && (kmax >> bits) != 0) ++bits;
+        uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
+            k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+            k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk,
+                                                              kout, vout);
+            LMMEW_CUDA(cudaGetLastError());
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, c_energy, n, B, out->perm,
+                                                             out->bin, out->energy);
+        k_bounds<<<(unsigned)((V + 1 + 127) / 128), 128, 0, st>>>(kin, n, (int)V, B, out->angle_start);
+        h->launches += 3 + 3 * ((bits + 7) / 8);
+        LMMEW_CUDA(cudaGetLastError());
+    } else {
+        LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (V + 1), st));
+    }
+    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, (int)V, out->tile_start);
+    k_tiles<<<(unsigned)((V + 127) / 128), 128, 0, st>>>(out->angle_start, out->tile_start,
+                                                         d_angle_of_v, (int)V, out->bin, out->tiles,
+                                                         d_real_of_v);
+    h->launches += 2;
+    LMMEW_CUDA(cudaGetLastError());
+    out->h_angle_start.resize(V + 1);
+    out->h_tile_start.resize(V + 1);
+    int status = 0;
+    LMMEW_CUDA(cudaMemcpyAsync(out->h_angle_start.data(), out->angle_start, 4 * (V + 1),
+                               cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(out->h_tile_start.data(), out->tile_start, 4 * (V + 1),
+                               cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    if (status & kStatusTimeout)
+        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
+    if (status & kStatusOutOfRange)
+        return set_error(LMMEW_ERR_OUT_OF_RANGE,
+                         "an event has an angle or bin outside the model or an energy outside "
+                         "every window");
+    out->n_valid = out->h_angle_start[V];
     return LMMEW_OK;
 }
 

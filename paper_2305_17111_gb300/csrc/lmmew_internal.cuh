@@ -52,6 +52,7 @@ struct Tile {
     int begin;      // first sorted event (index into the sorted arrays)
     int count;      // 1..kET
     int b_lo_hi;    // (b_lo << 16) | b_hi: bin range of the tile's events
+    int r;          // realisation (0 outside batched reconstruction)
 };
 
 struct Scratch {
@@ -85,6 +86,14 @@ struct lm_handle {
     int sm_count = 0;
     int row_blocks_per_sm = 0;
     int row_blocks[3] = {0, 0, 0};   // resident row-kernel CTAs per SM, per precision
+    // launch shape of the row kernel (set by the batch autotuner)
+    int unit_order = 0;            // 0: tile-major units, 1: voxel-tile-major units
+    int grid_per_sm = 0;           // persistent CTAs per SM (0: occupancy maximum)
+    cudaStream_t cap_stream = nullptr;     // private stream for CUDA-graph capture
+    cudaGraphExec_t graph_exec = nullptr;  // last batched reconstruction graph
+    cudaGraph_t graph = nullptr;
+    uint64_t tune_key = 0;         // batch shape the launch shape was tuned for
+    float tune_ms = 0.f;           // the tuned row launch's time
     // scatter-term precision: 0 FP32, 1 FP16, 2 BF16 (reduced-precision form)
     int prec = 0;
     int tabh_prec = 0;
@@ -147,6 +156,9 @@ struct SortedFixed {
     int64_t n_valid = 0;
 };
 size_t sort_fixed_bytes(int64_t n, int A);
+size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R);
+int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
+                      SortedEvents* out, char*& arena, cudaStream_t st);
 int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
                       cudaStream_t st);
 
@@ -163,6 +175,7 @@ struct RowLaunch {
     float* ypart;           // [nqt][ypart_stride], indexed by sorted event - row_base
     int64_t ypart_stride;
     int64_t n_events;       // events covered by the tile range (for accounting)
+    int lam_stride = 0;     // batched: image of realisation r at lam_v + r * lam_stride
 };
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
 int set_precision(lm_handle* h, int prec);
@@ -181,6 +194,20 @@ int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, doubl
                         cudaStream_t st);
 int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
                   const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st);
+struct BpChunk {
+    int64_t begin;   // first event, relative to the row block's base
+    int count;       // 1..128
+    int r;           // realisation
+};
+int launch_bp_batch(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                    int64_t ypart_stride, const BpChunk* chunks, int n_chunks, float* bpart,
+                    int64_t row0, double* llpart, cudaStream_t st);
+int launch_reduce_update_batch(lm_handle* h, int R, const float* bpart, const int* part_start,
+                               double* num, float* lam_v, const double* sens,
+                               const double* llpart, double* loglik, int ll_stride,
+                               cudaStream_t st);
+int launch_images_batch(lm_handle* h, int R, float* images, float* lam_v, bool to_voxels,
+                        cudaStream_t st);
 int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStream_t st);
 int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStream_t st);
 int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStream_t st);

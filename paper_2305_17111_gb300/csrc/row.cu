@@ -100,7 +100,9 @@ struct RowParams {
     int tile_begin, tile_end;
     const uint16_t* ev_bin;
     const float* ev_e;
-    const float* lam;     // [nq] or null
+    const float* lam;     // [nq] (per realisation, lam_stride apart) or null
+    int lam_stride;
+    int unit_order;       // 0: tile-major, 1: voxel-tile-major work units
     float* rows;          // or null
     int64_t row_base;
     int row_stride;
@@ -340,8 +342,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     uint32_t g = 0;                                       // pipeline stages issued so far
 
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
-        const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
-        const int qt = unit % P.nqt;
+        const Tile T = P.tiles[P.tile_begin + (P.unit_order ? unit % n_tiles : unit / P.nqt)];
+        const int qt = P.unit_order ? unit / n_tiles : unit % P.nqt;
+        const float* lam = P.lam ? P.lam + (size_t)T.r * P.lam_stride : nullptr;
         const int b_lo = T.b_lo_hi >> 16, b_hi = T.b_lo_hi & 0xffff;
         const uint32_t c_bytes = (uint32_t)(b_hi - b_lo + 1) * kCPad * 4u;
 
@@ -469,11 +472,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                     P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + q] = tt[e * 33 + ql];
             }
         }
-        if (P.lam && tid < T.count) {
+        if (lam && tid < T.count) {
             const int e = tid;
             float s = 0.f;
             const int qmax = min(kQT, P.nq - qt * kQT);
-            for (int ql = 0; ql < qmax; ++ql) s = fmaf(P.lam[qt * kQT + ql], tt[e * 33 + ql], s);
+            for (int ql = 0; ql < qmax; ++ql) s = fmaf(lam[qt * kQT + ql], tt[e * 33 + ql], s);
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
         }
         __syncthreads();
@@ -530,6 +533,8 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     P.ev_bin = L.ev_bin;
     P.ev_e = L.ev_e;
     P.lam = L.lam_v;
+    P.lam_stride = L.lam_stride;
+    P.unit_order = h->unit_order;
     P.rows = L.rows;
     P.row_base = L.row_base;
     P.row_stride = L.row_stride;
@@ -593,7 +598,9 @@ int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     if (n_units <= 0) return LMMEW_OK;
     const int prec = h->prec;
     RowParams P = make_params(h, L, prec);
-    const int grid = std::min(n_units, h->sm_count * h->row_blocks[prec]);
+    const int per_sm = h->grid_per_sm > 0 ? std::min(h->grid_per_sm, h->row_blocks[prec])
+                                          : h->row_blocks[prec];
+    const int grid = std::min(n_units, h->sm_count * per_sm);
     row_kernel_for(h->mc.W, prec)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());

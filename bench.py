@@ -393,6 +393,30 @@ def run_batch_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, iters=
             "speedup_batched_vs_one_at_a_time": float(np.sum(seq) / np.median(batch))}
 
 
+def run_comparison_form(noise_realisations=16, events=10_000, seed=21):
+    """The paper's comparison (LM-MEW vs LM-SEW vs Binned-SEW) on its study
+    object and protocol: ensemble normalised RMSE, bias and standard
+    deviation of the four lesions' uptake."""
+    import time as _time
+
+    from paper_2305_17111_gb300 import studies
+    from synthetic import preset
+    sc = preset("paper_study")
+    t0 = _time.perf_counter()
+    res = studies.run_study(sc, noise_realisations, events, seed=seed)
+    wall = _time.perf_counter() - t0
+    out = {"workload": f"paper_study: 64x64 of 4.6 mm, 120 angles, EW1-EW3, lesions r = "
+                       f"7/10/12/14 mm at SBR 4:1, {noise_realisations} noise realisations x "
+                       f"{events} events (seed {seed}), {sc.n_subsets} subsets x {sc.n_iters} "
+                       f"iterations", "wall_s_incl_event_generation": wall}
+    for name, r in res.items():
+        out[name] = {"events_mean": r["events_mean"],
+                     "enrmse": [float(v) for v in r["enrmse"]],
+                     "bias": [float(v) for v in r["bias"]],
+                     "std": [float(v) for v in r["std"]]}
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, local_rank, world):
     import numpy as np
@@ -497,7 +521,8 @@ def run_gpu(args, rank, local_rank, world):
     }
     if world == 1 and not args.no_forms and not args.events:
         model.close()
-        line["forms"] = {"precision": run_precision_form(), "batching": run_batch_form()}
+        line["forms"] = {"precision": run_precision_form(), "batching": run_batch_form(),
+                         "comparison": run_comparison_form()}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

@@ -33,12 +33,18 @@ class Disc:
 
 @dataclass(frozen=True)
 class PhantomSpec:
-    """Ellipse body + one bone disc + circular lesions (all centred in cm)."""
+    """Ellipse body + optional bone disc + circular lesions (all centred in cm).
 
-    bone: Disc
+    ``rim_cm`` > 0 gives the body a denser outer rim (the paper's attenuation
+    map has a rim of 0.21 and an inner region of 0.18 1/cm at 85 keV, i.e.
+    water whose density differs between the two)."""
+
+    bone: Disc | None
     lesions: tuple[Disc, ...]
     semi_axes_cm: tuple[float, float] = ELLIPSE_SEMI_AXES_CM
     lesion_ratio: float = LESION_TO_BACKGROUND
+    rim_cm: float = 0.0
+    rim_density: float = 1.0
 
 
 # Two lesions and a bone disc (the 32x32 and 64x64 workloads).
@@ -58,6 +64,18 @@ def _four_lesions() -> tuple[Disc, ...]:
 
 # Four lesions of radius 1-4 cm (the 128x128 workloads).
 FOUR_LESION = PhantomSpec(bone=Disc(0.0, 0.0, 1.2), lesions=_four_lesions())
+
+
+def paper_study_phantom(sbr: float = 4.0) -> PhantomSpec:
+    """The paper's study object: four lesions of radius 7/10/12/14 mm placed
+    symmetrically about the centre, signal-to-background ratio ``sbr``, and a
+    rim/inner attenuation map (0.21 vs 0.18 1/cm at 85 keV)."""
+    lesions = []
+    for r_cm, deg in zip((0.7, 1.0, 1.2, 1.4), (45.0, 135.0, 225.0, 315.0)):
+        t = np.deg2rad(deg)
+        lesions.append(Disc(4.5 * float(np.cos(t)), 4.5 * float(np.sin(t)), r_cm))
+    return PhantomSpec(bone=None, lesions=tuple(lesions), lesion_ratio=sbr, rim_cm=1.0,
+                       rim_density=0.21 / 0.18)
 
 
 def pixel_centres_cm(n: int, pixel_cm: float) -> tuple[np.ndarray, np.ndarray]:
@@ -83,8 +101,12 @@ def make_phantom(spec: PhantomSpec, n: int, pixel_cm: float) -> Phantom:
     ax, ay = spec.semi_axes_cm
     body = (x / ax) ** 2 + (y / ay) ** 2 <= 1.0
     rho = np.where(body, 1.0, 0.0)
-    bone = body & _inside(x, y, spec.bone)
-    rho = np.where(bone, BONE_DENSITY, rho)
+    if spec.rim_cm > 0:
+        inner = (x / (ax - spec.rim_cm)) ** 2 + (y / (ay - spec.rim_cm)) ** 2 <= 1.0
+        rho = np.where(body & ~inner, spec.rim_density, rho)
+    if spec.bone is not None:
+        bone = body & _inside(x, y, spec.bone)
+        rho = np.where(bone, BONE_DENSITY, rho)
     act = np.where(body, 1.0, 0.0)
     masks = []
     for d in spec.lesions:

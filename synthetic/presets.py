@@ -16,7 +16,8 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-from .phantom import FOUR_LESION, TWO_LESION, Phantom, PhantomSpec, make_phantom
+from .phantom import (FOUR_LESION, TWO_LESION, Phantom, PhantomSpec, make_phantom,
+                      paper_study_phantom)
 
 
 @dataclass(frozen=True)
@@ -82,6 +83,12 @@ PRESETS: dict[str, Scenario] = {
     "small_32_4w": Scenario("small_32_4w", 32, 0.8, 16, 40, 16, 1500, 13, 4, 1,
                             windows=((68.0, 102.0), (123.0, 184.0), (243.0, 297.0))),
     "tiny_8": Scenario("tiny_8", 8, 3.2, 4, 10, 4, 64, 14, 2, 2),
+    # The paper's comparison study (Sec. Experiments): 64x64 grid of 4.6 mm,
+    # 120 angles, the three photopeak windows, ~1e4 events per realisation,
+    # 4 subsets x 16 iterations, four lesions at 4:1.
+    "paper_study": Scenario("paper_study", 64, 0.46, 120, 64, 32, 10_000, 21, 4, 16,
+                            phantom=paper_study_phantom(4.0),
+                            windows=((68.0, 102.0), (123.0, 184.0), (243.0, 297.0))),
     "noscatter_16": Scenario("noscatter_16", 16, 1.6, 8, 16, 0, 400, 15, 2, 3),
 }
 

@@ -242,6 +242,81 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
  * (ms).  Not part of the paper's method.  Errors: INVALID_ARG. */
 int lm_batch_tuning(const lm_handle* h, double* out4);
 
+/* ---------------------------------------------------------------------
+ * Learned surrogate of the single-scatter term (not in the paper: the
+ * paper evaluates Eq. s_p with n = 1 exactly; this replaces that sum by a
+ * small network, trained on samples of the exact sum).
+ *
+ * The network maps 32 inputs of one (event, voxel, line w) -- voxel x, y,
+ * detector direction cos/sin, bin centre, recorded energy, line one-hot (up
+ * to 3 lines) and the optical depth mu_w(E_w) x (rho line integral from the
+ * voxel to the image edge along theta_a + k pi/4, k = 0..7) -- through three
+ * 128-wide GELU (tanh form) layers to ln(S_w + 1e-8), S_w the single-scatter
+ * part of the system-matrix element for that line.  Weights BF16 for the
+ * tensor-core kernels, FP32 masters, Adam.  Parameter vector (FP32):
+ * W1[128][32], b1[128], W2[128][128], b2, W3[128][128], b3, w4[128], b4. */
+typedef struct lm_surrogate lm_surrogate;
+
+/* Number of FP32 parameters (37 377). */
+int lm_surrogate_param_count(void);
+
+/* New network with Xavier-uniform weights drawn from a SplitMix64 stream of
+ * `seed`.  Errors: INVALID_ARG, OOM, CUDA. */
+int lm_surrogate_create(uint64_t seed, lm_surrogate** out);
+int lm_surrogate_destroy(lm_surrogate* s);
+
+/* Copy the FP32 parameters to / from HOST memory (param_count floats). */
+int lm_surrogate_get_params(const lm_surrogate* s, float* host_out);
+int lm_surrogate_set_params(lm_surrogate* s, const float* host_in);
+
+/* Network outputs for n input rows.  x: DEVICE float[n][32] (rounded to
+ * BF16 inside); out: DEVICE float[n].  Asynchronous on the stream. */
+int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out, lm_stream stream);
+
+/* Gradient of the weighted mean squared error
+ *   L = (1/n) sum_i v_i (net(x_i) - target_i)^2
+ * with respect to the parameters.  x: DEVICE float[n][32], target: DEVICE
+ * float[n], weight: DEVICE float[n] or NULL (all v_i = 1), grad_out: DEVICE
+ * float[param_count]; loss_out: NULL or HOST.  Synchronises the stream. */
+int lm_surrogate_gradient(lm_surrogate* s, const float* x, const float* target,
+                          const float* weight, int64_t n, float* grad_out, double* loss_out,
+                          lm_stream stream);
+
+/* Adam training (beta 0.9 / 0.999, eps 1e-8, bias-corrected) for `steps`
+ * minibatches of `batch` rows drawn with replacement from the n DEVICE
+ * samples: row i of the minibatch of step k (counted over the surrogate's
+ * life) is SplitMix64(seed ^ SplitMix64(k * 0x100000001b3 + i)) mod n, with
+ * SplitMix64(z) the generator's output for state z.  Sample weights
+ * v_i = exp(weight_power (t_i - max_j t_j)), normalised to mean 1 over the n
+ * samples (weight_power 0: unweighted), so that with targets ln(S + eps)
+ * the loss counts each sample by (S + eps)^weight_power.  loss_history:
+ * NULL or HOST double[steps] (each minibatch's loss before its update; this
+ * synchronises every step).  Synchronises the stream.
+ * Errors: INVALID_ARG (n <= 0, n >= 2^32, batch not in 1..2^20, lr <= 0,
+ * weight_power not in [0, 64]), OOM, CUDA. */
+int lm_surrogate_train(lm_surrogate* s, const float* x, const float* target, int64_t n, int steps,
+                       int batch, float lr, float weight_power, uint64_t seed,
+                       double* loss_history, lm_stream stream);
+
+/* n training samples from a model: events drawn uniformly from `events`
+ * (device), voxels uniformly from the support, lines uniformly; x_out:
+ * DEVICE float[n][32] inputs, target_out: DEVICE float[n] = ln(S_w + 1e-8)
+ * with S_w the exact single-scatter sum of the model's tables (FP32 terms,
+ * FP64 sum).  SplitMix64 of `seed`.  Errors: INVALID_ARG, NOT_IMPLEMENTED
+ * (more than 3 lines), CUDA. */
+int lm_surrogate_sample(lm_handle* h, const lm_events* events, int64_t n, uint64_t seed,
+                        float* x_out, float* target_out, lm_stream stream);
+
+/* Scatter model of the handle's later lm_forward / lm_osem calls:
+ * LMMEW_SCATTER_EXACT (default, s ignored), LMMEW_SCATTER_SURROGATE (the
+ * network s, which must outlive its use), LMMEW_SCATTER_NONE (unscattered
+ * paths only: the method without a scatter model).
+ * Errors: INVALID_ARG, NOT_IMPLEMENTED (surrogate with more than 3 lines). */
+#define LMMEW_SCATTER_EXACT 0
+#define LMMEW_SCATTER_SURROGATE 1
+#define LMMEW_SCATTER_NONE 2
+int lm_set_scatter_model(lm_handle* h, int model, const lm_surrogate* s);
+
 /* Free every device buffer of the handle (NULL is ignored). */
 int lm_destroy(lm_handle* h);
 

@@ -102,6 +102,7 @@ def _load():
             "orc_line_integral": (_D, [_P, _D, _D, _D, _D]),
             "orc_detector_integral": (_D, [_P, _D, _D, _I]),
             "orc_row": (None, [_P, _I, _I, _D, _PD]),
+            "orc_scatter_line_row": (None, [_P, _I, _I, _D, _I, _PD]),
             "orc_forward": (None, [_P, _I64, _PU16, _PU16, _PF, _PD, _PD]),
             "orc_backproject": (None, [_P, _I64, _PU16, _PU16, _PF, _PD, _PD]),
             "orc_sensitivity": (None, [_P, _I, _I, _PD]),
@@ -240,6 +241,15 @@ class Model:
         """System-matrix row over the voxel set (raster order of voxel_pixels)."""
         out = np.zeros(self.nq, dtype=np.float64)
         _load().orc_row(self._h, int(a), int(b), float(e_hat), _ptr(out, ctypes.c_double))
+        return out
+
+    def scatter_line_row(self, a, b, e_hat, w) -> np.ndarray:
+        """Single-scatter part of line w's row: alpha_w times the n = 1 paths
+        of Eq. (s_p) summed over the scatter points, times the detector
+        response (voxel order of voxel_pixels)."""
+        out = np.zeros(self.nq, dtype=np.float64)
+        _load().orc_scatter_line_row(self._h, int(a), int(b), float(e_hat), int(w),
+                                     _ptr(out, ctypes.c_double))
         return out
 
     def row_image(self, a, b, e_hat) -> np.ndarray:

@@ -530,6 +530,28 @@ void orc_row(const orc_model* m, int a, int b, double e_hat, double* out_row) {
     angle_paths_free(&ap);
 }
 
+/* Single-scatter part of one line's row for one event:
+ *   out[q] = alpha_w sum_{P, n = 1} pr(A_j | P, E_0^w) s(P, E_0^w)
+ * i.e. the n = 1 paths of Eq. (s_p) summed over the scatter points, times the
+ * detector response (the quantity the learned surrogate is trained on). */
+void orc_scatter_line_row(const orc_model* m, int a, int b, double e_hat, int w, double* out_row) {
+    angle_paths ap;
+    angle_paths_build(m, a, &ap);
+    const int nq = m->nq, np = m->np;
+    double* c_p = (double*)malloc(sizeof(double) * (np > 0 ? np : 1));
+    for (int p = 0; p < np; p++) c_p[p] = orc_bin_prob(m, b, ap.u_p[p], ap.sig_p[p]);
+    for (int q = 0; q < nq; q++) {
+        const double* s = ap.s_scat + ((size_t)w * nq + q) * np;
+        const double* e1 = ap.e_scat + ((size_t)w * nq + q) * np;
+        double acc = 0.0;
+        for (int p = 0; p < np; p++)
+            if (s[p] != 0.0) acc += s[p] * c_p[p] * orc_energy_density(m, e_hat, e1[p]);
+        out_row[q] = m->p.line_yield[w] * acc;
+    }
+    free(c_p);
+    angle_paths_free(&ap);
+}
+
 /* Visit events angle by angle: build s(P) for that angle once, then hand
  * each event's row to a callback together with the index of the thread that
  * computed it (callbacks keep per-thread partial sums). */

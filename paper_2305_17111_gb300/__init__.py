@@ -14,7 +14,7 @@ import numpy as np
 from . import _native
 from ._native import LmmewError
 
-__all__ = ["Model", "DeviceEvents", "LmmewError", "library_path"]
+__all__ = ["Model", "DeviceEvents", "Surrogate", "LmmewError", "library_path"]
 
 
 def library_path() -> str:
@@ -218,6 +218,29 @@ class Model:
         _native.check(_native.load().lm_set_scatter_precision(self._h,
                                                               self.PRECISIONS[precision]))
 
+    SCATTER_MODELS = {"exact": _native.SCATTER_EXACT, "surrogate": _native.SCATTER_SURROGATE,
+                      "none": _native.SCATTER_NONE}
+
+    def set_scatter_model(self, model="exact", surrogate: "Surrogate | None" = None):
+        """Scatter part of the rows: 'exact' (the single-scatter sum),
+        'surrogate' (the learned network, which must stay alive while used)
+        or 'none' (unscattered paths only)."""
+        ptr = surrogate._s if surrogate is not None else None
+        _native.check(_native.load().lm_set_scatter_model(self._h, self.SCATTER_MODELS[model], ptr))
+        self._surrogate_ref = surrogate
+
+    def surrogate_samples(self, events: DeviceEvents, n, seed=0, stream=None):
+        """n training samples (x [n, 32], target [n]) for the surrogate: random
+        (event, voxel, line) with the exact ln(S_w + 1e-8) as target."""
+        torch = _torch()
+        x = torch.empty((int(n), Surrogate.N_IN), dtype=torch.float32, device="cuda")
+        t = torch.empty(int(n), dtype=torch.float32, device="cuda")
+        ev = events.struct()
+        _native.check(_native.load().lm_surrogate_sample(
+            self._h, ctypes.byref(ev), int(n), ctypes.c_uint64(seed), ctypes.c_void_p(x.data_ptr()),
+            ctypes.c_void_p(t.data_ptr()), _stream(stream)))
+        return x, t
+
     def profile_enable(self, on=True):
         _native.check(_native.load().lm_profile_enable(self._h, 1 if on else 0))
 
@@ -226,3 +249,82 @@ class Model:
         _native.check(_native.load().lm_profile_read(self._h, out))
         return {"ms": out[0], "launches": int(out[1]), "terms": out[2], "elements": out[3],
                 "kernels": int(out[4])}
+
+
+class Surrogate:
+    """The learned single-scatter surrogate (an ``lm_surrogate``): an MLP
+    32 -> 128 -> 128 -> 128 -> 1 with GELU, BF16 tensor-core kernels and FP32
+    master parameters."""
+
+    N_IN = 32
+
+    def __init__(self, seed=0):
+        lib = _native.load()
+        s = ctypes.c_void_p()
+        _native.check(lib.lm_surrogate_create(ctypes.c_uint64(seed), ctypes.byref(s)))
+        self._s = s
+        self.n_params = int(lib.lm_surrogate_param_count())
+
+    def close(self):
+        if getattr(self, "_s", None) is not None and self._s.value:
+            _native.load().lm_surrogate_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _native.check(_native.load().lm_surrogate_get_params(self._s, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _native.check(_native.load().lm_surrogate_set_params(self._s, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+        _native.check(_native.load().lm_surrogate_forward(self._s, ctypes.c_void_p(x.data_ptr()),
+                                                          int(x.shape[0]),
+                                                          ctypes.c_void_p(out.data_ptr()),
+                                                          _stream(stream)))
+        return out
+
+    def gradient(self, x, target, weight=None, stream=None):
+        """(grad [n_params] float32 CUDA tensor, weighted mean squared error)."""
+        torch = _torch()
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        target = target.to(device="cuda", dtype=torch.float32).contiguous()
+        if weight is not None:
+            weight = weight.to(device="cuda", dtype=torch.float32).contiguous()
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        _native.check(_native.load().lm_surrogate_gradient(
+            self._s, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+            ctypes.c_void_p(weight.data_ptr()) if weight is not None else None,
+            int(x.shape[0]), ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train(self, x, target, steps, batch=4096, lr=1e-3, seed=0, weight_power=0.0,
+              record_loss=True, stream=None):
+        """Adam on minibatches drawn from (x, target), each sample weighted
+        by exp(weight_power (t - max t)).  Returns the loss of every
+        minibatch before its update (record_loss; this synchronises each
+        step), else None."""
+        torch = _torch()
+        x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        target = target.to(device="cuda", dtype=torch.float32).contiguous()
+        hist = np.zeros(int(steps), dtype=np.float64) if record_loss else None
+        _native.check(_native.load().lm_surrogate_train(
+            self._s, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+            int(x.shape[0]) if x.dim() else 0, int(steps), int(batch), ctypes.c_float(lr),
+            ctypes.c_float(weight_power), ctypes.c_uint64(seed),
+            hist.ctypes.data_as(ctypes.c_void_p) if hist is not None else None, _stream(stream)))
+        return hist

@@ -86,7 +86,27 @@ SYMBOLS = {
     "lm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "lm_model_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "lm_surrogate_param_count": (ctypes.c_int, []),
+    "lm_surrogate_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
+    "lm_surrogate_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "lm_surrogate_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_surrogate_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_surrogate_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_surrogate_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "lm_surrogate_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_surrogate_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Events),
+                                           ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_set_scatter_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
 }
+
+SCATTER_EXACT, SCATTER_SURROGATE, SCATTER_NONE = 0, 1, 2
 
 
 def load(path: str = LIB_PATH):

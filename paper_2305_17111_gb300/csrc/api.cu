@@ -236,6 +236,8 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_tab);
     cudaFree(h->d_cs);
     cudaFree(h->d_crange);
+    cudaFree(h->d_g8);
+    cudaFree(h->d_rho);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -245,6 +247,7 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_cv);
     cudaFree(h->d_prim);
     cudaFree(h->d_sens_a);
+    cudaFree(h->d_sens_a_prim);
     cudaFree(h->d_status);
     cudaFree(h->d_sens_sub);
     cudaFree(h->scratch_sort.ptr);
@@ -292,21 +295,29 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     SortedEvents se;
     rc = sort_events(h, ev, 1, &se, arena, st);
     if (rc != LMMEW_OK) return rc;
-    const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / m.nqt));
+    // the surrogate adds its scatter part to stored rows; the other models
+    // need only the partial forward sums
+    const bool keep_rows = h->scatter_model == LMMEW_SCATTER_SURROGATE;
+    const int rs = row_stride_of(h);
+    const int64_t max_ev =
+        std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / (keep_rows ? rs : m.nqt)));
     std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
     int64_t biggest = 0;
     for (const Chunk& c : chunks) biggest = std::max(biggest, c.e1 - c.e0);
     rc = ensure(h, h->scratch_work,
-                bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * m.nqt * biggest), st);
+                bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * m.nqt * biggest) +
+                    (keep_rows ? bump_bytes(sizeof(float) * rs * biggest) : 0),
+                st);
     if (rc != LMMEW_OK) return rc;
     char* w = (char*)h->scratch_work.ptr;
     float* lam_v = bump<float>(w, m.nq);
     float* ypart = bump<float>(w, (size_t)m.nqt * std::max<int64_t>(biggest, 1));
+    float* rows = keep_rows ? bump<float>(w, (size_t)rs * std::max<int64_t>(biggest, 1)) : nullptr;
     rc = launch_gather_image(h, image, lam_v, st);
     if (rc != LMMEW_OK) return rc;
     for (const Chunk& c : chunks) {
-        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, nullptr, c.e0, 0, ypart,
-                    c.e1 - c.e0, c.e1 - c.e0};
+        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, keep_rows ? rs : 0,
+                    ypart, c.e1 - c.e0, c.e1 - c.e0};
         rc = launch_row_profiled(h, L, st);
         if (rc != LMMEW_OK) return rc;
         rc = launch_forward_out(h, ypart, c.e1 - c.e0, c.e0, c.e1 - c.e0, se.perm, out_y, st);
@@ -551,7 +562,8 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     if (rc != LMMEW_OK) return rc;
 
     // autotune the row kernel's launch shape on this batch's first row block
-    const uint64_t key = ((uint64_t)n_total << 24) ^ ((uint64_t)R << 8) ^ (uint64_t)n_subsets;
+    const uint64_t key = ((uint64_t)n_total << 24) ^ ((uint64_t)R << 8) ^ (uint64_t)n_subsets ^
+                         ((uint64_t)h->scatter_model << 60) ^ ((uint64_t)h->prec << 62);
     if (h->tune_key != key && !rchunks[0].empty()) {
         const RowChunk& c = rchunks[0][0];
         RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,

@@ -99,6 +99,14 @@ struct lm_handle {
     int tabh_prec = 0;
     float* d_tabh = nullptr;       // reduced-precision copy of d_tab
     float* d_tscale = nullptr;     // [A][nqt][npc] block scales 2^base
+    // learned scatter surrogate
+    float* d_g8 = nullptr;         // [A][nq][8] rho line integrals along theta_a + k pi/4 (cm)
+    float* d_rho = nullptr;        // [n][n] relative density (surrogate inputs)
+    double mu_line[LMMEW_MAX_LINES] = {};   // mu_water at each line energy
+    const struct lm_surrogate* surrogate = nullptr;   // scatter model when set
+    int scatter_model = 0;         // 0 exact, 1 surrogate, 2 none
+    double* d_sens_a_prim = nullptr;   // [A][nq] unscattered part of the sensitivity
+    int sens_prim_only = 0;
     float setup_ms = 0.f;
     int64_t terms_per_event = 0;   // exponentials per event row (primary + scatter)
     // optional timing of the row kernel (CUDA events around each launch)
@@ -176,9 +184,13 @@ struct RowLaunch {
     int64_t ypart_stride;
     int64_t n_events;       // events covered by the tile range (for accounting)
     int lam_stride = 0;     // batched: image of realisation r at lam_v + r * lam_stride
+    int skip_scatter = 0;   // unscattered terms only (the surrogate adds the rest)
 };
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
 int set_precision(lm_handle* h, int prec);
+// mlp.cu: the surrogate's rows (adds the learned scatter part to rows k_row
+// wrote without scatter, then the partial forward sums)
+int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st);
 size_t row_smem_bytes(const lm_handle* h);
 int row_kernel_occupancy(lm_handle* h);
 
@@ -212,6 +224,65 @@ int launch_gather_image(lm_handle* h, const float* image, float* lam_v, cudaStre
 int launch_scatter_image(lm_handle* h, const float* lam_v, float* image, cudaStream_t st);
 int launch_scatter_image_d(lm_handle* h, const double* v, double* image, cudaStream_t st);
 int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStream_t st);
+
+// Inputs of the learned scatter surrogate for one (event, voxel q, line w).
+// Geometry in cm in the frame of detector angle a: depth t = x cos + y sin,
+// detector coordinate u = -x sin + y cos.  The recorded energy fixes, through
+// Compton's relation, the scattering angle phi a single scatter needs to
+// bring E_w down to e_hat: 1 - cos(phi) = kappa = m_e c^2 (1/e_hat - 1/E_w).
+// The scatter point p* on the bin's projection line (u = u_b) seen from q at
+// that angle to the detector direction dominates S_w; its position,
+// distance and density are inputs, together with the optical depths
+// mu_w(E_w) x rho-integral from q to the image edge along theta_a + k pi/4.
+//   0-1 x, y      2-3 cos, sin of theta_a   4 u_b   5 e_hat   6-8 line one-hot
+//   9-16 optical depths   17 u_b - u_q   18 t_q   19 kappa   20 e_hat / E_w
+//   21 |u_b - u_q|   22-23 p*   24 |p* - q|   25 cos(phi)   26 h / (|p* - q| + h)
+//   27 [kappa < 0]   28 rho(p*)   29-31 zero
+constexpr int kSurrogateIn = 32;
+constexpr float kSurrogateEps = 1e-8f;   // target = ln(S + eps)
+constexpr float kElectronRestKeV = 510.99895f;
+__host__ __device__ __forceinline__ void surrogate_features(float xq, float yq, float ca, float sa,
+                                                            float ub, float e_hat, int w,
+                                                            float e_line, float mu_w,
+                                                            const float* g8, const float* rho,
+                                                            int n, float h, float* f) {
+    f[0] = xq * 0.05f;
+    f[1] = yq * 0.05f;
+    f[2] = ca;
+    f[3] = sa;
+    f[4] = ub * 0.05f;
+    f[5] = (e_hat - 150.f) * 0.01f;
+    f[6] = w == 0 ? 1.f : 0.f;
+    f[7] = w == 1 ? 1.f : 0.f;
+    f[8] = w == 2 ? 1.f : 0.f;
+    for (int k = 0; k < 8; ++k) f[9 + k] = mu_w * g8[k] * 0.25f;
+    const float uq = -xq * sa + yq * ca, tq = xq * ca + yq * sa;
+    const float du = ub - uq;
+    const float kappa = kElectronRestKeV * (1.f / e_hat - 1.f / e_line);
+    f[17] = du * 0.2f;
+    f[18] = tq * 0.05f;
+    f[19] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
+    f[20] = e_hat / e_line;
+    f[21] = fabsf(du) * 0.2f;
+    const float c = fminf(fmaxf(1.f - kappa, -1.f), 1.f);
+    const float s = fmaxf(sqrtf(fmaxf(1.f - c * c, 0.f)), 0.05f);
+    const float lim = n * h;
+    const float dt = fminf(fmaxf(fabsf(du) * c / s, -lim), lim);
+    const float tp = tq + dt;
+    const float xp = tp * ca - ub * sa, yp = tp * sa + ub * ca;
+    const float r = sqrtf(dt * dt + du * du);
+    f[22] = xp * 0.05f;
+    f[23] = yp * 0.05f;
+    f[24] = r * 0.05f;
+    f[25] = c;
+    f[26] = h / (r + h);
+    f[27] = kappa < 0.f ? 1.f : 0.f;
+    const float gx = floorf(xp / h + 0.5f * n), gy = floorf(yp / h + 0.5f * n);
+    f[28] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n)
+                ? rho[(int)gy * n + (int)gx]
+                : 0.f;
+    f[29] = f[30] = f[31] = 0.f;
+}
 
 // Bump allocation from a scratch arena (256-byte aligned).
 template <class T>

@@ -1,0 +1,989 @@
+// Learned surrogate of the single-scatter sum: a 4-layer MLP
+//   x (32, BF16) -> 128 -> 128 -> 128 (GELU, tanh form) -> 1
+// predicting ln(S_w + eps) for one (event, voxel, line), where S_w is the
+// single-scatter part of the system-matrix element for line w (Eq. s_p with
+// n = 1 summed over the scatter points).  Forward, backward and Adam run in
+// kernels written here; the matrix products use the BF16 tensor cores
+// through mma.sync m16n8k16 fragments loaded with ldmatrix, FP32
+// accumulation.  A CTA owns 128 samples; each of its 8 warps owns 16 rows.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lmmew_internal.cuh"
+
+namespace lmmew {
+namespace mlp {
+
+constexpr int kIn = 32, kHid = 128;
+constexpr int kLdX = kIn + 8;    // padded rows keep ldmatrix conflict-free
+constexpr int kLdH = kHid + 8;
+constexpr int kTile = 128;       // samples per CTA
+constexpr int kThreads = 256;
+// parameter vector (FP32 masters): W1[128][32] b1 W2[128][128] b2 W3 b3 w4[128] b4
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+              kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid,
+              kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kHid,
+              kParams = kOffB4 + 1;
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t* r, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr(p)));
+}
+__device__ __forceinline__ void mma(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// GELU, tanh form: 0.5 z (1 + tanh(c (z + 0.044715 z^3))), c = sqrt(2/pi)
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu(float z) {
+    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
+    return 0.5f * z * (1.f + tanh_fast(u));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
+    const float t = tanh_fast(u);
+    return 0.5f * (1.f + t) +
+           0.5f * z * (1.f - t * t) * 0.7978845608028654f * (1.f + 3.f * 0.044715f * z * z);
+}
+
+// acc[16 rows m0.. of this warp][N] += A[m][k] * W[n][k]   (A, W row-major in smem)
+template <int K, int N>
+__device__ __forceinline__ void gemm_nt(float (*acc)[4], const bf16* A, int lda, int m0,
+                                        const bf16* W, int ldw, int lane) {
+#pragma unroll
+    for (int kk = 0; kk < K; kk += 16) {
+        uint32_t a[4];
+        ldsm4(a, A + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * lda + kk + (lane >> 4) * 8);
+#pragma unroll
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            uint32_t b[4];
+            ldsm4(b, W + (n0 + (lane & 7) + (lane >> 4) * 8) * ldw + kk + ((lane >> 3) & 1) * 8);
+            mma(acc[n0 / 8], a, b[0], b[1]);
+            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
+        }
+    }
+}
+
+// acc[16 rows][N] += A[m][k] * Bm[k][n]   (Bm row-major [K][N])
+template <int K, int N>
+__device__ __forceinline__ void gemm_nn(float (*acc)[4], const bf16* A, int lda, int m0,
+                                        const bf16* Bm, int ldb, int lane) {
+#pragma unroll
+    for (int kk = 0; kk < K; kk += 16) {
+        uint32_t a[4];
+        ldsm4(a, A + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * lda + kk + (lane >> 4) * 8);
+#pragma unroll
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            uint32_t b[4];
+            ldsm4t(b, Bm + (kk + (lane & 7) + ((lane >> 3) & 1) * 8) * ldb + n0 + (lane >> 4) * 8);
+            mma(acc[n0 / 8], a, b[0], b[1]);
+            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
+        }
+    }
+}
+
+// acc[16 rows i0..][N] += sum_m P[m][i] * Q[m][j]   (P, Q row-major [M][.]), M = 128
+template <int N>
+__device__ __forceinline__ void gemm_tn(float (*acc)[4], const bf16* P, int ldp, int i0,
+                                        const bf16* Q, int ldq, int lane) {
+#pragma unroll 2
+    for (int m0 = 0; m0 < kTile; m0 += 16) {
+        uint32_t a[4];
+        ldsm4t(a, P + (m0 + (lane & 7) + (lane >> 4) * 8) * ldp + i0 + ((lane >> 3) & 1) * 8);
+#pragma unroll
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            uint32_t b[4];
+            ldsm4t(b, Q + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * ldq + n0 + (lane >> 4) * 8);
+            mma(acc[n0 / 8], a, b[0], b[1]);
+            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void zero(float (*acc)[4]) {
+#pragma unroll
+    for (int i = 0; i < N / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+}
+
+__device__ __forceinline__ void copy_rows(bf16* dst, int ldd, const bf16* src, int lds, int rows,
+                                          int cols) {
+    // 16-byte chunks
+    const int per_row = cols / 8;
+    for (int i = threadIdx.x; i < rows * per_row; i += blockDim.x) {
+        const int r = i / per_row, c = (i % per_row) * 8;
+        *reinterpret_cast<uint4*>(dst + r * ldd + c) =
+            *reinterpret_cast<const uint4*>(src + (size_t)r * lds + c);
+    }
+}
+
+struct Weights {
+    const bf16* W1;    // [128][32]
+    const bf16* W2;    // [128][128]
+    const bf16* W3;
+    const float* p;    // FP32 parameters (biases, w4, b4)
+};
+
+constexpr size_t kFwdSmem = sizeof(bf16) * (kTile * kLdX + kHid * kLdX + 2 * kHid * kLdH + kTile * kLdH);
+
+// Forward for n samples; out[i] = network output.  If z_out is set (training),
+// the pre-activations of the three hidden layers are stored, BF16 [3][n][128].
+__global__ void __launch_bounds__(kThreads) k_forward(Weights w, const bf16* x, int64_t n,
+                                                      float* out, bf16* z_out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16* Xs = reinterpret_cast<bf16*>(sm);
+    bf16* W1s = Xs + kTile * kLdX;
+    bf16* W2s = W1s + kHid * kLdX;
+    bf16* W3s = W2s + kHid * kLdH;
+    bf16* Hs = W3s + kHid * kLdH;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int rows = (n - base) < kTile ? (int)(n - base) : kTile;
+    copy_rows(W1s, kLdX, w.W1, kIn, kHid, kIn);
+    copy_rows(W2s, kLdH, w.W2, kHid, kHid, kHid);
+    copy_rows(W3s, kLdH, w.W3, kHid, kHid, kHid);
+    for (int i = threadIdx.x; i < kTile * (kIn / 8); i += kThreads) {
+        const int r = i / (kIn / 8), c = (i % (kIn / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r < rows) v = *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + c);
+        *reinterpret_cast<uint4*>(Xs + r * kLdX + c) = v;
+    }
+    __syncthreads();
+    const int m0 = warp * 16;
+    const int g = lane >> 2, cpair = (lane & 3) * 2;
+    float acc[16][4];
+    // hidden layers
+    for (int layer = 0; layer < 3; ++layer) {
+        zero<kHid>(acc);
+        if (layer == 0) gemm_nt<kIn, kHid>(acc, Xs, kLdX, m0, W1s, kLdX, lane);
+        else if (layer == 1) gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W2s, kLdH, lane);
+        else gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W3s, kLdH, lane);
+        const float* bias = w.p + (layer == 0 ? kOffB1 : layer == 1 ? kOffB2 : kOffB3);
+        if (layer < 2) __syncwarp();
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const int col = nt * 8 + cpair;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = m0 + g + h * 8;
+                const float z0 = acc[nt][2 * h] + bias[col], z1 = acc[nt][2 * h + 1] + bias[col + 1];
+                if (z_out && row < rows) {
+                    bf16* zp = z_out + ((size_t)layer * n + base + row) * kHid + col;
+                    *reinterpret_cast<__nv_bfloat162*>(zp) = __floats2bfloat162_rn(z0, z1);
+                }
+                if (layer < 2) {
+                    *reinterpret_cast<__nv_bfloat162*>(Hs + row * kLdH + col) =
+                        __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                } else {
+                    acc[nt][2 * h] = gelu(z0);
+                    acc[nt][2 * h + 1] = gelu(z1);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // output layer: dot with w4
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 16; ++nt) {
+        const int col = nt * 8 + cpair;
+        const float w0 = w.p[kOffW4 + col], w1 = w.p[kOffW4 + col + 1];
+        s0 += acc[nt][0] * w0 + acc[nt][1] * w1;
+        s1 += acc[nt][2] * w0 + acc[nt][3] * w1;
+    }
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+    if ((lane & 3) == 0) {
+        const float b4 = w.p[kOffB4];
+        if (m0 + g < rows) out[base + m0 + g] = s0 + b4;
+        if (m0 + g + 8 < rows) out[base + m0 + g + 8] = s1 + b4;
+    }
+}
+
+// Output layer backward.  loss = (1/n) sum_i v_i (out_i - t_i)^2 with sample
+// weights v_i (1 when weight is null).  dZ3 = dout w4 gelu'(Z3); per-CTA
+// partial sums of dL/dw4 and dL/db4.
+__global__ void __launch_bounds__(kThreads) k_back_out(const float* p, const float* out,
+                                                       const float* target, const float* weight,
+                                                       const bf16* z3, int64_t n, float inv_n,
+                                                       bf16* dz3, float* part /* [cta][kHid + 1] */) {
+    __shared__ float dout[kTile];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int rows = (n - base) < kTile ? (int)(n - base) : kTile;
+    if (threadIdx.x < kTile) {
+        float d = 0.f;
+        if (threadIdx.x < rows) {
+            const int64_t i = base + threadIdx.x;
+            d = 2.f * inv_n * (out[i] - target[i]);
+            if (weight) d *= weight[i];
+        }
+        dout[threadIdx.x] = d;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTile * kHid; i += kThreads) {
+        const int r = i / kHid, c = i % kHid;
+        float v = 0.f;
+        if (r < rows) {
+            const float z = __bfloat162float(z3[(size_t)(base + r) * kHid + c]);
+            v = dout[r] * p[kOffW4 + c] * gelu_grad(z);
+        }
+        dz3[(size_t)(base + r) * kHid + c] = __float2bfloat16_rn(v);
+    }
+    if (threadIdx.x < kHid) {
+        const int c = threadIdx.x;
+        float s = 0.f;
+        for (int r = 0; r < rows; ++r)
+            s += dout[r] * gelu(__bfloat162float(z3[(size_t)(base + r) * kHid + c]));
+        part[(size_t)blockIdx.x * (kHid + 1) + c] = s;
+    }
+    if (threadIdx.x == kHid) {
+        float s = 0.f;
+        for (int r = 0; r < rows; ++r) s += dout[r];
+        part[(size_t)blockIdx.x * (kHid + 1) + kHid] = s;
+    }
+}
+
+constexpr size_t back_smem(int K) {
+    return sizeof(bf16) * (kTile * kLdH + kTile * (K + 8) + kHid * (K + 8));
+}
+
+// Backward through one hidden layer l with input width K (32 for l = 1).
+//   gW[i][j] = sum_m dZ[m][i] H[m][j],  gb[i] = sum_m dZ[m][i]       (per CTA)
+//   dZprev[m][j] = (sum_i dZ[m][i] W[i][j]) gelu'(Zprev[m][j])        (l > 1)
+// H = gelu(Zprev) for l > 1, the input x for l = 1.
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_back_layer(const bf16* dz, const bf16* zprev,
+                                                         const bf16* x, const bf16* W, int64_t n,
+                                                         float* part_w /* [cta][128][K] */,
+                                                         float* part_b /* [cta][128] */,
+                                                         bf16* dzprev) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int ldk = K + 8;
+    bf16* Ds = reinterpret_cast<bf16*>(sm);        // [128][kLdH] dZ
+    bf16* Hs = Ds + kTile * kLdH;                  // [128][ldk]  layer input
+    bf16* Ws = Hs + kTile * ldk;                   // [128][ldk]  W (out x in)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const int rows = (n - base) < kTile ? (int)(n - base) : kTile;
+    for (int i = threadIdx.x; i < kTile * (kHid / 8); i += kThreads) {
+        const int r = i / (kHid / 8), c = (i % (kHid / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r < rows) v = *reinterpret_cast<const uint4*>(dz + (size_t)(base + r) * kHid + c);
+        *reinterpret_cast<uint4*>(Ds + r * kLdH + c) = v;
+    }
+    for (int i = threadIdx.x; i < kTile * K; i += kThreads) {
+        const int r = i / K, c = i % K;
+        float h = 0.f;
+        if (r < rows) {
+            if (zprev) h = gelu(__bfloat162float(zprev[(size_t)(base + r) * kHid + c]));
+            else h = __bfloat162float(x[(size_t)(base + r) * kIn + c]);
+        }
+        Hs[r * ldk + c] = __float2bfloat16_rn(h);
+    }
+    copy_rows(Ws, ldk, W, K, kHid, K);
+    __syncthreads();
+    const int i0 = warp * 16;
+    const int g = lane >> 2, cpair = (lane & 3) * 2;
+    {
+        float acc[K / 8][4];
+        zero<K>(acc);
+        gemm_tn<K>(acc, Ds, kLdH, i0, Hs, ldk, lane);
+        float* pw = part_w + (size_t)blockIdx.x * kHid * K;
+#pragma unroll
+        for (int nt = 0; nt < K / 8; ++nt) {
+            const int col = nt * 8 + cpair;
+            pw[(size_t)(i0 + g) * K + col] = acc[nt][0];
+            pw[(size_t)(i0 + g) * K + col + 1] = acc[nt][1];
+            pw[(size_t)(i0 + g + 8) * K + col] = acc[nt][2];
+            pw[(size_t)(i0 + g + 8) * K + col + 1] = acc[nt][3];
+        }
+    }
+    if (threadIdx.x < kHid) {
+        float s = 0.f;
+        for (int r = 0; r < rows; ++r) s += __bfloat162float(Ds[r * kLdH + threadIdx.x]);
+        part_b[(size_t)blockIdx.x * kHid + threadIdx.x] = s;
+    }
+    if (dzprev) {
+        float acc[16][4];
+        zero<kHid>(acc);
+        gemm_nn<kHid, kHid>(acc, Ds, kLdH, i0, Ws, ldk, lane);
+#pragma unroll
+        for (int nt = 0; nt < 16; ++nt) {
+            const int col = nt * 8 + cpair;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = i0 + g + h * 8;
+                if (row < rows) {
+                    const size_t o = (size_t)(base + row) * kHid + col;
+                    const float d0 = acc[nt][2 * h] * gelu_grad(__bfloat162float(zprev[o]));
+                    const float d1 = acc[nt][2 * h + 1] * gelu_grad(__bfloat162float(zprev[o + 1]));
+                    *reinterpret_cast<__nv_bfloat162*>(dzprev + o) = __floats2bfloat162_rn(d0, d1);
+                }
+            }
+        }
+    }
+}
+
+// Sum the per-CTA partials in CTA order into the gradient vector.
+__global__ void k_reduce_grad(const float* pw1, const float* pb1, const float* pw2,
+                              const float* pb2, const float* pw3, const float* pb3,
+                              const float* pout, int n_cta, float* grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kParams) return;
+    const float* src;
+    int stride, off;
+    if (i < kOffB1) { src = pw1; stride = kHid * kIn; off = i - kOffW1; }
+    else if (i < kOffW2) { src = pb1; stride = kHid; off = i - kOffB1; }
+    else if (i < kOffB2) { src = pw2; stride = kHid * kHid; off = i - kOffW2; }
+    else if (i < kOffW3) { src = pb2; stride = kHid; off = i - kOffB2; }
+    else if (i < kOffB3) { src = pw3; stride = kHid * kHid; off = i - kOffW3; }
+    else if (i < kOffW4) { src = pb3; stride = kHid; off = i - kOffB3; }
+    else { src = pout; stride = kHid + 1; off = i - kOffW4; }
+    float s = 0.f;
+    for (int c = 0; c < n_cta; ++c) s += src[(size_t)c * stride + off];
+    grad[i] = s;
+}
+
+__global__ void k_adam(float* p, float* m1, float* m2, const float* grad, float lr, float b1,
+                       float b2, float eps, float c1, float c2, bf16* W1, bf16* W2, bf16* W3) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kParams) return;
+    const float gi = grad[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float np = p[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    p[i] = np;
+    if (i < kOffB1) W1[i - kOffW1] = __float2bfloat16_rn(np);
+    else if (i >= kOffW2 && i < kOffB2) W2[i - kOffW2] = __float2bfloat16_rn(np);
+    else if (i >= kOffW3 && i < kOffB3) W3[i - kOffW3] = __float2bfloat16_rn(np);
+}
+
+__global__ void k_to_bf16(const float* src, int64_t n, bf16* dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__global__ void k_mse(const float* out, const float* target, const float* weight, int64_t n,
+                      double* acc) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const double d = (double)out[i] - target[i];
+        s += (weight ? (double)weight[i] : 1.0) * d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) acc[blockIdx.x] = red[0];
+}
+
+// batch gather for SGD: idx[i] -> rows of x (BF16), targets and weights
+__global__ void k_gather_batch_rows(const bf16* x, const float* t, const float* v,
+                                    const uint32_t* idx, int n, bf16* xb, float* tb, float* vb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * (kIn / 8)) return;
+    const int r = i / (kIn / 8), c = (i % (kIn / 8)) * 8;
+    const uint32_t s = idx[r];
+    *reinterpret_cast<uint4*>(xb + (size_t)r * kIn + c) =
+        *reinterpret_cast<const uint4*>(x + (size_t)s * kIn + c);
+    if (c == 0) {
+        tb[r] = t[s];
+        if (v) vb[r] = v[s];
+    }
+}
+
+// Sample weights of the training set: v_i = exp(gamma (t_i - max t)),
+// normalised to mean 1.  One CTA of 1024 threads: max, then the weights and
+// their sum, then the scaling.
+__global__ void __launch_bounds__(1024) k_train_weights(const float* t, int64_t n, float gamma,
+                                                        float* v) {
+    __shared__ float redf[1024];
+    __shared__ double redd[1024];
+    float mx = -3.0e38f;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) mx = fmaxf(mx, t[i]);
+    redf[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) redf[threadIdx.x] = fmaxf(redf[threadIdx.x], redf[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const float tmax = redf[0];
+    double sum = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        const float w = __expf(gamma * (t[i] - tmax));
+        v[i] = w;
+        sum += w;
+    }
+    redd[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) redd[threadIdx.x] += redd[threadIdx.x + o];
+        __syncthreads();
+    }
+    const float scale = (float)((double)n / redd[0]);
+    for (int64_t i = threadIdx.x; i < n; i += 1024) v[i] *= scale;
+}
+
+// counter-based random index (SplitMix64 of (seed, step, i))
+__device__ __forceinline__ uint64_t splitmix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void k_batch_indices(uint64_t seed, uint64_t step, int n, uint64_t n_total,
+                                uint32_t* idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) idx[i] = (uint32_t)(splitmix(seed ^ splitmix(step * 0x100000001b3ull + i)) % n_total);
+}
+
+
+// ---------------------------------------------------------------------------
+// The surrogate inside the row pipeline: after k_row wrote the unscattered
+// part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
+// adds sum_w (exp(net(x_w)) - eps) for every (event, voxel) and writes the
+// unit's partial forward sums.  Persistent CTAs; the weights stay in shared
+// memory; 128 (event, voxel) samples per pass (4 events x 32 voxels).
+struct SurrogateRowParams {
+    Weights w;
+    const Tile* tiles;
+    int tile_begin, tile_end;
+    const uint16_t* ev_bin;
+    const float* ev_e;
+    const int* q_pix;
+    const float* g8;       // [A][nq][8]
+    const double* cs_dummy;
+    float* rows;
+    int64_t row_base;
+    int row_stride;
+    const float* lam;      // may be null
+    int lam_stride;
+    float* ypart;
+    int64_t ypart_stride;
+    int n, A, B, W, nq, nqt;
+    float h, bin_w;
+    float mu_line[LMMEW_MAX_LINES];
+    float e_line[LMMEW_MAX_LINES];
+    const float* rho;
+};
+
+constexpr size_t kRowSurrogateSmem =
+    sizeof(bf16) * (kHid * kLdX + 2 * kHid * kLdH + kTile * kLdX + kTile * kLdH) +
+    sizeof(float) * kTile * 33;
+
+__global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowParams P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16* W1s = reinterpret_cast<bf16*>(sm);
+    bf16* W2s = W1s + kHid * kLdX;
+    bf16* W3s = W2s + kHid * kLdH;
+    bf16* Xs = W3s + kHid * kLdH;
+    bf16* Hs = Xs + kTile * kLdX;
+    float* St = reinterpret_cast<float*>(Hs + kTile * kLdH);   // [128 events][33]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    copy_rows(W1s, kLdX, P.w.W1, kIn, kHid, kIn);
+    copy_rows(W2s, kLdH, P.w.W2, kHid, kHid, kHid);
+    copy_rows(W3s, kLdH, P.w.W3, kHid, kHid, kHid);
+    const int n_tiles = P.tile_end - P.tile_begin;
+    const int n_units = n_tiles * P.nqt;
+    const int m0 = warp * 16, g = lane >> 2, cpair = (lane & 3) * 2;
+    const float half_det = 0.5f * P.B * P.bin_w;
+    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+        const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
+        const int qt = unit % P.nqt;
+        const int nq_here = min(32, P.nq - qt * 32);
+        __syncthreads();   // previous unit done with St / Xs
+        // start from the unscattered rows
+        for (int i = tid; i < kET * 32; i += kThreads) {
+            const int e = i >> 5, ql = i & 31;
+            St[e * 33 + ql] = (e < T.count && ql < nq_here)
+                                  ? P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql]
+                                  : 0.f;
+        }
+        const float th = 6.283185307179586f * T.a / P.A;
+        float ca, sa;
+        sincosf(th, &sa, &ca);
+        for (int c = 0; c < (T.count + 3) / 4; ++c) {
+            for (int wl = 0; wl < P.W; ++wl) {
+                __syncthreads();   // Xs free
+                if (tid < kTile) {
+                    const int e = c * 4 + (tid >> 5), ql = tid & 31;
+                    float f[kSurrogateIn];
+                    if (e < T.count && ql < nq_here) {
+                        const int q = qt * 32 + ql;
+                        const int pix = P.q_pix[q];
+                        const float xq = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
+                        const float yq = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
+                        const int b = P.ev_bin[T.begin + e];
+                        const float ub = -half_det + (b + 0.5f) * P.bin_w;
+                        surrogate_features(xq, yq, ca, sa, ub, P.ev_e[T.begin + e], wl,
+                                           P.e_line[wl], P.mu_line[wl],
+                                           P.g8 + ((size_t)T.a * P.nq + q) * 8, P.rho, P.n, P.h, f);
+                    } else {
+                        for (int k = 0; k < kSurrogateIn; ++k) f[k] = 0.f;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kSurrogateIn; k += 2)
+                        *reinterpret_cast<__nv_bfloat162*>(Xs + tid * kLdX + k) =
+                            __floats2bfloat162_rn(f[k], f[k + 1]);
+                }
+                __syncthreads();
+                float acc[16][4];
+                for (int layer = 0; layer < 3; ++layer) {
+                    zero<kHid>(acc);
+                    if (layer == 0) gemm_nt<kIn, kHid>(acc, Xs, kLdX, m0, W1s, kLdX, lane);
+                    else if (layer == 1) gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W2s, kLdH, lane);
+                    else gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W3s, kLdH, lane);
+                    const float* bias = P.w.p + (layer == 0 ? kOffB1 : layer == 1 ? kOffB2 : kOffB3);
+                    __syncwarp();
+#pragma unroll
+                    for (int nt = 0; nt < 16; ++nt) {
+                        const int col = nt * 8 + cpair;
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const float z0 = acc[nt][2 * hh] + bias[col];
+                            const float z1 = acc[nt][2 * hh + 1] + bias[col + 1];
+                            if (layer < 2) {
+                                *reinterpret_cast<__nv_bfloat162*>(Hs + (m0 + g + hh * 8) * kLdH + col) =
+                                    __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                            } else {
+                                acc[nt][2 * hh] = gelu(z0);
+                                acc[nt][2 * hh + 1] = gelu(z1);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt) {
+                    const int col = nt * 8 + cpair;
+                    const float w0 = P.w.p[kOffW4 + col], w1 = P.w.p[kOffW4 + col + 1];
+                    s0 += acc[nt][0] * w0 + acc[nt][1] * w1;
+                    s1 += acc[nt][2] * w0 + acc[nt][3] * w1;
+                }
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+                if ((lane & 3) == 0) {
+                    const float b4 = P.w.p[kOffB4];
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int srow = m0 + g + hh * 8;          // sample = event * 32 + voxel
+                        const int e = c * 4 + (srow >> 5), ql = srow & 31;
+                        if (e < T.count && ql < nq_here) {
+                            const float v = __expf((hh ? s1 : s0) + b4) - kSurrogateEps;
+                            St[e * 33 + ql] += v > 0.f ? v : 0.f;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < kET * 32; i += kThreads) {
+            const int e = i >> 5, ql = i & 31;
+            if (e < T.count && ql < nq_here)
+                P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] = St[e * 33 + ql];
+        }
+        if (P.lam && tid < T.count) {
+            const float* lam = P.lam + (size_t)T.r * P.lam_stride;
+            float s = 0.f;
+            for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], St[tid * 33 + ql], s);
+            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + tid - P.row_base)] = s;
+        }
+    }
+}
+
+}  // namespace mlp
+}  // namespace lmmew
+
+// ---------------------------------------------------------------------------
+// Host side: the surrogate object and its C ABI.
+using lmmew::mlp::bf16;
+namespace M = lmmew::mlp;
+
+struct lm_surrogate {
+    float* p = nullptr;      // FP32 master parameters [kParams]
+    float* m1 = nullptr;     // Adam moments
+    float* m2 = nullptr;
+    float* grad = nullptr;
+    bf16* W1 = nullptr;      // BF16 copies used by the tensor-core kernels
+    bf16* W2 = nullptr;
+    bf16* W3 = nullptr;
+    int64_t step = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace lmmew {
+
+const void* surrogate_weights(const lm_surrogate* s, void* out_weights) {
+    mlp::Weights* w = reinterpret_cast<mlp::Weights*>(out_weights);
+    w->W1 = s->W1;
+    w->W2 = s->W2;
+    w->W3 = s->W3;
+    w->p = s->p;
+    return out_weights;
+}
+
+int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
+    const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
+    if (n_units <= 0) return LMMEW_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_surrogate_rows,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mlp::kRowSurrogateSmem));
+        attr_set = true;
+    }
+    mlp::SurrogateRowParams P;
+    surrogate_weights(h->surrogate, &P.w);
+    P.tiles = L.tiles;
+    P.tile_begin = L.tile_begin;
+    P.tile_end = L.tile_end;
+    P.ev_bin = L.ev_bin;
+    P.ev_e = L.ev_e;
+    P.q_pix = h->d_q_pix;
+    P.g8 = h->d_g8;
+    P.cs_dummy = nullptr;
+    P.rows = L.rows;
+    P.row_base = L.row_base;
+    P.row_stride = L.row_stride;
+    P.lam = L.lam_v;
+    P.lam_stride = L.lam_stride;
+    P.ypart = L.ypart;
+    P.ypart_stride = L.ypart_stride;
+    P.n = h->mc.n;
+    P.A = h->mc.A;
+    P.B = h->mc.B;
+    P.W = h->mc.W;
+    P.nq = h->mc.nq;
+    P.nqt = h->mc.nqt;
+    P.h = (float)h->mc.h;
+    P.bin_w = (float)h->mc.bin_w;
+    for (int w = 0; w < LMMEW_MAX_LINES; ++w) {
+        P.mu_line[w] = (float)h->mu_line[w];
+        P.e_line[w] = (float)h->mc.line_e[w];
+    }
+    P.rho = h->d_rho;
+    const int grid = std::min(n_units, h->sm_count);
+    mlp::k_surrogate_rows<<<grid, mlp::kThreads, mlp::kRowSurrogateSmem, st>>>(P);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+namespace {
+
+int ensure_scratch(lm_surrogate* s, size_t bytes) {
+    if (s->scratch_bytes >= bytes) return LMMEW_OK;
+    LMMEW_CUDA(cudaDeviceSynchronize());
+    cudaFree(s->scratch);
+    s->scratch = nullptr;
+    s->scratch_bytes = 0;
+    if (cudaMalloc(&s->scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LMMEW_ERR_OOM, "cannot allocate surrogate scratch");
+    }
+    s->scratch_bytes = bytes;
+    return LMMEW_OK;
+}
+
+int refresh_bf16(lm_surrogate* s, cudaStream_t st) {
+    M::k_to_bf16<<<(M::kHid * M::kIn + 255) / 256, 256, 0, st>>>(s->p + M::kOffW1, M::kHid * M::kIn, s->W1);
+    M::k_to_bf16<<<(M::kHid * M::kHid + 255) / 256, 256, 0, st>>>(s->p + M::kOffW2, M::kHid * M::kHid, s->W2);
+    M::k_to_bf16<<<(M::kHid * M::kHid + 255) / 256, 256, 0, st>>>(s->p + M::kOffW3, M::kHid * M::kHid, s->W3);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+bool g_attrs = false;
+int set_attrs() {
+    if (g_attrs) return LMMEW_OK;
+    LMMEW_CUDA(cudaFuncSetAttribute(M::k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)M::kFwdSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(M::k_back_layer<M::kHid>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)M::back_smem(M::kHid)));
+    LMMEW_CUDA(cudaFuncSetAttribute(M::k_back_layer<M::kIn>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)M::back_smem(M::kIn)));
+    g_attrs = true;
+    return LMMEW_OK;
+}
+
+// Full-batch gradient of mean squared error over n samples of BF16 inputs
+// xb; grad (device) receives dL/dp.  Optionally the loss (host).
+int gradient(lm_surrogate* s, const bf16* xb, const float* t, const float* v, int64_t n,
+             double* loss, cudaStream_t st) {
+    const int64_t n_cta = (n + M::kTile - 1) / M::kTile;
+    const int64_t npad = n_cta * M::kTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+    const size_t o_out = take(sizeof(float) * npad);
+    const size_t o_z = take(sizeof(bf16) * 3 * npad * M::kHid);
+    const size_t o_d3 = take(sizeof(bf16) * npad * M::kHid);
+    const size_t o_d2 = take(sizeof(bf16) * npad * M::kHid);
+    const size_t o_d1 = take(sizeof(bf16) * npad * M::kHid);
+    const size_t o_pw1 = take(sizeof(float) * n_cta * M::kHid * M::kIn);
+    const size_t o_pb1 = take(sizeof(float) * n_cta * M::kHid);
+    const size_t o_pw2 = take(sizeof(float) * n_cta * M::kHid * M::kHid);
+    const size_t o_pb2 = take(sizeof(float) * n_cta * M::kHid);
+    const size_t o_pw3 = take(sizeof(float) * n_cta * M::kHid * M::kHid);
+    const size_t o_pb3 = take(sizeof(float) * n_cta * M::kHid);
+    const size_t o_po = take(sizeof(float) * n_cta * (M::kHid + 1));
+    const size_t o_mse = take(sizeof(double) * 256);
+    int rc = ensure_scratch(s, off);
+    if (rc != LMMEW_OK) return rc;
+    rc = set_attrs();
+    if (rc != LMMEW_OK) return rc;
+    char* base = (char*)s->scratch;
+    float* out = (float*)(base + o_out);
+    bf16* z = (bf16*)(base + o_z);
+    bf16* d3 = (bf16*)(base + o_d3);
+    bf16* d2 = (bf16*)(base + o_d2);
+    bf16* d1 = (bf16*)(base + o_d1);
+    M::Weights w{s->W1, s->W2, s->W3, s->p};
+    M::k_forward<<<(unsigned)n_cta, M::kThreads, M::kFwdSmem, st>>>(w, xb, n, out, z);
+    M::k_back_out<<<(unsigned)n_cta, M::kThreads, 0, st>>>(s->p, out, t, v, z + 2 * n * M::kHid, n,
+                                                          1.f / (float)n, d3, (float*)(base + o_po));
+    M::k_back_layer<M::kHid><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kHid), st>>>(
+        d3, z + n * M::kHid, nullptr, s->W3, n, (float*)(base + o_pw3), (float*)(base + o_pb3), d2);
+    M::k_back_layer<M::kHid><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kHid), st>>>(
+        d2, z, nullptr, s->W2, n, (float*)(base + o_pw2), (float*)(base + o_pb2), d1);
+    M::k_back_layer<M::kIn><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kIn), st>>>(
+        d1, nullptr, xb, s->W1, n, (float*)(base + o_pw1), (float*)(base + o_pb1), nullptr);
+    M::k_reduce_grad<<<(M::kParams + 255) / 256, 256, 0, st>>>(
+        (float*)(base + o_pw1), (float*)(base + o_pb1), (float*)(base + o_pw2), (float*)(base + o_pb2),
+        (float*)(base + o_pw3), (float*)(base + o_pb3), (float*)(base + o_po), (int)n_cta, s->grad);
+    LMMEW_CUDA(cudaGetLastError());
+    if (loss) {
+        double* mse = (double*)(base + o_mse);
+        M::k_mse<<<64, 256, 0, st>>>(out, t, v, n, mse);
+        double host[64];
+        LMMEW_CUDA(cudaMemcpyAsync(host, mse, sizeof(host), cudaMemcpyDeviceToHost, st));
+        LMMEW_CUDA(cudaStreamSynchronize(st));
+        double sum = 0.0;
+        for (int i = 0; i < 64; ++i) sum += host[i];
+        *loss = sum / (double)n;
+    }
+    return LMMEW_OK;
+}
+
+int to_bf16_inputs(lm_surrogate* s, const float* x, int64_t n, bf16** xb, size_t extra_off,
+                   cudaStream_t st) {
+    (void)s;
+    M::k_to_bf16<<<(unsigned)((n * M::kIn + 255) / 256), 256, 0, st>>>(x, n * M::kIn, *xb);
+    LMMEW_CUDA(cudaGetLastError());
+    (void)extra_off;
+    return LMMEW_OK;
+}
+
+uint64_t splitmix_host(uint64_t& state) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+}  // namespace lmmew
+
+using namespace lmmew;
+
+extern "C" {
+
+int lm_surrogate_param_count(void) { return M::kParams; }
+
+int lm_surrogate_create(uint64_t seed, lm_surrogate** out) {
+    if (!out) return set_error(LMMEW_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    lm_surrogate* s = new lm_surrogate();
+    const size_t pb = sizeof(float) * M::kParams;
+    if (cudaMalloc(&s->p, pb) != cudaSuccess || cudaMalloc(&s->m1, pb) != cudaSuccess ||
+        cudaMalloc(&s->m2, pb) != cudaSuccess || cudaMalloc(&s->grad, pb) != cudaSuccess ||
+        cudaMalloc(&s->W1, sizeof(bf16) * M::kHid * M::kIn) != cudaSuccess ||
+        cudaMalloc(&s->W2, sizeof(bf16) * M::kHid * M::kHid) != cudaSuccess ||
+        cudaMalloc(&s->W3, sizeof(bf16) * M::kHid * M::kHid) != cudaSuccess) {
+        cudaGetLastError();
+        lm_surrogate_destroy(s);
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the surrogate");
+    }
+    // Xavier-uniform weights, zero biases, output bias at a typical log value
+    std::vector<float> p(M::kParams, 0.f);
+    uint64_t st = seed;
+    auto uni = [&](float lim) {
+        const double u = (double)(splitmix_host(st) >> 11) * (1.0 / 9007199254740992.0);
+        return (float)((2.0 * u - 1.0) * lim);
+    };
+    const float l1 = std::sqrt(6.f / (M::kIn + M::kHid)), l2 = std::sqrt(6.f / (2 * M::kHid)),
+                l4 = std::sqrt(6.f / (M::kHid + 1));
+    for (int i = 0; i < M::kHid * M::kIn; ++i) p[M::kOffW1 + i] = uni(l1);
+    for (int i = 0; i < M::kHid * M::kHid; ++i) p[M::kOffW2 + i] = uni(l2);
+    for (int i = 0; i < M::kHid * M::kHid; ++i) p[M::kOffW3 + i] = uni(l2);
+    for (int i = 0; i < M::kHid; ++i) p[M::kOffW4 + i] = uni(l4);
+    p[M::kOffB4] = -10.f;
+    int rc = LMMEW_OK;
+    if (cudaMemcpy(s->p, p.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s->m1, 0, pb) != cudaSuccess || cudaMemset(s->m2, 0, pb) != cudaSuccess)
+        rc = set_error(LMMEW_ERR_CUDA, "surrogate initialisation");
+    if (rc == LMMEW_OK) rc = refresh_bf16(s, 0);
+    if (rc == LMMEW_OK && cudaDeviceSynchronize() != cudaSuccess)
+        rc = set_error(LMMEW_ERR_CUDA, "surrogate initialisation");
+    if (rc != LMMEW_OK) {
+        lm_surrogate_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return LMMEW_OK;
+}
+
+int lm_surrogate_destroy(lm_surrogate* s) {
+    if (!s) return LMMEW_OK;
+    cudaFree(s->p);
+    cudaFree(s->m1);
+    cudaFree(s->m2);
+    cudaFree(s->grad);
+    cudaFree(s->W1);
+    cudaFree(s->W2);
+    cudaFree(s->W3);
+    cudaFree(s->scratch);
+    delete s;
+    return LMMEW_OK;
+}
+
+int lm_surrogate_get_params(const lm_surrogate* s, float* host_out) {
+    if (!s || !host_out) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    LMMEW_CUDA(cudaMemcpy(host_out, s->p, sizeof(float) * M::kParams, cudaMemcpyDeviceToHost));
+    return LMMEW_OK;
+}
+
+int lm_surrogate_set_params(lm_surrogate* s, const float* host_in) {
+    if (!s || !host_in) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    LMMEW_CUDA(cudaMemcpy(s->p, host_in, sizeof(float) * M::kParams, cudaMemcpyHostToDevice));
+    int rc = refresh_bf16(s, 0);
+    if (rc != LMMEW_OK) return rc;
+    LMMEW_CUDA(cudaDeviceSynchronize());
+    return LMMEW_OK;
+}
+
+int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out, lm_stream stream) {
+    if (!s || (n > 0 && (!x || !out))) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0) return LMMEW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_scratch(s, sizeof(bf16) * (size_t)n * M::kIn + 256);
+    if (rc != LMMEW_OK) return rc;
+    rc = set_attrs();
+    if (rc != LMMEW_OK) return rc;
+    bf16* xb = (bf16*)s->scratch;
+    rc = to_bf16_inputs(s, x, n, &xb, 0, st);
+    if (rc != LMMEW_OK) return rc;
+    M::Weights w{s->W1, s->W2, s->W3, s->p};
+    M::k_forward<<<(unsigned)((n + M::kTile - 1) / M::kTile), M::kThreads, M::kFwdSmem, st>>>(
+        w, xb, n, out, nullptr);
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int lm_surrogate_gradient(lm_surrogate* s, const float* x, const float* target,
+                          const float* weight, int64_t n, float* grad_out, double* loss_out,
+                          lm_stream stream) {
+    if (!s || !x || !target || !grad_out || n <= 0)
+        return set_error(LMMEW_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    bf16* xb = nullptr;
+    if (cudaMalloc(&xb, sizeof(bf16) * (size_t)n * M::kIn) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the BF16 inputs");
+    }
+    int rc = to_bf16_inputs(s, x, n, &xb, 0, st);
+    if (rc == LMMEW_OK) rc = gradient(s, xb, target, weight, n, loss_out, st);
+    if (rc == LMMEW_OK &&
+        cudaMemcpyAsync(grad_out, s->grad, sizeof(float) * M::kParams, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess)
+        rc = set_error(LMMEW_ERR_CUDA, "gradient copy");
+    cudaStreamSynchronize(st);
+    cudaFree(xb);
+    return rc;
+}
+
+int lm_surrogate_train(lm_surrogate* s, const float* x, const float* target, int64_t n, int steps,
+                       int batch, float lr, float weight_power, uint64_t seed,
+                       double* loss_history, lm_stream stream) {
+    if (!s || !x || !target || n <= 0 || steps < 0 || batch < 1 || batch > (1 << 20) ||
+        !(lr > 0.f) || !(weight_power >= 0.f) || !(weight_power <= 64.f))
+        return set_error(LMMEW_ERR_INVALID_ARG, "bad argument");
+    if (n >= (int64_t(1) << 32)) return set_error(LMMEW_ERR_INVALID_ARG, "too many samples");
+    cudaStream_t st = (cudaStream_t)stream;
+    bf16* xall = nullptr;
+    bf16* xb = nullptr;
+    float* tb = nullptr;
+    uint32_t* idx = nullptr;
+    float* vall = nullptr;
+    float* vb = nullptr;
+    const bool weighted = weight_power > 0.f;
+    if (cudaMalloc(&xall, sizeof(bf16) * (size_t)n * M::kIn) != cudaSuccess ||
+        cudaMalloc(&xb, sizeof(bf16) * (size_t)batch * M::kIn) != cudaSuccess ||
+        cudaMalloc(&tb, sizeof(float) * batch) != cudaSuccess ||
+        cudaMalloc(&idx, sizeof(uint32_t) * batch) != cudaSuccess ||
+        (weighted && (cudaMalloc(&vall, sizeof(float) * (size_t)n) != cudaSuccess ||
+                      cudaMalloc(&vb, sizeof(float) * batch) != cudaSuccess))) {
+        cudaGetLastError();
+        cudaFree(xall); cudaFree(xb); cudaFree(tb); cudaFree(idx); cudaFree(vall); cudaFree(vb);
+        return set_error(LMMEW_ERR_OOM, "cannot allocate training buffers");
+    }
+    int rc = to_bf16_inputs(s, x, n, &xall, 0, st);
+    if (weighted) M::k_train_weights<<<1, 1024, 0, st>>>(target, n, weight_power, vall);
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int k = 0; k < steps && rc == LMMEW_OK; ++k) {
+        M::k_batch_indices<<<(batch + 255) / 256, 256, 0, st>>>(seed, (uint64_t)s->step, batch,
+                                                                (uint64_t)n, idx);
+        M::k_gather_batch_rows<<<(batch * (M::kIn / 8) + 255) / 256, 256, 0, st>>>(
+            xall, target, vall, idx, batch, xb, tb, vb);
+        double loss = 0.0;
+        rc = gradient(s, xb, tb, vb, batch, loss_history ? &loss : nullptr, st);
+        if (rc != LMMEW_OK) break;
+        if (loss_history) loss_history[k] = loss;
+        s->step += 1;
+        const float c1 = 1.f - std::pow(b1, (float)s->step), c2 = 1.f - std::pow(b2, (float)s->step);
+        M::k_adam<<<(M::kParams + 255) / 256, 256, 0, st>>>(s->p, s->m1, s->m2, s->grad, lr, b1, b2,
+                                                          eps, c1, c2, s->W1, s->W2, s->W3);
+        if (cudaGetLastError() != cudaSuccess) rc = set_error(LMMEW_ERR_CUDA, "training step");
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(xall); cudaFree(xb); cudaFree(tb); cudaFree(idx); cudaFree(vall); cudaFree(vb);
+    return rc;
+}
+
+}  // extern "C"

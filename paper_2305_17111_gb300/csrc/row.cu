@@ -103,6 +103,7 @@ struct RowParams {
     const float* lam;     // [nq] (per realisation, lam_stride apart) or null
     int lam_stride;
     int unit_order;       // 0: tile-major, 1: voxel-tile-major work units
+    int skip_scatter;     // 1: unscattered terms only
     float* rows;          // or null
     int64_t row_base;
     int row_stride;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         // of the tile: a contiguous run of chunks in this angle's point order;
         // every other term is an exact zero and is not evaluated
         int pc_lo = P.npc, pc_hi = 0;
-        for (int b = b_lo; b <= b_hi; ++b) {
+        for (int b = b_lo; b <= b_hi && !P.skip_scatter; ++b) {
             const int2 r = P.crange[(size_t)T.a * P.B + b];
             if (r.y > r.x) {
                 pc_lo = min(pc_lo, r.x);
@@ -534,6 +535,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     P.ev_e = L.ev_e;
     P.lam = L.lam_v;
     P.lam_stride = L.lam_stride;
+    P.skip_scatter = L.skip_scatter;
     P.unit_order = h->unit_order;
     P.rows = L.rows;
     P.row_base = L.row_base;
@@ -593,7 +595,9 @@ int row_kernel_occupancy(lm_handle* h) {
     return LMMEW_OK;
 }
 
-int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
+namespace {
+
+int launch_row_kernel(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
     if (n_units <= 0) return LMMEW_OK;
     const int prec = h->prec;
@@ -605,6 +609,24 @@ int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
+}
+
+}  // namespace
+
+// Rows of the scatter model in use: exact (both terms in k_row), none
+// (unscattered term only) or the learned surrogate (k_row writes the
+// unscattered rows, the network adds the scatter part and the forward sums).
+int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
+    if (h->scatter_model == LMMEW_SCATTER_EXACT) return launch_row_kernel(h, L, st);
+    RowLaunch U = L;
+    U.skip_scatter = 1;
+    if (h->scatter_model == LMMEW_SCATTER_NONE) return launch_row_kernel(h, U, st);
+    if (!L.rows)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED, "the surrogate scatter model needs stored rows");
+    U.lam_v = nullptr;
+    const int rc = launch_row_kernel(h, U, st);
+    if (rc != LMMEW_OK) return rc;
+    return launch_surrogate_rows(h, L, st);
 }
 
 // Reduced-precision tables from the FP32 ones: per (angle, voxel tile, point

@@ -139,6 +139,8 @@ __device__ double seg_integral(const float* rho, int n, double x0, double y0, do
     return acc * len;
 }
 
+__device__ __forceinline__ int n_of(const ModelConst& m) { return m.n; }
+
 __device__ __forceinline__ double det_integral(const float* rho, int n, double x, double y,
                                                double c, double s) {
     const double far = 4.0 * n + 8.0;
@@ -187,6 +189,21 @@ __global__ void k_gamma_det(ModelConst m, const float* rho, const double* cs_a,
     const double g = m.h * det_integral(rho, m.n, x, y, cs_a[2 * a], cs_a[2 * a + 1]);
     if (i < m.nq) g_q[(size_t)a * m.nq + i] = g;
     else g_p[(size_t)a * m.np + (i - m.nq)] = g;
+}
+
+// Path features of the learned scatter surrogate: for every (angle, voxel)
+// the line integral of rho (cm) from the voxel centre to the image edge along
+// the 8 directions theta_a + k pi/4.
+__global__ void k_gamma8(ModelConst m, const float* rho, const int* q_pix, float* g8) {
+    const int a = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m.nq) return;
+    const int pix = q_pix[q];
+    const double x = (pix % m.n) + 0.5, y = (pix / m.n) + 0.5;
+    for (int k = 0; k < 8; ++k) {
+        const double th = 2.0 * kPi * a / m.A + k * 0.25 * kPi;
+        g8[((size_t)a * m.nq + q) * 8 + k] = (float)(m.h * det_integral(rho, n_of(m), x, y, cos(th), sin(th)));
+    }
 }
 
 // Emission-to-scatter path integrals and distances (cm).
@@ -404,19 +421,22 @@ struct DevBuf {
 
 int subset_sensitivity(lm_handle* h, int parts, cudaStream_t st) {
     const ModelConst& m = h->mc;
-    if (h->sens_parts != parts) {
+    const int prim_only = h->scatter_model == 2 ? 1 : 0;
+    if (h->sens_parts != parts || h->sens_prim_only != prim_only) {
+        const double* src = prim_only ? h->d_sens_a_prim : h->d_sens_a;
         if (h->d_sens_sub) { cudaFree(h->d_sens_sub); h->d_sens_sub = nullptr; }
         const size_t bytes = sizeof(double) * (size_t)(parts + 1) * m.nq;
         if (cudaMalloc(&h->d_sens_sub, bytes) != cudaSuccess)
             return set_error(LMMEW_ERR_OOM, "cannot allocate subset sensitivities");
         dim3 g((m.nq + 255) / 256, parts);
-        k_sum_subsets<<<g, 256, 0, st>>>(h->d_sens_a, m.A, m.nq, parts, h->d_sens_sub);
+        k_sum_subsets<<<g, 256, 0, st>>>(src, m.A, m.nq, parts, h->d_sens_sub);
         ++h->launches;
-        k_sum_all<<<(m.nq + 255) / 256, 256, 0, st>>>(h->d_sens_a, m.A, m.nq,
+        k_sum_all<<<(m.nq + 255) / 256, 256, 0, st>>>(src, m.A, m.nq,
                                                        h->d_sens_sub + (size_t)parts * m.nq);
         ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
         h->sens_parts = parts;
+        h->sens_prim_only = prim_only;
     }
     return LMMEW_OK;
 }
@@ -525,6 +545,18 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     LMMEW_CUDA(cudaMemcpy(d_mu_line.p, mu_line_h, sizeof(mu_line_h), cudaMemcpyHostToDevice));
     const double* mu_line = (const double*)d_mu_line.p;
 
+    for (int w = 0; w < m.W; ++w) h->mu_line[w] = mu_line_h[w];
+    // surrogate path features and the density map they look up
+    if (cudaMalloc(&h->d_g8, sizeof(float) * (size_t)m.A * m.nq * 8) != cudaSuccess ||
+        cudaMalloc(&h->d_rho, sizeof(float) * (size_t)n * n) != cudaSuccess)
+        return set_error(LMMEW_ERR_OOM, "cannot allocate path features");
+    LMMEW_CUDA(cudaMemcpy(h->d_rho, rho, sizeof(float) * (size_t)n * n, cudaMemcpyDeviceToDevice));
+    {
+        dim3 g((m.nq + 127) / 128, m.A);
+        k_gamma8<<<g, 128>>>(m, rho, h->d_q_pix, h->d_g8);
+        LMMEW_CUDA(cudaGetLastError());
+    }
+
     // path integrals
     LMMEW_CUDA(cudaMalloc(&d_gq.p, sizeof(double) * (size_t)m.A * m.nq));
     LMMEW_CUDA(cudaMalloc(&d_gp.p, sizeof(double) * (size_t)m.A * np_alloc));
@@ -590,6 +622,11 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
                               h->d_sens_a);
         ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
+        // keep the unscattered part alone for the model without scatter
+        if (cudaMalloc(&h->d_sens_a_prim, sizeof(double) * (size_t)m.A * m.nq) != cudaSuccess)
+            return set_error(LMMEW_ERR_OOM, "cannot allocate primary sensitivity");
+        LMMEW_CUDA(cudaMemcpy(h->d_sens_a_prim, h->d_sens_a, sizeof(double) * (size_t)m.A * m.nq,
+                              cudaMemcpyDeviceToDevice));
     }
 
     // single-scatter paths

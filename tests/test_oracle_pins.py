@@ -387,3 +387,29 @@ def test_no_attenuation_map_gives_blur_only_rows():
                       * stats.norm.pdf(90.0, e0, 0.1 * math.sqrt(140 * e0) / FWHM)
                       for e0, al in ((82.0, 0.6), (154.0, 0.2), (270.0, 0.2)))
             assert row[iy, ix] == pytest.approx(ref, rel=1e-11)
+
+
+# ---------------------------------------------------------------- single-scatter split
+def test_scatter_line_rows_are_the_row_minus_the_scatter_free_row():
+    """row = primary + sum_w (single-scatter part of line w); the primary part
+    is the row of the same object with no scatter points at all, so the split
+    is pinned by a model built without the scatter grid."""
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.5, 1.5, (8, 8)).astype(np.float32)
+    full = small_model(rho=rho, scatter_n=4)
+    prim = small_model(rho=rho, scatter_n=0)
+    for a, b, e in ((0, 5, 80.0), (3, 6, 150.0), (6, 2, 265.0), (5, 9, 120.0)):
+        split = sum(full.scatter_line_row(a, b, e, w) for w in range(3))
+        np.testing.assert_allclose(prim.row(a, b, e) + split, full.row(a, b, e), rtol=1e-12,
+                                   atol=1e-300)
+        assert np.all(split >= 0) and np.any(split > 0)
+
+
+def test_scatter_line_row_scales_with_the_line_yield():
+    rho = np.ones((8, 8), dtype=np.float32)
+    m1 = small_model(rho=rho, scatter_n=4, yields=(0.6, 0.2, 0.2))
+    m2 = small_model(rho=rho, scatter_n=4, yields=(0.3, 0.2, 0.8))
+    np.testing.assert_allclose(m2.scatter_line_row(2, 6, 100.0, 0),
+                               0.5 * m1.scatter_line_row(2, 6, 100.0, 0), rtol=1e-13)
+    np.testing.assert_allclose(m2.scatter_line_row(2, 6, 240.0, 2),
+                               4.0 * m1.scatter_line_row(2, 6, 240.0, 2), rtol=1e-13)

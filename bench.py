@@ -47,7 +47,9 @@ def parse_args():
                     help="override the workload's event count (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the reduced-precision / batched forms section")
+                    help="skip the forms section (precision, batching, comparison, surrogate)")
+    ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
+                    help="comma-separated forms to measure")
     return ap.parse_args()
 
 
@@ -331,6 +333,90 @@ def run_precision_form(workload="lmmew_128", iters=None):
     return out
 
 
+def run_surrogate_form(workload="lmmew_64", n_samples=1_000_000, iters=None):
+    """The learned single-scatter surrogate against the exact FP32 path on the
+    same GPU.  The network is trained on samples of this object's own exact
+    single-scatter sums (drawn by lm_surrogate_sample, weighted by the
+    square root of the scatter mass); reported: sampling and training time,
+    the mass-weighted error of the scatter sum on held-out samples, seconds
+    per OSEM iteration, and the deviation of forward projections, images and
+    lesion activities from the exact path -- next to the same deviations of
+    the model without scatter, which is what the surrogate has to beat."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    ev = simulate_cached(sc)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    n_it = sc.n_iters if iters is None else iters
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    (x, t), t_sample = timed(lambda: model.surrogate_samples(dev, n_samples, seed=5))
+    sur = lm.Surrogate(5)
+    schedule = ((3000, 2e-3), (2000, 6e-4), (1000, 2e-4))
+
+    def train():
+        for steps, lr in schedule:
+            sur.train(x, t, steps=steps, batch=4096, lr=lr, seed=6 + steps, weight_power=0.5,
+                      record_loss=False)
+    _, t_train = timed(train)
+    xv, tv = model.surrogate_samples(dev, 100_000, seed=8)
+    sv = torch.exp(tv.double()) - 1e-8
+    pe = torch.clamp(torch.exp(sur.forward(xv).double()) - 1e-8, min=0)
+    mass_err = float(torch.sum(torch.abs(pe - sv)) / torch.sum(sv))
+    mass_ratio = float(torch.sum(pe) / torch.sum(sv))
+    del x, t
+
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
+    res = {}
+    for kind in ("exact", "surrogate", "none"):
+        model.set_scatter_model(kind, sur if kind == "surrogate" else None)
+        y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)
+        img = lam0.clone()
+        model.osem(dev, img, sc.n_subsets, 1)               # warm-up iteration
+        img = lam0.clone()
+        _, sec = timed(lambda: model.osem(dev, img, sc.n_subsets, n_it))
+        res[kind] = {"y": y, "img": img.cpu().numpy().astype(np.float64), "s_per_iter": sec / n_it}
+    model.set_scatter_model("exact")
+    ex = res["exact"]
+    roi_ex = roi_sums(ex["img"], ph.lesion_masks)
+    out = {"workload": f"{sc.name}: {sc.n}x{sc.n}, {sc.n_angles} angles, {sc.n_bins} bins, "
+                       f"{sc.scatter_n}x{sc.scatter_n} scatter grid, {len(ev)} events, "
+                       f"{sc.n_subsets} subsets x {n_it} iterations",
+           "training": {"samples": n_samples, "sample_s": t_sample, "train_s": t_train,
+                        "steps": sum(k for k, _ in schedule), "batch": 4096,
+                        "loss_weight": "(S + 1e-8)^0.5",
+                        "heldout_mass_rel_err": mass_err, "heldout_mass_ratio": mass_ratio},
+           "exact": {"s_per_iter": ex["s_per_iter"], "roi_activity": roi_ex}}
+    for kind in ("surrogate", "none"):
+        r = res[kind]
+        roi = roi_sums(r["img"], ph.lesion_masks)
+        out[kind] = {"s_per_iter": r["s_per_iter"],
+                     "speedup_vs_exact": ex["s_per_iter"] / r["s_per_iter"],
+                     "fwd_rel_l2_vs_exact": float(np.linalg.norm(r["y"] - ex["y"])
+                                                  / np.linalg.norm(ex["y"])),
+                     "image_rel_l2_vs_exact": float(np.linalg.norm(r["img"] - ex["img"])
+                                                    / np.linalg.norm(ex["img"])),
+                     "roi_rel_dev_vs_exact": [abs(a - b) / b for a, b in zip(roi, roi_ex)]}
+    sur.close()
+    model.close()
+    return out
+
+
 def run_batch_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, iters=None, repeats=3,
                    seed=3):
     """Many noise realisations with uneven event counts in one batched call
@@ -521,8 +607,9 @@ def run_gpu(args, rank, local_rank, world):
     }
     if world == 1 and not args.no_forms and not args.events:
         model.close()
-        line["forms"] = {"precision": run_precision_form(), "batching": run_batch_form(),
-                         "comparison": run_comparison_form()}
+        runners = {"precision": run_precision_form, "batching": run_batch_form,
+                   "comparison": run_comparison_form, "surrogate": run_surrogate_form}
+        line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

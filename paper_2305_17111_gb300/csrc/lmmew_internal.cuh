@@ -18,6 +18,7 @@ constexpr int kET = 128;    // events per tile (4 per lane, 32 lanes)
 constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
 constexpr int kRowThreads = 256;
 constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path
+constexpr float kPosHuge = 1.0e30f;    // its negative (square-root form of the tables)
 // Collimator probabilities below this are stored as exactly 0: a term that
 // small is below FP32 resolution of any row it could enter.
 constexpr double kCollimatorFloor = 1e-20;
@@ -68,7 +69,7 @@ struct lm_handle {
     int n_subsets_default;
     // geometry on the device
     int* d_q_pix = nullptr;        // [nq] pixel index of each support voxel
-    float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  lh, nk, -E'
+    float* d_tab = nullptr;        // [A][nqt][npc][3][W][kQT][kPC]  nlh, sr, m (square-root form)
     float* d_cs = nullptr;         // [A][npc][B][kCPad] collimator prob. of scatter points,
                                    // points in each angle's ascending-u order
     int2* d_crange = nullptr;      // [A][B] chunks with non-zero probability: [first, last+1)

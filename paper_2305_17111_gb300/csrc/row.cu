@@ -14,12 +14,15 @@
 // cp.async.bulk + mbarrier, double buffered).  Each of the 8 warps owns 4
 // voxels; each lane owns 4 events, so a table entry read from shared memory
 // is a broadcast that feeds 4 events, and the collimator value of an
-// (event, point) pair feeds every voxel and line.  Per scatter term:
-//   d = E_hat - E'; arg = (nk d) d + lh; term = ex2(arg)   (MUFU)
-// with the FP32 arithmetic on packed pairs of scatter points (f32x2), so one
-// instruction covers two terms.
-// with lh = log2(alpha s / (sqrt(2 pi) sigma_E(E'))) and nk = -log2(e) /
-// (2 sigma_E(E')^2) precomputed in FP64.  Sums are hierarchical: per stage,
+// (event, point) pair feeds every voxel and line.  Per scatter term, in the
+// square-root form of the energy Gaussian:
+//   d = sr E_hat + m;  arg = d d + nlh;  term = ex2(-arg)   (FMA, FMA, MUFU)
+// with sr = sqrt(log2(e) / 2) / sigma_E(E'), m = -sr E' and
+// nlh = -log2(alpha s / (sqrt(2 pi) sigma_E(E'))) precomputed in FP64, so a
+// term costs two FMA-pipe operations before its exponential (plus the line
+// sum and the collimator product, one more per term amortised) instead of
+// three; the FP32 arithmetic runs on packed pairs of scatter points (f32x2),
+// one instruction covering two terms.  Sums are hierarchical: per stage,
 // per unit, then across warps in a fixed order, so results are
 // deterministic.  Every mbarrier wait is bounded in time; a wait that runs
 // out sets the status word and the CTA stops cleanly.
@@ -87,7 +90,7 @@ __device__ __forceinline__ float fast_ex2(float x) {
 }
 
 struct RowParams {
-    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: lh, nk, -E'
+    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: nlh, sr, m
     const float* tabh;    // reduced-precision form: [A][nqt][npc]{-E' f32 [W][kQT][kPC],
                           //   (lh - base, nk) halves [W][kQT][kPC/4][8]}
     const float* tscale;  // [A][nqt][npc] 2^base of each block (reduced precision)
@@ -141,15 +144,13 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-// ex2 of both halves of the exponent pair lh + nk d^2 with d = e_hat - E'
-// (the table holds -E'), for one event and two scatter points.
-__device__ __forceinline__ f32x2 term2(f32x2 eh2, f32x2 neg_ep, f32x2 nk, f32x2 lh) {
-    const f32x2 d = add2(eh2, neg_ep);
-    const f32x2 t = mul2(nk, d);
-    const f32x2 a = fma2(t, d, lh);
+// 2^-(d^2 + nlh) with d = sr e_hat + m, for one event and two scatter points.
+__device__ __forceinline__ f32x2 term2(f32x2 eh2, f32x2 sr, f32x2 m, f32x2 nlh) {
+    const f32x2 d = fma2(sr, eh2, m);
+    const f32x2 a = fma2(d, d, nlh);
     float a0, a1;
     upk(a, a0, a1);
-    return pk(fast_ex2(a0), fast_ex2(a1));
+    return pk(fast_ex2(-a0), fast_ex2(-a1));
 }
 
 // Packed half-precision arithmetic for the reduced-precision form: PREC 1 =
@@ -243,16 +244,16 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
             f32x2 inA[4], inB[4];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                const float4 lh = *reinterpret_cast<const float4*>(tq + (0 * W + w) * kQT * kPC);
-                const float4 nk = *reinterpret_cast<const float4*>(tq + (1 * W + w) * kQT * kPC);
-                const float4 ne = *reinterpret_cast<const float4*>(tq + (2 * W + w) * kQT * kPC);
-                const f32x2 lhA = pk(lh.x, lh.y), lhB = pk(lh.z, lh.w);
-                const f32x2 nkA = pk(nk.x, nk.y), nkB = pk(nk.z, nk.w);
-                const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
+                const float4 nl = *reinterpret_cast<const float4*>(tq + (0 * W + w) * kQT * kPC);
+                const float4 sr = *reinterpret_cast<const float4*>(tq + (1 * W + w) * kQT * kPC);
+                const float4 mm = *reinterpret_cast<const float4*>(tq + (2 * W + w) * kQT * kPC);
+                const f32x2 nlA = pk(nl.x, nl.y), nlB = pk(nl.z, nl.w);
+                const f32x2 srA = pk(sr.x, sr.y), srB = pk(sr.z, sr.w);
+                const f32x2 mA = pk(mm.x, mm.y), mB = pk(mm.z, mm.w);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const f32x2 tA = term2(eh2[k], neA, nkA, lhA);
-                    const f32x2 tB = term2(eh2[k], neB, nkB, lhB);
+                    const f32x2 tA = term2(eh2[k], srA, mA, nlA);
+                    const f32x2 tB = term2(eh2[k], srB, mB, nlB);
                     inA[k] = (w == 0) ? tA : add2(inA[k], tA);
                     inB[k] = (w == 0) ? tB : add2(inB[k], tB);
                 }
@@ -637,12 +638,13 @@ __global__ void __launch_bounds__(256) k_half_tables(const float* tab, int W, fl
                                                      float* tscale) {
     const size_t blk = blockIdx.x;
     const int n = W * kQT * kPC;
+    // the FP32 tables hold (nlh, sr, m): lh = -nlh, nk = -sr^2, -E' = m / sr
     const float* src = tab + blk * (size_t)(3 * n);
     float* dst = tabh + blk * (size_t)(2 * n);
     __shared__ float red[256];
     float mx = -3.0e38f;
     for (int i = threadIdx.x; i < n; i += 256) {
-        const float v = src[i];
+        const float v = -src[i];
         if (v > -1.0e29f) mx = fmaxf(mx, v);
     }
     red[threadIdx.x] = mx;
@@ -653,12 +655,15 @@ __global__ void __launch_bounds__(256) k_half_tables(const float* tab, int W, fl
     }
     const float base = red[0] > -1.0e29f ? red[0] : 0.f;
     if (threadIdx.x == 0) tscale[blk] = red[0] > -1.0e29f ? exp2f(base) : 0.f;
-    for (int i = threadIdx.x; i < n; i += 256) dst[i] = src[2 * n + i];   // -E'
+    for (int i = threadIdx.x; i < n; i += 256) {   // -E'
+        const float sr = src[n + i];
+        dst[i] = sr > 0.f ? src[2 * n + i] / sr : 0.f;
+    }
     uint16_t* hl = reinterpret_cast<uint16_t*>(dst + n);
     // layout [W][kQT][kPC/4][8]: lh of 4 points, then nk of the same 4 points
     for (int i = threadIdx.x; i < n; i += 256) {
         const int wq = i / kPC, p = i % kPC, pq = p / 4, pl = p % 4;
-        const float lh = src[i], nk = src[n + i];
+        const float lh = -src[i], nk = -src[n + i] * src[n + i];
         const float rel = lh > -1.0e29f ? lh - base : -1.0e30f;
         uint16_t a, b;
         if (PREC == 1) {

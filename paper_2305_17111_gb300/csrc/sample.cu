@@ -72,11 +72,12 @@ __global__ void k_sample(const SampleParams P) {
         const float c = P.cs[(((size_t)a * P.npc + pc) * P.B + b) * kCPad + sl];
         if (c == 0.f) continue;
         const float* tb = P.tab + (((size_t)a * P.nqt + qt) * P.npc + pc) * blk;
-        const float lh = tb[((0 * P.W + w) * kQT + ql) * kPC + sl];
-        const float nk = tb[((1 * P.W + w) * kQT + ql) * kPC + sl];
-        const float ne = tb[((2 * P.W + w) * kQT + ql) * kPC + sl];
-        const double d = (double)eh + ne;
-        s += (double)c * exp2((double)lh + (double)nk * d * d);
+        // square-root form: alpha s(P) g(e_hat; E') = 2^-(d^2 + nlh), d = sr e_hat + m
+        const float nlh = tb[((0 * P.W + w) * kQT + ql) * kPC + sl];
+        const float sr = tb[((1 * P.W + w) * kQT + ql) * kPC + sl];
+        const float mm = tb[((2 * P.W + w) * kQT + ql) * kPC + sl];
+        const double d = (double)sr * eh + mm;
+        s += (double)c * exp2(-(d * d + (double)nlh));
     }
     P.t[i] = (float)log(s + (double)kSurrogateEps);
 }

@@ -323,9 +323,12 @@ __global__ void k_primary(ModelConst m, const double* cs_a, const int* q_pix, co
 }
 
 // Single-scatter paths.  One warp per (angle, voxel), lanes over scatter
-// points.  Writes the FP32 hot-kernel tables
-//   lh = log2(alpha_w s(P) / (sqrt(2 pi) sigma_E(E'))), nk = -log2(e)/(2 sigma_E(E')^2), -E'
-// and adds sum_w alpha_w sum_p s(P) Prob(detector) Prob(window | E') to the
+// points.  Writes the FP32 hot-kernel tables in the square-root form of the
+// energy Gaussian, alpha_w s(P) g(E_hat; E') = 2^-(d^2 + nlh) with
+//   d = sr E_hat + m,  sr = sqrt(log2(e) / 2) / sigma_E(E'),  m = -sr E',
+//   nlh = -log2(alpha_w s(P) / (sqrt(2 pi) sigma_E(E')))
+// (sr and m rounded once from FP64, so sr E_hat + m in one FMA carries the
+// same error as E_hat - E' with E' rounded), and adds sum_w alpha_w sum_p s(P) Prob(detector) Prob(window | E') to the
 // per-angle sensitivity.
 __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_a,
                                                  const int* q_pix, const int* p_cell,
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
         float* base = tab + (((size_t)a * m.nqt + qt) * m.npc + pc) * (size_t)(3 * m.W * kQT * kPC);
         if (r >= m.np) {
             for (int w = 0; w < m.W; ++w) {
-                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kNegHuge;
+                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kPosHuge;
                 base[((1 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
                 base[((2 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
             }
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
         const int cell = p_cell[p];
         if (cell == own_cell) {   // the emission voxel's own cell carries no path
             for (int w = 0; w < m.W; ++w) {
-                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kNegHuge;
+                base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kPosHuge;
                 base[((1 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
                 base[((2 * m.W + w) * kQT + ql) * kPC + lane] = 0.f;
             }
@@ -385,9 +388,10 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
                                 kn_shape(e0, cos_t) / m.kn_norm[w];
             const double sg = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
             const double wgt = m.alpha[w] * path / (sqrt(2.0 * kPi) * sg);
-            base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)log2(wgt) : kNegHuge;
-            base[((1 * m.W + w) * kQT + ql) * kPC + lane] = (float)(-kLog2e / (2.0 * sg * sg));
-            base[((2 * m.W + w) * kQT + ql) * kPC + lane] = (float)(-e1);
+            const double sr = sqrt(0.5 * kLog2e) / sg;
+            base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-log2(wgt)) : kPosHuge;
+            base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
+            base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
             if (path > 0.0) sens += m.alpha[w] * path * on_det * window_mass(m, e1);
         }
     }

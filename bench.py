@@ -131,11 +131,11 @@ def measured_peaks():
         return None
 
 
-# DRAM bytes (read + write) per launch of the current k_row revision on this
-# workload, from the one-pass ncu capture summarised in
-# profiles/k_row_lmmew64.md.  Set to None whenever k_row changes until the
-# counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# current k_row revision (square-root form) on this workload: the mean over
+# the 8 launches of one OSEM iteration in a one-pass ncu capture of the full
+# workload.  Emptied whenever k_row changes until the counters are taken again.
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 499_951_136}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.

@@ -19,9 +19,13 @@ constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
 constexpr int kRowThreads = 256;
 constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path
 constexpr float kPosHuge = 1.0e30f;    // its negative (square-root form of the tables)
-// Collimator probabilities below this are stored as exactly 0: a term that
-// small is below FP32 resolution of any row it could enter.
-constexpr double kCollimatorFloor = 1e-20;
+// Collimator probabilities of scatter points below this are stored as exactly
+// 0, and the row kernel never visits a run of points that are all 0 for the
+// tile's bins.  A dropped term is below 1e-12 of its own path weight, so an
+// event's forward value moves by less than 1e-9 relative (the path that made
+// the event enters with a collimator factor of order 1), far below the FP32
+// resolution of the sums.  Voxel (unscattered) probabilities keep every value.
+constexpr double kCollimatorFloor = 1e-12;
 
 // Status bits written by kernels into the handle's device status word.
 constexpr int kStatusOutOfRange = 1;

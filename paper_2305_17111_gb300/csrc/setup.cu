@@ -254,8 +254,8 @@ __global__ void k_point_order(ModelConst m, const double* cs_a, const int* p_cel
 }
 
 // Collimator bin probabilities: voxels [A][B][nq], scatter points [A][npc][B][kCPad]
-// with the points of each angle in the order of k_point_order.  Probabilities
-// below kCollimatorFloor are stored as 0 (no row can resolve them in FP32).
+// with the points of each angle in the order of k_point_order.  Scatter-point
+// probabilities below kCollimatorFloor are stored as 0.
 __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
                              const int* p_cell, const int* inv, float* cv, float* csp) {
     const int a = blockIdx.z, b = blockIdx.y;

@@ -225,29 +225,71 @@ def _simulate_chunk(sc: Scenario, rho, act_cdf, marcher, rng, m, z_plane):
                      q[sel].astype(np.int32), w[sel].astype(np.uint8), ~prim[sel])
 
 
+CHUNK_PHOTONS = 200_000       # candidate decays per chunk
+
+
+def _chunk(args):
+    """Chunk ``i`` of a simulation: its own Philox stream (the seed's stream
+    jumped i times), so the event list depends on the seed alone, however
+    the chunks are spread over processes."""
+    sc, act, seed, i = args
+    ph = sc.make_phantom()
+    cdf = np.cumsum(act)
+    cdf = cdf / cdf[-1]
+    marcher = _Marcher(sc, ph.rho)
+    z_plane = np.array([_kn_plane_integral(e) for e in sc.line_keV])
+    rng = np.random.Generator(np.random.Philox(seed).jumped(i))
+    return _simulate_chunk(sc, ph.rho, cdf, marcher, rng, CHUNK_PHOTONS, z_plane)
+
+
+def _workers() -> int:
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(n, 32))
+
+
 def simulate(sc: Scenario, n_events: int | None = None, seed: int | None = None,
-             activity: np.ndarray | None = None) -> EventList:
-    """Draw ``n_events`` list-mode events (default: the scenario's count/seed)."""
+             activity: np.ndarray | None = None, workers: int | None = None) -> EventList:
+    """Draw ``n_events`` list-mode events (default: the scenario's count/seed).
+
+    Chunks of CHUNK_PHOTONS candidate decays are simulated in order and
+    concatenated; with more than a few chunks they run in a process pool
+    (started with spawn), which changes nothing in the result."""
     n_events = sc.n_events if n_events is None else int(n_events)
     seed = sc.seed if seed is None else int(seed)
     ph = sc.make_phantom()
     act = ph.activity if activity is None else np.asarray(activity, dtype=np.float64)
     act = np.asarray(act, dtype=np.float64).reshape(-1)
-    cdf = np.cumsum(act)
-    cdf = cdf / cdf[-1]
-    marcher = _Marcher(sc, ph.rho)
-    z_plane = np.array([_kn_plane_integral(e) for e in sc.line_keV])
-    rng = np.random.Generator(np.random.Philox(seed))
-    parts, total = [], 0
+    parts = [_chunk((sc, act, seed, 0))]
+    total = len(parts[0])
+    i = 1
+    if total < n_events:
+        per_chunk = max(total, 1)
+        n_more = int(np.ceil((n_events - total) / per_chunk * 1.05)) + 1
+        workers = _workers() if workers is None else int(workers)
+        if n_more >= 3 and workers > 1:
+            import multiprocessing as mp
+            with mp.get_context("spawn").Pool(min(workers, n_more)) as pool:
+                more = pool.map(_chunk, [(sc, act, seed, i + k) for k in range(n_more)])
+            parts += more
+            total += sum(len(p) for p in more)
+            i += n_more
     while total < n_events:
-        need = n_events - total
-        m = int(min(max(4 * need, 4096), 200_000))
-        ev = _simulate_chunk(sc, ph.rho, cdf, marcher, rng, m, z_plane)
+        ev = _chunk((sc, act, seed, i))
         parts.append(ev)
         total += len(ev)
-    out = EventList(*[np.concatenate([getattr(p, f) for p in parts])[:n_events]
-                      for f in ("angle", "bin", "energy", "origin", "line", "scattered")])
-    return out
+        i += 1
+    # keep whole chunks in order, then cut: the result depends only on the seed
+    kept, cum = [], 0
+    for p in parts:
+        kept.append(p)
+        cum += len(p)
+        if cum >= n_events:
+            break
+    return EventList(*[np.concatenate([getattr(p, f) for p in kept])[:n_events]
+                       for f in ("angle", "bin", "energy", "origin", "line", "scattered")])
 
 
 def _cache_dir() -> str:
@@ -260,7 +302,7 @@ def simulate_cached(sc: Scenario, n_events: int | None = None,
     """``simulate`` with an on-disk cache keyed by the scenario, count and seed."""
     n_events = sc.n_events if n_events is None else int(n_events)
     seed = sc.seed if seed is None else int(seed)
-    key = hashlib.sha1(repr((sc, n_events, seed, "mc-v1")).encode()).hexdigest()[:16]
+    key = hashlib.sha1(repr((sc, n_events, seed, "mc-v2")).encode()).hexdigest()[:16]
     path = os.path.join(_cache_dir(), f"events_{sc.name}_{n_events}_{seed}_{key}.npz")
     if os.path.exists(path):
         z = np.load(path)

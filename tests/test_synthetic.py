@@ -1,0 +1,35 @@
+"""The seeded input generators (CPU): the Monte-Carlo event list depends on
+the seed alone -- not on how its chunks are spread over processes -- and has
+the paper's structure (photopeaks plus a Compton continuum inside the window)."""
+from __future__ import annotations
+
+import numpy as np
+
+from synthetic import preset, simulate
+
+
+def test_event_list_independent_of_worker_count():
+    sc = preset("lmmew_32")
+    a = simulate(sc, n_events=130_000, seed=3, workers=1)
+    b = simulate(sc, n_events=130_000, seed=3, workers=3)
+    for f in ("angle", "bin", "energy", "origin", "line", "scattered"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+    c = simulate(sc, n_events=130_000, seed=4, workers=1)
+    assert not np.array_equal(a.energy, c.energy)
+
+
+def test_event_ranges_and_spectrum():
+    sc = preset("lmmew_32")
+    ev = simulate(sc, n_events=40_000, seed=5)
+    assert len(ev) == 40_000
+    assert ev.angle.max() < sc.n_angles and ev.bin.max() < sc.n_bins
+    assert ev.energy.min() >= 50.0 and ev.energy.max() < 300.0
+    # primaries cluster at their line (within 3 FWHM); scattered events lose energy
+    prim = ~ev.scattered
+    e0 = np.asarray(sc.line_keV)[ev.line[prim]]
+    fwhm = 0.10 * np.sqrt(140.0 * e0)
+    assert np.mean(np.abs(ev.energy[prim] - e0) < 3 * fwhm) > 0.99
+    sca = ev.scattered
+    e0s = np.asarray(sc.line_keV)[ev.line[sca]]
+    assert np.mean(ev.energy[sca] < e0s + 3 * 0.10 * np.sqrt(140.0 * e0s)) > 0.99
+    assert 0.05 < sca.mean() < 0.8

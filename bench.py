@@ -333,26 +333,37 @@ def run_precision_form(workload="lmmew_128", iters=None):
     return out
 
 
-def run_surrogate_form(workload="lmmew_64", n_samples=1_000_000, iters=None):
+def _object_events(args):
+    """Events of one random training object (a process-pool task)."""
+    k, seed, workload, n_events = args
+    from synthetic import preset, random_water_bone_object, simulate
+    sc = preset(workload).with_(phantom=random_water_bone_object(seed, k))
+    return simulate(sc, n_events=n_events, seed=seed * 1000 + k, workers=1)
+
+
+def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_000,
+                       object_events=20_000, iters=2, seed=5):
     """The learned single-scatter surrogate against the exact FP32 path on the
-    same GPU.  The network is trained on samples of this object's own exact
-    single-scatter sums (drawn by lm_surrogate_sample, weighted by the
-    square root of the scatter mass); reported: sampling and training time,
-    the mass-weighted error of the scatter sum on held-out samples, seconds
-    per OSEM iteration, and the deviation of forward projections, images and
-    lesion activities from the exact path -- next to the same deviations of
-    the model without scatter, which is what the surrogate has to beat."""
+    same GPU, on the 128 x 128, 2 M-event workload.  The network is trained
+    on 10^7 exact single-scatter sums drawn (lm_surrogate_sample) from eight
+    random water/bone objects on the same grid -- never from the workload's
+    own object -- with the loss weighted by the square root of the scatter
+    mass.  Reported: sampling and training time, the mass-weighted error of
+    the scatter sum on samples of the workload's object, seconds per OSEM
+    iteration and network throughput, and the deviation of forward
+    projections, images and lesion activities from the exact path -- next to
+    the same deviations of the model without scatter, which is what the
+    surrogate has to beat."""
+    import multiprocessing as mp
+
     import numpy as np
     import torch
 
     import paper_2305_17111_gb300 as lm
-    from synthetic import preset, simulate_cached
+    from synthetic import preset, random_water_bone_object, simulate_cached
     sc = preset(workload)
     ph = sc.make_phantom()
     ev = simulate_cached(sc)
-    model = lm.Model.from_scenario(sc, ph.rho)
-    dev = lm.DeviceEvents.from_list(ev)
-    n_it = sc.n_iters if iters is None else iters
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -364,43 +375,68 @@ def run_surrogate_form(workload="lmmew_64", n_samples=1_000_000, iters=None):
         torch.cuda.synchronize()
         return r, e0.elapsed_time(e1) / 1e3
 
-    (x, t), t_sample = timed(lambda: model.surrogate_samples(dev, n_samples, seed=5))
-    sur = lm.Surrogate(5)
-    schedule = ((3000, 2e-3), (2000, 6e-4), (1000, 2e-4))
+    with mp.get_context("spawn").Pool(min(n_objects, os.cpu_count() or 1)) as pool:
+        obj_events = pool.map(_object_events,
+                              [(k, seed, workload, object_events) for k in range(n_objects)])
+    xs, ts, t_sample = [], [], 0.0
+    for k in range(n_objects):
+        sck = sc.with_(phantom=random_water_bone_object(seed, k))
+        mk = lm.Model.from_scenario(sck, sck.make_phantom().rho)
+        dk = lm.DeviceEvents.from_list(obj_events[k])
+        (x, t), dt = timed(lambda: mk.surrogate_samples(dk, n_samples // n_objects,
+                                                        seed=seed * 100 + k))
+        xs.append(x)
+        ts.append(t)
+        t_sample += dt
+        mk.close()
+        del dk
+    x, t = torch.cat(xs), torch.cat(ts)
+    del xs, ts
+    sur = lm.Surrogate(seed)
+    batch = 16384
+    schedule = ((2000, 2e-3), (1500, 6e-4), (500, 2e-4))
 
     def train():
         for steps, lr in schedule:
-            sur.train(x, t, steps=steps, batch=4096, lr=lr, seed=6 + steps, weight_power=0.5,
-                      record_loss=False)
+            sur.train(x, t, steps=steps, batch=batch, lr=lr, seed=seed * 10 + steps,
+                      weight_power=0.5, record_loss=False)
     _, t_train = timed(train)
-    xv, tv = model.surrogate_samples(dev, 100_000, seed=8)
+    del x, t
+
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    xv, tv = model.surrogate_samples(dev, 200_000, seed=8)
     sv = torch.exp(tv.double()) - 1e-8
     pe = torch.clamp(torch.exp(sur.forward(xv).double()) - 1e-8, min=0)
     mass_err = float(torch.sum(torch.abs(pe - sv)) / torch.sum(sv))
     mass_ratio = float(torch.sum(pe) / torch.sum(sv))
-    del x, t
+    del xv, tv
 
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
     res = {}
     for kind in ("exact", "surrogate", "none"):
         model.set_scatter_model(kind, sur if kind == "surrogate" else None)
-        y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)
+        y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)   # also warms up
         img = lam0.clone()
-        model.osem(dev, img, sc.n_subsets, 1)               # warm-up iteration
-        img = lam0.clone()
-        _, sec = timed(lambda: model.osem(dev, img, sc.n_subsets, n_it))
-        res[kind] = {"y": y, "img": img.cpu().numpy().astype(np.float64), "s_per_iter": sec / n_it}
+        _, sec = timed(lambda: model.osem(dev, img, sc.n_subsets, iters))
+        res[kind] = {"y": y, "img": img.cpu().numpy().astype(np.float64), "s_per_iter": sec / iters}
     model.set_scatter_model("exact")
     ex = res["exact"]
     roi_ex = roi_sums(ex["img"], ph.lesion_masks)
+    samples_per_iter = len(ev) * model.nq * len(sc.line_keV)
+    flop_per_sample = 2 * (32 * 128 + 2 * 128 * 128) + 2 * 128
     out = {"workload": f"{sc.name}: {sc.n}x{sc.n}, {sc.n_angles} angles, {sc.n_bins} bins, "
                        f"{sc.scatter_n}x{sc.scatter_n} scatter grid, {len(ev)} events, "
-                       f"{sc.n_subsets} subsets x {n_it} iterations",
-           "training": {"samples": n_samples, "sample_s": t_sample, "train_s": t_train,
-                        "steps": sum(k for k, _ in schedule), "batch": 4096,
+                       f"{sc.n_subsets} subsets x {iters} iterations",
+           "training": {"objects": f"{n_objects} random water/bone ellipses (seed {seed}), "
+                                    f"{object_events} MC events each; the workload's object "
+                                    "is not among them",
+                        "samples": n_samples, "sample_s": t_sample, "train_s": t_train,
+                        "steps": sum(k for k, _ in schedule), "batch": batch,
                         "loss_weight": "(S + 1e-8)^0.5",
-                        "heldout_mass_rel_err": mass_err, "heldout_mass_ratio": mass_ratio},
+                        "heldout_object_mass_rel_err": mass_err,
+                        "heldout_object_mass_ratio": mass_ratio},
            "exact": {"s_per_iter": ex["s_per_iter"], "roi_activity": roi_ex}}
     for kind in ("surrogate", "none"):
         r = res[kind]
@@ -412,6 +448,9 @@ def run_surrogate_form(workload="lmmew_64", n_samples=1_000_000, iters=None):
                      "image_rel_l2_vs_exact": float(np.linalg.norm(r["img"] - ex["img"])
                                                     / np.linalg.norm(ex["img"])),
                      "roi_rel_dev_vs_exact": [abs(a - b) / b for a, b in zip(roi, roi_ex)]}
+    out["surrogate"]["network_samples_per_s"] = samples_per_iter / res["surrogate"]["s_per_iter"]
+    out["surrogate"]["network_tflops"] = (samples_per_iter * flop_per_sample
+                                          / res["surrogate"]["s_per_iter"] / 1e12)
     sur.close()
     model.close()
     return out

@@ -78,6 +78,34 @@ def paper_study_phantom(sbr: float = 4.0) -> PhantomSpec:
                        rim_density=0.21 / 0.18)
 
 
+def random_water_bone_object(seed: int, k: int) -> PhantomSpec:
+    """Object ``k`` of a seeded family of random water/bone ellipses (the
+    surrogate's training objects): semi-axes 7-12.5 cm x 5.5-10 cm, a denser
+    rim in half of them, a bone disc of radius 0.8-2.5 cm somewhere inside,
+    and two to four lesions at 2:1-8:1."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, k]))
+    ax, ay = rng.uniform(7.0, 12.5), rng.uniform(5.5, 10.0)
+
+    def inside(margin):
+        while True:
+            x, y = rng.uniform(-ax, ax), rng.uniform(-ay, ay)
+            if (x / (ax - margin)) ** 2 + (y / (ay - margin)) ** 2 <= 1.0:
+                return float(x), float(y)
+
+    rb = rng.uniform(0.8, 2.5)
+    bx, by = inside(rb + 0.5)
+    lesions = []
+    for _ in range(int(rng.integers(2, 5))):
+        r = rng.uniform(0.6, 2.0)
+        lx, ly = inside(r + 0.3)
+        lesions.append(Disc(lx, ly, float(r)))
+    rim = float(rng.uniform(0.5, 1.5)) if rng.random() < 0.5 else 0.0
+    return PhantomSpec(bone=Disc(bx, by, float(rb)), lesions=tuple(lesions),
+                       semi_axes_cm=(float(ax), float(ay)),
+                       lesion_ratio=float(rng.uniform(2.0, 8.0)), rim_cm=rim,
+                       rim_density=float(rng.uniform(1.05, 1.2)))
+
+
 def pixel_centres_cm(n: int, pixel_cm: float) -> tuple[np.ndarray, np.ndarray]:
     """Return (x, y) pixel-centre coordinates, each shaped (n, n) as [iy, ix]."""
     c = (np.arange(n, dtype=np.float64) + 0.5 - n / 2.0) * pixel_cm

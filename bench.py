@@ -50,6 +50,8 @@ def parse_args():
                     help="skip the forms section (precision, batching, comparison, surrogate)")
     ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
                     help="comma-separated forms to measure")
+    ap.add_argument("--case", default=None, choices=["surrogate_rows"],
+                    help="run one small kernel case (for profiling) instead of the benchmark")
     return ap.parse_args()
 
 
@@ -663,9 +665,50 @@ def run_gpu(args, rank, local_rank, world):
     return 0
 
 
+def run_surrogate_rows_case(n_events=20_000, repeats=3):
+    """Small case for profiling the surrogate row kernel: the 64 x 64 object,
+    20 000 MC events, lm_forward with the surrogate scatter model (untrained
+    weights: the work does not depend on them).  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate
+    sc = preset("lmmew_64")
+    ph = sc.make_phantom()
+    ev = simulate(sc, n_events=n_events, seed=3)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    sur = lm.Surrogate(1)
+    model.set_scatter_model("surrogate", sur)
+    lam = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
+    times = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        model.forward(dev, lam)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    model.set_scatter_model("exact")
+    samples = len(ev) * model.nq * len(sc.line_keV)
+    ms = min(times)
+    print(json.dumps({"case": "surrogate_rows", "events": len(ev), "samples": samples,
+                      "ms": ms, "samples_per_s": samples / ms * 1e3,
+                      "tflops": samples * (2 * (32 * 128 + 2 * 128 * 128) + 256) / ms / 1e9}),
+          flush=True)
+    sur.close()
+    model.close()
+    return 0
+
+
 def main():
     args = parse_args()
     rank, local_rank, world = dist_env()
+    if args.case == "surrogate_rows":
+        return run_surrogate_rows_case()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_gpu(args, rank, local_rank, world)

@@ -14,7 +14,8 @@ namespace lmmew {
 // ---------------------------------------------------------------- tiling
 constexpr int kQT = 32;     // voxels per q-tile of the row kernel
 constexpr int kPC = 32;     // scatter points per pipeline stage
-constexpr int kET = 128;    // events per tile (4 per lane, 32 lanes)
+constexpr int kET = 128;    // events per tile (kEPL per lane, 32 lanes)
+constexpr int kEPL = kET / 32;
 constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
 constexpr int kRowThreads = 256;
 constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path

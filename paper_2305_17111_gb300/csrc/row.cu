@@ -231,9 +231,9 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
     const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
 #pragma unroll 1
     for (int pq = 0; pq < kPC / 4; ++pq) {
-        f32x2 cA[4], cB[4];
+        f32x2 cA[kEPL], cB[kEPL];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kEPL; ++k) {
             const float4 c4 = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
             cA[k] = pk(c4.x, c4.y);
             cB[k] = pk(c4.z, c4.w);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi) {
             const float* tq = tb + qi * kPC + pq * 4;
-            f32x2 inA[4], inB[4];
+            f32x2 inA[kEPL], inB[kEPL];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 const float4 nl = *reinterpret_cast<const float4*>(tq + (0 * W + w) * kQT * kPC);
@@ -251,7 +251,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
                 const f32x2 srA = pk(sr.x, sr.y), srB = pk(sr.z, sr.w);
                 const f32x2 mA = pk(mm.x, mm.y), mB = pk(mm.z, mm.w);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < kEPL; ++k) {
                     const f32x2 tA = term2(eh2[k], srA, mA, nlA);
                     const f32x2 tB = term2(eh2[k], srB, mB, nlB);
                     inA[k] = (w == 0) ? tA : add2(inA[k], tA);
@@ -259,7 +259,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kEPL; ++k) {
                 acc2[k][qi] = fma2(cA[k], inA[k], acc2[k][qi]);
                 acc2[k][qi] = fma2(cB[k], inB[k], acc2[k][qi]);
             }
@@ -283,16 +283,16 @@ __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, co
     const f32x2 sc2 = pk(scale, scale);
 #pragma unroll 1
     for (int pq = 0; pq < kPC / 4; ++pq) {
-        f32x2 cA[4], cB[4];
+        f32x2 cA[kEPL], cB[kEPL];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kEPL; ++k) {
             const float4 c4 = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
             cA[k] = mul2(pk(c4.x, c4.y), sc2);
             cB[k] = mul2(pk(c4.z, c4.w), sc2);
         }
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi) {
-            uint32_t inA[4], inB[4];
+            uint32_t inA[kEPL], inB[kEPL];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 const float4 ne =
@@ -300,7 +300,7 @@ __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, co
                 const uint4 hl = ln[(w * kQT) * (kPC / 4) + qi * (kPC / 4) + pq];
                 const f32x2 neA = pk(ne.x, ne.y), neB = pk(ne.z, ne.w);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < kEPL; ++k) {
                     float d0, d1;
                     upk(add2(eh2[k], neA), d0, d1);
                     uint32_t dh = H::cvt(d0, d1);
@@ -313,7 +313,7 @@ __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, co
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kEPL; ++k) {
                 acc2[k][qi] = fma2(cA[k], H::widen(inA[k]), acc2[k][qi]);
                 acc2[k][qi] = fma2(cB[k], H::widen(inB[k]), acc2[k][qi]);
             }
@@ -350,11 +350,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         const int b_lo = T.b_lo_hi >> 16, b_hi = T.b_lo_hi & 0xffff;
         const uint32_t c_bytes = (uint32_t)(b_hi - b_lo + 1) * kCPad * 4u;
 
-        float eh[4];
-        f32x2 eh2[4];
-        int bo[4];
+        float eh[kEPL];
+        f32x2 eh2[kEPL];
+        int bo[kEPL];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kEPL; ++k) {
             const int e = k * 32 + lane;
             const bool v = e < T.count;
             eh[k] = v ? P.ev_e[T.begin + e] : 0.f;
@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             bo[k] = v ? (int)P.ev_bin[T.begin + e] - b_lo : 0;
         }
         // two partial sums per (event, voxel): even and odd scatter points
-        f32x2 acc2[4][4];
+        f32x2 acc2[kEPL][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kEPL; ++k)
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc2[k][i] = 0ull;
 
@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             }
         }
 
-        float acc[4][4];
+        float acc[kEPL][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kEPL; ++k)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 float lo, hi;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 const int q = qt * kQT + warp * 4 + qi;
                 if (q < P.nq) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < kEPL; ++k) {
                         if (k * 32 + lane < T.count) {
                             float s = 0.f;
 #pragma unroll
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         // transpose through shared memory: tile [128 events][32 voxels]
         float* tt = reinterpret_cast<float*>(smem);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kEPL; ++k)
 #pragma unroll
             for (int qi = 0; qi < 4; ++qi) tt[(k * 32 + lane) * 33 + warp * 4 + qi] = acc[k][qi];
         __syncthreads();

@@ -53,15 +53,28 @@ __device__ __forceinline__ void mma(float* c, const uint32_t* a, uint32_t b0, ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// GELU, tanh form: 0.5 z (1 + tanh(c (z + 0.044715 z^3))), c = sqrt(2/pi)
+// GELU, tanh form: 0.5 z (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3),
+// evaluated as u = z (c + c k z^2), h = hz tanh(u) + hz with hz = z / 2.  The
+// scalar and the packed (f32x2) forms perform the same IEEE operations in the
+// same order, so every kernel produces the same activations.
+constexpr float kGeluC = 0.7978845608028654f;
+constexpr float kGeluCK = 0.7978845608028654f * 0.044715f;
 __device__ __forceinline__ float tanh_fast(float x) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 __device__ __forceinline__ float gelu(float z) {
-    const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-    return 0.5f * z * (1.f + tanh_fast(u));
+    const float u = z * fmaf(z * z, kGeluCK, kGeluC);
+    const float hz = z * 0.5f;
+    return fmaf(hz, tanh_fast(u), hz);
+}
+__device__ __forceinline__ f32x2 gelu2(f32x2 z) {
+    const f32x2 u = mul2(z, fma2(mul2(z, z), pk(kGeluCK, kGeluCK), pk(kGeluC, kGeluC)));
+    float u0, u1;
+    upk(u, u0, u1);
+    const f32x2 hz = mul2(z, pk(0.5f, 0.5f));
+    return fma2(hz, pk(tanh_fast(u0), tanh_fast(u1)), hz);
 }
 __device__ __forceinline__ float gelu_grad(float z) {
     const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
@@ -187,20 +200,25 @@ __global__ void __launch_bounds__(kThreads) k_forward(Weights w, const bf16* x, 
 #pragma unroll
         for (int nt = 0; nt < 16; ++nt) {
             const int col = nt * 8 + cpair;
+            const f32x2 b2 = pk(bias[col], bias[col + 1]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int row = m0 + g + h * 8;
-                const float z0 = acc[nt][2 * h] + bias[col], z1 = acc[nt][2 * h + 1] + bias[col + 1];
+                const f32x2 z = add2(pk(acc[nt][2 * h], acc[nt][2 * h + 1]), b2);
+                float z0, z1;
+                upk(z, z0, z1);
                 if (z_out && row < rows) {
                     bf16* zp = z_out + ((size_t)layer * n + base + row) * kHid + col;
                     *reinterpret_cast<__nv_bfloat162*>(zp) = __floats2bfloat162_rn(z0, z1);
                 }
+                float h0, h1;
+                upk(gelu2(z), h0, h1);
                 if (layer < 2) {
                     *reinterpret_cast<__nv_bfloat162*>(Hs + row * kLdH + col) =
-                        __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                        __floats2bfloat162_rn(h0, h1);
                 } else {
-                    acc[nt][2 * h] = gelu(z0);
-                    acc[nt][2 * h + 1] = gelu(z1);
+                    acc[nt][2 * h] = h0;
+                    acc[nt][2 * h + 1] = h1;
                 }
             }
         }
@@ -498,11 +516,19 @@ struct SurrogateRowParams {
     const float* rho;
 };
 
+// 16 warps: warp w owns rows 16 (w mod 8) .. + 16 of the 128-sample tile and
+// output columns 64 (w / 8) .. + 64 of every layer; the two warps of a row
+// block meet at a named barrier (ids 1..8) between the layers.
+constexpr int kRowSurThreads = 512;
 constexpr size_t kRowSurrogateSmem =
     sizeof(bf16) * (kHid * kLdX + 2 * kHid * kLdH + kTile * kLdX + kTile * kLdH) +
-    sizeof(float) * kTile * 33;
+    sizeof(float) * (kTile * 33 + 4 * kHid + kTile);
 
-__global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowParams P) {
+__device__ __forceinline__ void pair_sync(int row_block) {
+    asm volatile("bar.sync %0, 64;" ::"r"(row_block + 1) : "memory");
+}
+
+__global__ void __launch_bounds__(kRowSurThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
     extern __shared__ __align__(16) unsigned char sm[];
     bf16* W1s = reinterpret_cast<bf16*>(sm);
     bf16* W2s = W1s + kHid * kLdX;
@@ -510,13 +536,24 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
     bf16* Xs = W3s + kHid * kLdH;
     bf16* Hs = Xs + kTile * kLdX;
     float* St = reinterpret_cast<float*>(Hs + kTile * kLdH);   // [128 events][33]
+    float* Bs = St + kTile * 33;                                // [3][128] hidden biases
+    float* W4s = Bs + 3 * kHid;                                 // [128] output weights
+    float* Red = W4s + kHid;                                    // [128] second half's output sums
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rb = warp & 7, nh = warp >> 3;
+    const int m0 = rb * 16, n0 = nh * 64;
     copy_rows(W1s, kLdX, P.w.W1, kIn, kHid, kIn);
     copy_rows(W2s, kLdH, P.w.W2, kHid, kHid, kHid);
     copy_rows(W3s, kLdH, P.w.W3, kHid, kHid, kHid);
+    for (int i = tid; i < 3 * kHid; i += kRowSurThreads) {
+        const int l = i / kHid;
+        Bs[i] = P.w.p[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + i % kHid];
+    }
+    for (int i = tid; i < kHid; i += kRowSurThreads) W4s[i] = P.w.p[kOffW4 + i];
+    const float b4 = P.w.p[kOffB4];
     const int n_tiles = P.tile_end - P.tile_begin;
     const int n_units = n_tiles * P.nqt;
-    const int m0 = warp * 16, g = lane >> 2, cpair = (lane & 3) * 2;
+    const int g = lane >> 2, cpair = (lane & 3) * 2;
     const float half_det = 0.5f * P.B * P.bin_w;
     for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
         const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
@@ -524,7 +561,7 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
         const int nq_here = min(32, P.nq - qt * 32);
         __syncthreads();   // previous unit done with St / Xs
         // start from the unscattered rows
-        for (int i = tid; i < kET * 32; i += kThreads) {
+        for (int i = tid; i < kET * 32; i += kRowSurThreads) {
             const int e = i >> 5, ql = i & 31;
             St[e * 33 + ql] = (e < T.count && ql < nq_here)
                                   ? P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql]
@@ -535,7 +572,7 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
         sincosf(th, &sa, &ca);
         for (int c = 0; c < (T.count + 3) / 4; ++c) {
             for (int wl = 0; wl < P.W; ++wl) {
-                __syncthreads();   // Xs free
+                __syncthreads();   // Xs free, Red read
                 if (tid < kTile) {
                     const int e = c * 4 + (tid >> 5), ql = tid & 31;
                     float f[kSurrogateIn];
@@ -558,37 +595,39 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
                             __floats2bfloat162_rn(f[k], f[k + 1]);
                 }
                 __syncthreads();
-                float acc[16][4];
+                float acc[8][4];
                 for (int layer = 0; layer < 3; ++layer) {
-                    zero<kHid>(acc);
-                    if (layer == 0) gemm_nt<kIn, kHid>(acc, Xs, kLdX, m0, W1s, kLdX, lane);
-                    else if (layer == 1) gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W2s, kLdH, lane);
-                    else gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W3s, kLdH, lane);
-                    const float* bias = P.w.p + (layer == 0 ? kOffB1 : layer == 1 ? kOffB2 : kOffB3);
-                    __syncwarp();
+                    zero<64>(acc);
+                    if (layer == 0) gemm_nt<kIn, 64>(acc, Xs, kLdX, m0, W1s + n0 * kLdX, kLdX, lane);
+                    else if (layer == 1) gemm_nt<kHid, 64>(acc, Hs, kLdH, m0, W2s + n0 * kLdH, kLdH, lane);
+                    else gemm_nt<kHid, 64>(acc, Hs, kLdH, m0, W3s + n0 * kLdH, kLdH, lane);
+                    if (layer == 1) pair_sync(rb);   // both halves read these rows of Hs
+                    const float* bias = Bs + layer * kHid;
 #pragma unroll
-                    for (int nt = 0; nt < 16; ++nt) {
-                        const int col = nt * 8 + cpair;
+                    for (int nt = 0; nt < 8; ++nt) {
+                        const int col = n0 + nt * 8 + cpair;
+                        const f32x2 b2 = pk(bias[col], bias[col + 1]);
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh) {
-                            const float z0 = acc[nt][2 * hh] + bias[col];
-                            const float z1 = acc[nt][2 * hh + 1] + bias[col + 1];
+                            float h0, h1;
+                            upk(gelu2(add2(pk(acc[nt][2 * hh], acc[nt][2 * hh + 1]), b2)), h0, h1);
                             if (layer < 2) {
                                 *reinterpret_cast<__nv_bfloat162*>(Hs + (m0 + g + hh * 8) * kLdH + col) =
-                                    __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                                    __floats2bfloat162_rn(h0, h1);
                             } else {
-                                acc[nt][2 * hh] = gelu(z0);
-                                acc[nt][2 * hh + 1] = gelu(z1);
+                                acc[nt][2 * hh] = h0;
+                                acc[nt][2 * hh + 1] = h1;
                             }
                         }
                     }
-                    __syncwarp();
+                    if (layer < 2) pair_sync(rb);   // both halves of the rows written
                 }
+                // output: this warp's 64 columns, then the two halves summed
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-                for (int nt = 0; nt < 16; ++nt) {
-                    const int col = nt * 8 + cpair;
-                    const float w0 = P.w.p[kOffW4 + col], w1 = P.w.p[kOffW4 + col + 1];
+                for (int nt = 0; nt < 8; ++nt) {
+                    const int col = n0 + nt * 8 + cpair;
+                    const float w0 = W4s[col], w1 = W4s[col + 1];
                     s0 += acc[nt][0] * w0 + acc[nt][1] * w1;
                     s1 += acc[nt][2] * w0 + acc[nt][3] * w1;
                 }
@@ -596,14 +635,18 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
                 s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
                 s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
                 s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-                if ((lane & 3) == 0) {
-                    const float b4 = P.w.p[kOffB4];
+                if (nh == 1 && (lane & 3) == 0) {
+                    Red[m0 + g] = s0;
+                    Red[m0 + g + 8] = s1;
+                }
+                pair_sync(rb);
+                if (nh == 0 && (lane & 3) == 0) {
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
                         const int srow = m0 + g + hh * 8;          // sample = event * 32 + voxel
                         const int e = c * 4 + (srow >> 5), ql = srow & 31;
                         if (e < T.count && ql < nq_here) {
-                            const float v = __expf((hh ? s1 : s0) + b4) - kSurrogateEps;
+                            const float v = __expf((hh ? s1 : s0) + Red[srow] + b4) - kSurrogateEps;
                             St[e * 33 + ql] += v > 0.f ? v : 0.f;
                         }
                     }
@@ -611,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) k_surrogate_rows(const SurrogateRowP
             }
         }
         __syncthreads();
-        for (int i = tid; i < kET * 32; i += kThreads) {
+        for (int i = tid; i < kET * 32; i += kRowSurThreads) {
             const int e = i >> 5, ql = i & 31;
             if (e < T.count && ql < nq_here)
                 P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] = St[e * 33 + ql];
@@ -698,7 +741,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     }
     P.rho = h->d_rho;
     const int grid = std::min(n_units, h->sm_count);
-    mlp::k_surrogate_rows<<<grid, mlp::kThreads, mlp::kRowSurrogateSmem, st>>>(P);
+    mlp::k_surrogate_rows<<<grid, mlp::kRowSurThreads, mlp::kRowSurrogateSmem, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -247,50 +247,119 @@ int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStrea
 constexpr int kSurrogateIn = 32;
 constexpr float kSurrogateEps = 1e-8f;   // target = ln(S + eps)
 constexpr float kElectronRestKeV = 510.99895f;
-__host__ __device__ __forceinline__ void surrogate_features(float xq, float yq, float ca, float sa,
-                                                            float ub, float e_hat, int w,
-                                                            float e_line, float mu_w,
-                                                            const float* g8, const float* rho,
-                                                            int n, float h, float* f) {
-    f[0] = xq * 0.05f;
-    f[1] = yq * 0.05f;
-    f[2] = ca;
-    f[3] = sa;
-    f[4] = ub * 0.05f;
-    f[5] = (e_hat - 150.f) * 0.01f;
-    f[6] = w == 0 ? 1.f : 0.f;
-    f[7] = w == 1 ? 1.f : 0.f;
-    f[8] = w == 2 ? 1.f : 0.f;
-    for (int k = 0; k < 8; ++k) f[9 + k] = mu_w * g8[k] * 0.25f;
+// Inputs 8 j .. 8 j + 7 (j = 0..3) of one (event, voxel, line); g8 holds the
+// 8 rho line integrals of the voxel at this angle.  Four threads can build
+// one sample's inputs side by side; surrogate_features calls this for all j,
+// so every kernel computes the same values.
+__host__ __device__ __forceinline__ void surrogate_features_chunk(
+    int j, float xq, float yq, float ca, float sa, float ub, float e_hat, int w, float e_line,
+    float mu_w, const float* g8, const float* rho, int n, float h, float* f8) {
+    if (j == 0) {
+        f8[0] = xq * 0.05f;
+        f8[1] = yq * 0.05f;
+        f8[2] = ca;
+        f8[3] = sa;
+        f8[4] = ub * 0.05f;
+        f8[5] = (e_hat - 150.f) * 0.01f;
+        f8[6] = w == 0 ? 1.f : 0.f;
+        f8[7] = w == 1 ? 1.f : 0.f;
+        return;
+    }
+    if (j == 1) {
+        f8[0] = w == 2 ? 1.f : 0.f;
+        for (int k = 0; k < 7; ++k) f8[1 + k] = mu_w * g8[k] * 0.25f;
+        return;
+    }
     const float uq = -xq * sa + yq * ca, tq = xq * ca + yq * sa;
     const float du = ub - uq;
     const float kappa = kElectronRestKeV * (1.f / e_hat - 1.f / e_line);
-    f[17] = du * 0.2f;
-    f[18] = tq * 0.05f;
-    f[19] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
-    f[20] = e_hat / e_line;
-    f[21] = fabsf(du) * 0.2f;
     const float c = fminf(fmaxf(1.f - kappa, -1.f), 1.f);
     const float s = fmaxf(sqrtf(fmaxf(1.f - c * c, 0.f)), 0.05f);
     const float lim = n * h;
     const float dt = fminf(fmaxf(fabsf(du) * c / s, -lim), lim);
     const float tp = tq + dt;
     const float xp = tp * ca - ub * sa, yp = tp * sa + ub * ca;
+    if (j == 2) {
+        f8[0] = mu_w * g8[7] * 0.25f;
+        f8[1] = du * 0.2f;
+        f8[2] = tq * 0.05f;
+        f8[3] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
+        f8[4] = e_hat / e_line;
+        f8[5] = fabsf(du) * 0.2f;
+        f8[6] = xp * 0.05f;
+        f8[7] = yp * 0.05f;
+        return;
+    }
     const float r = sqrtf(dt * dt + du * du);
-    f[22] = xp * 0.05f;
-    f[23] = yp * 0.05f;
-    f[24] = r * 0.05f;
-    f[25] = c;
-    f[26] = h / (r + h);
-    f[27] = kappa < 0.f ? 1.f : 0.f;
+    f8[0] = r * 0.05f;
+    f8[1] = c;
+    f8[2] = h / (r + h);
+    f8[3] = kappa < 0.f ? 1.f : 0.f;
     const float gx = floorf(xp / h + 0.5f * n), gy = floorf(yp / h + 0.5f * n);
-    f[28] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n)
-                ? rho[(int)gy * n + (int)gx]
-                : 0.f;
-    f[29] = f[30] = f[31] = 0.f;
+    f8[4] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n) ? rho[(int)gy * n + (int)gx]
+                                                                       : 0.f;
+    f8[5] = f8[6] = f8[7] = 0.f;
+}
+__host__ __device__ __forceinline__ void surrogate_features(float xq, float yq, float ca, float sa,
+                                                            float ub, float e_hat, int w,
+                                                            float e_line, float mu_w,
+                                                            const float* g8, const float* rho,
+                                                            int n, float h, float* f) {
+    for (int j = 0; j < 4; ++j)
+        surrogate_features_chunk(j, xq, yq, ca, sa, ub, e_hat, w, e_line, mu_w, g8, rho, n, h,
+                                 f + 8 * j);
 }
 
 #ifdef __CUDACC__
+// Shared-memory addresses, the global timer and mbarriers (every wait on an
+// mbarrier is bounded in time), and the bulk asynchronous copy engine.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per pipeline wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t global_timer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for a barrier phase with a time limit; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer();
+    while (!mbar_try_wait(bar, parity))
+        if (global_timer() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
 // Packed pairs of FP32 values (Blackwell's f32x2 arithmetic): one instruction,
 // two IEEE round-to-nearest results.
 typedef unsigned long long f32x2;

@@ -488,11 +488,270 @@ __global__ void k_batch_indices(uint64_t seed, uint64_t step, int n, uint64_t n_
 
 
 // ---------------------------------------------------------------------------
-// The surrogate inside the row pipeline: after k_row wrote the unscattered
-// part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
-// adds sum_w (exp(net(x_w)) - eps) for every (event, voxel) and writes the
-// unit's partial forward sums.  Persistent CTAs; the weights stay in shared
-// memory; 128 (event, voxel) samples per pass (4 events x 32 voxels).
+// Tensor-core (tcgen05) forward pass of the network, for inference.
+//
+// One CTA of 512 threads per SM, persistent over tiles of 128 samples.  W1
+// (K padded from 32 to 64 with zeros), W2 and W3 stay in shared memory in the
+// canonical K-major layout with 128-byte swizzle (8-row x 128-byte atoms,
+// 16-byte chunk j of row r stored at chunk j ^ (r mod 8), 64-element K blocks
+// one after the other); the input tile X (128 x 64) and the hidden tile H
+// (128 x 128) use the same layout.  Per layer one thread issues the
+// M = 128 x N = 128 x K = 16 MMAs (kind::f16, BF16 operands, FP32
+// accumulator in 128 columns of tensor memory) and commits them to an
+// mbarrier; warp w then reads TMEM lanes 32 (w mod 4) .. + 32 (its samples)
+// and columns 32 (w / 4) .. + 32 with tcgen05.ld, adds the bias, applies
+// GELU and writes BF16 into H (the next layer's A operand) -- or, after the
+// last layer, its partial dot with the output weights.
+constexpr int kTcThreads = 512;
+constexpr uint32_t kTcCols = 128;                  // TMEM columns (FP32 accumulator 128 x 128)
+constexpr uint32_t kAtomBlock = 128 * 128;         // bytes of one 64-wide K block of a 128-row tile
+constexpr uint32_t kTcOffW1 = 0;                   // 128 x 64
+constexpr uint32_t kTcOffW2 = kTcOffW1 + kAtomBlock;       // 128 x 128
+constexpr uint32_t kTcOffW3 = kTcOffW2 + 2 * kAtomBlock;   // 128 x 128
+constexpr uint32_t kTcOffX = kTcOffW3 + 2 * kAtomBlock;    // 128 x 64
+constexpr uint32_t kTcOffH = kTcOffX + kAtomBlock;         // 128 x 128
+constexpr uint32_t kTcOffF = kTcOffH + 2 * kAtomBlock;     // floats: bias [3][128], w4 [128], red [4][128]
+constexpr uint32_t kTcOffSt = kTcOffF + (3 * 128 + 128 + 4 * 128) * 4;   // rows: St [128][33]
+constexpr uint32_t kTcOffV = kTcOffSt + 128 * 33 * 4;      // rows: the unit's voxels and events
+constexpr uint32_t kTcOffBar = kTcOffV + (32 * 2 + 32 * 8 + 128 * 2) * 4;   // mbarrier, TMEM, abort
+constexpr size_t kTcSmem = kTcOffBar + 64 + 1024;          // + room to align the base to 1 KB
+static_assert(kTcOffX % 1024 == 0 && kTcOffH % 1024 == 0 && kTcOffW2 % 1024 == 0 &&
+                  kTcOffW3 % 1024 == 0, "swizzle atoms need 1 KB alignment");
+static_assert(kTcSmem <= 227 * 1024, "shared memory");
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 128, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+// Byte offset of 16-byte chunk j (0..7) of K block kb of row r in a 128-row tile.
+__device__ __forceinline__ uint32_t sw_chunk(int r, int kb, int j) {
+    return (uint32_t)kb * kAtomBlock + (uint32_t)r * 128u + ((uint32_t)(j ^ (r & 7)) << 4);
+}
+// Shared-memory matrix descriptor of a K-major, 128-byte-swizzled operand
+// starting at byte address saddr (8-row groups 1024 bytes apart).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused within a swizzle atom)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // descriptor version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void tc_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcShared {
+    unsigned char* base;   // 1 KB aligned
+    uint32_t sbase;        // its shared-window address
+    uint32_t bar;          // mbarrier address
+    uint32_t* tmem_slot;
+    int* abort;
+};
+
+__device__ __forceinline__ TcShared tc_shared(unsigned char* raw) {
+    TcShared t;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(raw);
+    const uint32_t pad = ((a + 1023u) & ~1023u) - a;
+    t.base = raw + pad;
+    t.sbase = a + pad;
+    t.bar = t.sbase + kTcOffBar;
+    t.tmem_slot = reinterpret_cast<uint32_t*>(t.base + kTcOffBar + 8);
+    t.abort = reinterpret_cast<int*>(t.base + kTcOffBar + 16);
+    return t;
+}
+
+// Weights into their swizzled tiles, the padding half of X zeroed, the
+// mbarrier initialised, TMEM allocated (warp 0).  Ends with a CTA barrier;
+// returns the TMEM address.
+__device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 128 * 8; i += kTcThreads) {
+        const int n = i >> 3, j = i & 7;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (j < 4) v = *reinterpret_cast<const uint4*>(w.W1 + (size_t)n * kIn + j * 8);
+        *reinterpret_cast<uint4*>(S.base + kTcOffW1 + sw_chunk(n, 0, j)) = v;
+    }
+    for (int i = tid; i < 128 * 16; i += kTcThreads) {
+        const int n = i >> 4, c = i & 15;
+        *reinterpret_cast<uint4*>(S.base + kTcOffW2 + sw_chunk(n, c >> 3, c & 7)) =
+            *reinterpret_cast<const uint4*>(w.W2 + (size_t)n * kHid + c * 8);
+        *reinterpret_cast<uint4*>(S.base + kTcOffW3 + sw_chunk(n, c >> 3, c & 7)) =
+            *reinterpret_cast<const uint4*>(w.W3 + (size_t)n * kHid + c * 8);
+    }
+    for (int i = tid; i < 128 * 4; i += kTcThreads)
+        *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(i >> 2, 0, 4 + (i & 3))) =
+            make_uint4(0u, 0u, 0u, 0u);
+    float* F = reinterpret_cast<float*>(S.base + kTcOffF);
+    for (int i = tid; i < 3 * kHid; i += kTcThreads) {
+        const int l = i / kHid;
+        F[i] = w.p[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + i % kHid];
+    }
+    for (int i = tid; i < kHid; i += kTcThreads) F[3 * kHid + i] = w.p[kOffW4 + i];
+    if (tid == 0) {
+        mbar_init(S.bar, 1);
+        mbar_fence_init();
+        *S.abort = 0;
+    }
+    if (tid < 32) tc_alloc(S.sbase + kTcOffBar + 8, kTcCols);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *S.tmem_slot;
+}
+
+// After an MMA wait ran out, wait once more (bounded) for the MMAs in
+// flight before the tensor memory they write is released.
+__device__ void tc_teardown(const TcShared& S, uint32_t tmem, uint32_t phase) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *S.abort && phase > 0) mbar_wait_bounded(S.bar, (phase - 1) & 1);
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tc_dealloc(tmem, kTcCols);
+}
+
+// The network on the 128 samples whose inputs sit in X (written, fenced and
+// followed by a CTA barrier).  Returns, in threads of warps 0..3, the output
+// of sample 32 warp + lane; false if an MMA wait ran out (the status word is
+// set and the caller stops).
+__device__ bool tc_network(const TcShared& S, uint32_t tmem, uint32_t& phase, float b4,
+                           float* out_row, int* status) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lq = warp & 3, cq = warp >> 2;
+    const int row = lq * 32 + lane;
+    const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
+    float* red = reinterpret_cast<float*>(S.base + kTcOffF) + 4 * kHid;
+    for (int layer = 0; layer < 3; ++layer) {
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = S.sbase + (layer == 0 ? kTcOffX : kTcOffH);
+            const uint32_t b0 = S.sbase + (layer == 0 ? kTcOffW1 : layer == 1 ? kTcOffW2 : kTcOffW3);
+            const int ksteps = layer == 0 ? 4 : 8;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                const uint32_t off = (uint32_t)(ks >> 2) * kAtomBlock + (uint32_t)(ks & 3) * 32u;
+                tc_mma(tmem, umma_desc(a0 + off), umma_desc(b0 + off), kTcIdesc, ks > 0 ? 1u : 0u);
+            }
+            tc_commit(S.bar);
+            if (!mbar_wait_bounded(S.bar, phase & 1)) {
+                *S.abort = 1;
+                atomicOr(status, kStatusTimeout);
+            }
+        }
+        ++phase;
+        __syncthreads();
+        if (*S.abort) return false;
+        tc_fence_after();
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * 32), v);
+        const float* bias = F + layer * kHid + cq * 32;
+        if (layer < 2) {
+            uint32_t hb[16];
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                float h0, h1;
+                upk(gelu2(add2(pk(v[i], v[i + 1]), pk(bias[i], bias[i + 1]))), h0, h1);
+                const __nv_bfloat162 t = __floats2bfloat162_rn(h0, h1);
+                hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t);
+            }
+            const int kb = cq >> 1, j0 = (cq & 1) * 4;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                *reinterpret_cast<uint4*>(S.base + kTcOffH + sw_chunk(row, kb, j0 + c)) =
+                    make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
+            fence_async_smem();
+        } else {
+            const float* w4 = F + 3 * kHid + cq * 32;
+            float sacc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                float h0, h1;
+                upk(gelu2(add2(pk(v[i], v[i + 1]), pk(bias[i], bias[i + 1]))), h0, h1);
+                sacc = fmaf(h0, w4[i], sacc);
+                sacc = fmaf(h1, w4[i + 1], sacc);
+            }
+            red[cq * 128 + row] = sacc;
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (cq == 0) *out_row = ((red[row] + red[128 + row]) + (red[256 + row] + red[384 + row])) + b4;
+    return true;
+}
+
+// Network outputs for n BF16 input rows.
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const bf16* x, int64_t n,
+                                                              float* out, int* status) {
+    extern __shared__ unsigned char smem_raw[];
+    const TcShared S = tc_shared(smem_raw);
+    const uint32_t tmem = tc_setup(S, w);
+    const float b4 = w.p[kOffB4];
+    const int tid = threadIdx.x;
+    uint32_t phase = 0;
+    const int64_t n_tiles = (n + 127) / 128;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t base = t * 128;
+        {   // 128 rows x 4 chunks of 8 inputs
+            const int r = tid >> 2, j = tid & 3;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (base + r < n) v = *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + j * 8);
+            *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(r, 0, j)) = v;
+        }
+        fence_async_smem();
+        __syncthreads();
+        float o = 0.f;
+        if (!tc_network(S, tmem, phase, b4, &o, status)) break;
+        const int row = (tid >> 5) * 32 + (tid & 31);
+        if (tid < 128 && base + row < n) out[base + row] = o;
+    }
+    tc_teardown(S, tmem, phase);
+}
+
 struct SurrogateRowParams {
     Weights w;
     const Tile* tiles;
@@ -501,7 +760,6 @@ struct SurrogateRowParams {
     const float* ev_e;
     const int* q_pix;
     const float* g8;       // [A][nq][8]
-    const double* cs_dummy;
     float* rows;
     int64_t row_base;
     int row_stride;
@@ -509,6 +767,7 @@ struct SurrogateRowParams {
     int lam_stride;
     float* ypart;
     int64_t ypart_stride;
+    int* status;
     int n, A, B, W, nq, nqt;
     float h, bin_w;
     float mu_line[LMMEW_MAX_LINES];
@@ -516,145 +775,94 @@ struct SurrogateRowParams {
     const float* rho;
 };
 
-// 16 warps: warp w owns rows 16 (w mod 8) .. + 16 of the 128-sample tile and
-// output columns 64 (w / 8) .. + 64 of every layer; the two warps of a row
-// block meet at a named barrier (ids 1..8) between the layers.
-constexpr int kRowSurThreads = 512;
-constexpr size_t kRowSurrogateSmem =
-    sizeof(bf16) * (kHid * kLdX + 2 * kHid * kLdH + kTile * kLdX + kTile * kLdH) +
-    sizeof(float) * (kTile * 33 + 4 * kHid + kTile);
-
-__device__ __forceinline__ void pair_sync(int row_block) {
-    asm volatile("bar.sync %0, 64;" ::"r"(row_block + 1) : "memory");
-}
-
-__global__ void __launch_bounds__(kRowSurThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    bf16* W1s = reinterpret_cast<bf16*>(sm);
-    bf16* W2s = W1s + kHid * kLdX;
-    bf16* W3s = W2s + kHid * kLdH;
-    bf16* Xs = W3s + kHid * kLdH;
-    bf16* Hs = Xs + kTile * kLdX;
-    float* St = reinterpret_cast<float*>(Hs + kTile * kLdH);   // [128 events][33]
-    float* Bs = St + kTile * 33;                                // [3][128] hidden biases
-    float* W4s = Bs + 3 * kHid;                                 // [128] output weights
-    float* Red = W4s + kHid;                                    // [128] second half's output sums
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rb = warp & 7, nh = warp >> 3;
-    const int m0 = rb * 16, n0 = nh * 64;
-    copy_rows(W1s, kLdX, P.w.W1, kIn, kHid, kIn);
-    copy_rows(W2s, kLdH, P.w.W2, kHid, kHid, kHid);
-    copy_rows(W3s, kLdH, P.w.W3, kHid, kHid, kHid);
-    for (int i = tid; i < 3 * kHid; i += kRowSurThreads) {
-        const int l = i / kHid;
-        Bs[i] = P.w.p[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + i % kHid];
-    }
-    for (int i = tid; i < kHid; i += kRowSurThreads) W4s[i] = P.w.p[kOffW4 + i];
+// The surrogate inside the row pipeline: after k_row wrote the unscattered
+// part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
+// adds sum_w max(exp(net(x_w)) - eps, 0) for every (event, voxel) and writes
+// the unit's partial forward sums.  Passes of 128 samples: 4 events x 32
+// voxels, one line.
+__global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    const TcShared S = tc_shared(smem_raw);
+    const uint32_t tmem = tc_setup(S, P.w);
     const float b4 = P.w.p[kOffB4];
+    float* St = reinterpret_cast<float*>(S.base + kTcOffSt);   // [128 events][33]
+    float* Vxy = reinterpret_cast<float*>(S.base + kTcOffV);   // [32] voxel centre (x, y), cm
+    float* Vg8 = Vxy + 32 * 2;                                   // [32][8] rho line integrals
+    float* Eeu = Vg8 + 32 * 8;                                   // [128] (recorded energy, bin centre)
+    const int tid = threadIdx.x;
+    uint32_t phase = 0;
     const int n_tiles = P.tile_end - P.tile_begin;
     const int n_units = n_tiles * P.nqt;
-    const int g = lane >> 2, cpair = (lane & 3) * 2;
     const float half_det = 0.5f * P.B * P.bin_w;
-    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+    bool ok = true;
+    for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x) {
         const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
         const int qt = unit % P.nqt;
         const int nq_here = min(32, P.nq - qt * 32);
-        __syncthreads();   // previous unit done with St / Xs
-        // start from the unscattered rows
-        for (int i = tid; i < kET * 32; i += kRowSurThreads) {
+        __syncthreads();   // the previous unit is done with St
+        for (int i = tid; i < kET * 32; i += kTcThreads) {
             const int e = i >> 5, ql = i & 31;
             St[e * 33 + ql] = (e < T.count && ql < nq_here)
                                   ? P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql]
                                   : 0.f;
         }
+        // the unit's voxels and events, once
+        if (tid < 32 && tid < nq_here) {
+            const int pix = P.q_pix[qt * 32 + tid];
+            Vxy[2 * tid] = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
+            Vxy[2 * tid + 1] = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
+        }
+        if (tid < 32 * 8 && (tid >> 3) < nq_here)
+            Vg8[tid] = P.g8[((size_t)T.a * P.nq + qt * 32 + (tid >> 3)) * 8 + (tid & 7)];
+        if (tid < T.count) {
+            Eeu[2 * tid] = P.ev_e[T.begin + tid];
+            Eeu[2 * tid + 1] = -half_det + (P.ev_bin[T.begin + tid] + 0.5f) * P.bin_w;
+        }
+        __syncthreads();
         const float th = 6.283185307179586f * T.a / P.A;
         float ca, sa;
         sincosf(th, &sa, &ca);
-        for (int c = 0; c < (T.count + 3) / 4; ++c) {
-            for (int wl = 0; wl < P.W; ++wl) {
-                __syncthreads();   // Xs free, Red read
-                if (tid < kTile) {
-                    const int e = c * 4 + (tid >> 5), ql = tid & 31;
-                    float f[kSurrogateIn];
+        for (int c = 0; c < (T.count + 3) / 4 && ok; ++c) {
+            for (int wl = 0; wl < P.W && ok; ++wl) {
+                // inputs 8 j .. 8 j + 7 of sample s = tid / 4 (event 4c + s / 32,
+                // voxel s mod 32) into chunk j = tid mod 4 of row s of X
+                {
+                    const int smp = tid >> 2, j = tid & 3;
+                    const int e = c * 4 + (smp >> 5), ql = smp & 31;
+                    float f8[8];
                     if (e < T.count && ql < nq_here) {
-                        const int q = qt * 32 + ql;
-                        const int pix = P.q_pix[q];
-                        const float xq = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
-                        const float yq = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
-                        const int b = P.ev_bin[T.begin + e];
-                        const float ub = -half_det + (b + 0.5f) * P.bin_w;
-                        surrogate_features(xq, yq, ca, sa, ub, P.ev_e[T.begin + e], wl,
-                                           P.e_line[wl], P.mu_line[wl],
-                                           P.g8 + ((size_t)T.a * P.nq + q) * 8, P.rho, P.n, P.h, f);
+                        surrogate_features_chunk(j, Vxy[2 * ql], Vxy[2 * ql + 1], ca, sa,
+                                                 Eeu[2 * e + 1], Eeu[2 * e], wl, P.e_line[wl],
+                                                 P.mu_line[wl], Vg8 + ql * 8, P.rho, P.n, P.h, f8);
                     } else {
-                        for (int k = 0; k < kSurrogateIn; ++k) f[k] = 0.f;
-                    }
 #pragma unroll
-                    for (int k = 0; k < kSurrogateIn; k += 2)
-                        *reinterpret_cast<__nv_bfloat162*>(Xs + tid * kLdX + k) =
-                            __floats2bfloat162_rn(f[k], f[k + 1]);
+                        for (int k = 0; k < 8; ++k) f8[k] = 0.f;
+                    }
+                    uint32_t u[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const __nv_bfloat162 t = __floats2bfloat162_rn(f8[2 * k], f8[2 * k + 1]);
+                        u[k] = *reinterpret_cast<const uint32_t*>(&t);
+                    }
+                    *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(smp, 0, j)) =
+                        make_uint4(u[0], u[1], u[2], u[3]);
                 }
+                fence_async_smem();
                 __syncthreads();
-                float acc[8][4];
-                for (int layer = 0; layer < 3; ++layer) {
-                    zero<64>(acc);
-                    if (layer == 0) gemm_nt<kIn, 64>(acc, Xs, kLdX, m0, W1s + n0 * kLdX, kLdX, lane);
-                    else if (layer == 1) gemm_nt<kHid, 64>(acc, Hs, kLdH, m0, W2s + n0 * kLdH, kLdH, lane);
-                    else gemm_nt<kHid, 64>(acc, Hs, kLdH, m0, W3s + n0 * kLdH, kLdH, lane);
-                    if (layer == 1) pair_sync(rb);   // both halves read these rows of Hs
-                    const float* bias = Bs + layer * kHid;
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        const int col = n0 + nt * 8 + cpair;
-                        const f32x2 b2 = pk(bias[col], bias[col + 1]);
-#pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            float h0, h1;
-                            upk(gelu2(add2(pk(acc[nt][2 * hh], acc[nt][2 * hh + 1]), b2)), h0, h1);
-                            if (layer < 2) {
-                                *reinterpret_cast<__nv_bfloat162*>(Hs + (m0 + g + hh * 8) * kLdH + col) =
-                                    __floats2bfloat162_rn(h0, h1);
-                            } else {
-                                acc[nt][2 * hh] = h0;
-                                acc[nt][2 * hh + 1] = h1;
-                            }
-                        }
-                    }
-                    if (layer < 2) pair_sync(rb);   // both halves of the rows written
-                }
-                // output: this warp's 64 columns, then the two halves summed
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const int col = n0 + nt * 8 + cpair;
-                    const float w0 = W4s[col], w1 = W4s[col + 1];
-                    s0 += acc[nt][0] * w0 + acc[nt][1] * w1;
-                    s1 += acc[nt][2] * w0 + acc[nt][3] * w1;
-                }
-                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-                s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-                s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-                if (nh == 1 && (lane & 3) == 0) {
-                    Red[m0 + g] = s0;
-                    Red[m0 + g + 8] = s1;
-                }
-                pair_sync(rb);
-                if (nh == 0 && (lane & 3) == 0) {
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int srow = m0 + g + hh * 8;          // sample = event * 32 + voxel
-                        const int e = c * 4 + (srow >> 5), ql = srow & 31;
-                        if (e < T.count && ql < nq_here) {
-                            const float v = __expf((hh ? s1 : s0) + Red[srow] + b4) - kSurrogateEps;
-                            St[e * 33 + ql] += v > 0.f ? v : 0.f;
-                        }
+                float o = 0.f;
+                ok = tc_network(S, tmem, phase, b4, &o, P.status);
+                if (ok && tid < 128) {
+                    const int e = c * 4 + (tid >> 5), ql = tid & 31;
+                    if (e < T.count && ql < nq_here) {
+                        const float v = __expf(o) - kSurrogateEps;
+                        St[e * 33 + ql] += v > 0.f ? v : 0.f;
                     }
                 }
             }
         }
+        if (!ok) break;
         __syncthreads();
-        for (int i = tid; i < kET * 32; i += kRowSurThreads) {
+        for (int i = tid; i < kET * 32; i += kTcThreads) {
             const int e = i >> 5, ql = i & 31;
             if (e < T.count && ql < nq_here)
                 P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] = St[e * 33 + ql];
@@ -666,6 +874,7 @@ __global__ void __launch_bounds__(kRowSurThreads, 1) k_surrogate_rows(const Surr
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + tid - P.row_base)] = s;
         }
     }
+    tc_teardown(S, tmem, phase);
 }
 
 }  // namespace mlp
@@ -687,6 +896,7 @@ struct lm_surrogate {
     int64_t step = 0;
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
+    int* status = nullptr;   // device status word of the tensor-core forward
 };
 
 namespace lmmew {
@@ -707,7 +917,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     if (!attr_set) {
         LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_surrogate_rows,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)mlp::kRowSurrogateSmem));
+                                        (int)mlp::kTcSmem));
         attr_set = true;
     }
     mlp::SurrogateRowParams P;
@@ -719,7 +929,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     P.ev_e = L.ev_e;
     P.q_pix = h->d_q_pix;
     P.g8 = h->d_g8;
-    P.cs_dummy = nullptr;
+    P.status = h->d_status;
     P.rows = L.rows;
     P.row_base = L.row_base;
     P.row_stride = L.row_stride;
@@ -741,7 +951,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     }
     P.rho = h->d_rho;
     const int grid = std::min(n_units, h->sm_count);
-    mlp::k_surrogate_rows<<<grid, mlp::kRowSurThreads, mlp::kRowSurrogateSmem, st>>>(P);
+    mlp::k_surrogate_rows<<<grid, mlp::kTcThreads, mlp::kTcSmem, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
@@ -782,8 +992,21 @@ int set_attrs() {
     LMMEW_CUDA(cudaFuncSetAttribute(M::k_back_layer<M::kIn>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)M::back_smem(M::kIn)));
+    LMMEW_CUDA(cudaFuncSetAttribute(M::k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)M::kTcSmem));
     g_attrs = true;
     return LMMEW_OK;
+}
+
+int sm_count() {
+    static int count = 0;
+    if (count == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            count = 1;
+    }
+    return count;
 }
 
 // Full-batch gradient of mean squared error over n samples of BF16 inputs
@@ -878,7 +1101,8 @@ int lm_surrogate_create(uint64_t seed, lm_surrogate** out) {
         cudaMalloc(&s->m2, pb) != cudaSuccess || cudaMalloc(&s->grad, pb) != cudaSuccess ||
         cudaMalloc(&s->W1, sizeof(bf16) * M::kHid * M::kIn) != cudaSuccess ||
         cudaMalloc(&s->W2, sizeof(bf16) * M::kHid * M::kHid) != cudaSuccess ||
-        cudaMalloc(&s->W3, sizeof(bf16) * M::kHid * M::kHid) != cudaSuccess) {
+        cudaMalloc(&s->W3, sizeof(bf16) * M::kHid * M::kHid) != cudaSuccess ||
+        cudaMalloc(&s->status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         lm_surrogate_destroy(s);
         return set_error(LMMEW_ERR_OOM, "cannot allocate the surrogate");
@@ -899,7 +1123,8 @@ int lm_surrogate_create(uint64_t seed, lm_surrogate** out) {
     p[M::kOffB4] = -10.f;
     int rc = LMMEW_OK;
     if (cudaMemcpy(s->p, p.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(s->m1, 0, pb) != cudaSuccess || cudaMemset(s->m2, 0, pb) != cudaSuccess)
+        cudaMemset(s->m1, 0, pb) != cudaSuccess || cudaMemset(s->m2, 0, pb) != cudaSuccess ||
+        cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess)
         rc = set_error(LMMEW_ERR_CUDA, "surrogate initialisation");
     if (rc == LMMEW_OK) rc = refresh_bf16(s, 0);
     if (rc == LMMEW_OK && cudaDeviceSynchronize() != cudaSuccess)
@@ -922,6 +1147,7 @@ int lm_surrogate_destroy(lm_surrogate* s) {
     cudaFree(s->W2);
     cudaFree(s->W3);
     cudaFree(s->scratch);
+    cudaFree(s->status);
     delete s;
     return LMMEW_OK;
 }
@@ -929,6 +1155,12 @@ int lm_surrogate_destroy(lm_surrogate* s) {
 int lm_surrogate_get_params(const lm_surrogate* s, float* host_out) {
     if (!s || !host_out) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
     LMMEW_CUDA(cudaMemcpy(host_out, s->p, sizeof(float) * M::kParams, cudaMemcpyDeviceToHost));
+    int status = 0;
+    LMMEW_CUDA(cudaMemcpy(&status, s->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status & kStatusTimeout) {
+        LMMEW_CUDA(cudaMemset(s->status, 0, sizeof(int)));
+        return set_error(LMMEW_ERR_TIMEOUT, "a tensor-core wait of an earlier forward pass ran out");
+    }
     return LMMEW_OK;
 }
 
@@ -953,8 +1185,9 @@ int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out,
     rc = to_bf16_inputs(s, x, n, &xb, 0, st);
     if (rc != LMMEW_OK) return rc;
     M::Weights w{s->W1, s->W2, s->W3, s->p};
-    M::k_forward<<<(unsigned)((n + M::kTile - 1) / M::kTile), M::kThreads, M::kFwdSmem, st>>>(
-        w, xb, n, out, nullptr);
+    const int64_t tiles = (n + 127) / 128;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());
+    M::k_tc_forward<<<grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status);
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }

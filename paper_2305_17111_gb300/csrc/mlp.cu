@@ -69,6 +69,15 @@ __device__ __forceinline__ float gelu(float z) {
     const float hz = z * 0.5f;
     return fmaf(hz, tanh_fast(u), hz);
 }
+// 2 gelu(z) = z + z tanh(u): the tensor-core kernels fold the factor 1/2 into
+// the next layer's weights (an exact power-of-two scaling, so the BF16
+// activations and every product come out bit for bit the same).
+__device__ __forceinline__ f32x2 gelu2_doubled(f32x2 z) {
+    const f32x2 u = mul2(z, fma2(mul2(z, z), pk(kGeluCK, kGeluCK), pk(kGeluC, kGeluC)));
+    float u0, u1;
+    upk(u, u0, u1);
+    return fma2(z, pk(tanh_fast(u0), tanh_fast(u1)), z);
+}
 __device__ __forceinline__ f32x2 gelu2(f32x2 z) {
     const f32x2 u = mul2(z, fma2(mul2(z, z), pk(kGeluCK, kGeluCK), pk(kGeluC, kGeluC)));
     float u0, u1;
@@ -490,33 +499,38 @@ __global__ void k_batch_indices(uint64_t seed, uint64_t step, int n, uint64_t n_
 // ---------------------------------------------------------------------------
 // Tensor-core (tcgen05) forward pass of the network, for inference.
 //
-// One CTA of 512 threads per SM, persistent over tiles of 128 samples.  W1
-// (K padded from 32 to 64 with zeros), W2 and W3 stay in shared memory in the
-// canonical K-major layout with 128-byte swizzle (8-row x 128-byte atoms,
-// 16-byte chunk j of row r stored at chunk j ^ (r mod 8), 64-element K blocks
-// one after the other); the input tile X (128 x 64) and the hidden tile H
-// (128 x 128) use the same layout.  Per layer one thread issues the
-// M = 128 x N = 128 x K = 16 MMAs (kind::f16, BF16 operands, FP32
-// accumulator in 128 columns of tensor memory) and commits them to an
-// mbarrier; warp w then reads TMEM lanes 32 (w mod 4) .. + 32 (its samples)
-// and columns 32 (w / 4) .. + 32 with tcgen05.ld, adds the bias, applies
-// GELU and writes BF16 into H (the next layer's A operand) -- or, after the
-// last layer, its partial dot with the output weights.
+// One CTA of 512 threads per SM, split into two independent groups of 256
+// threads that share the weights: W1 (K padded from 32 to 64 with zeros), W2
+// and W3 stay in shared memory in the canonical K-major layout with 128-byte
+// swizzle (8-row x 128-byte atoms, 16-byte chunk j of row r stored at chunk
+// j ^ (r mod 8), 64-element K blocks one after the other).  Each group owns an
+// input tile X (128 samples x 64), a hidden tile H (128 x 128) in the same
+// layout, 128 columns of tensor memory, an mbarrier and a named barrier, and
+// works through its own tiles of 128 samples: per layer one of its threads
+// issues the M = 128 x N = 128 x K = 16 MMAs (kind::f16, BF16 operands, FP32
+// accumulator) and commits them to the group's mbarrier; each of its warps
+// then reads TMEM lanes 32 (warp mod 4) .. + 32 (its samples) and 64 of the
+// 128 columns with tcgen05.ld, adds the bias, applies GELU and writes BF16 into
+// H (the next layer's A operand) -- or, after the last layer, its partial dot
+// with the output weights.  While one group waits for its MMAs the other
+// computes, so the tensor core and the epilogues overlap.
 constexpr int kTcThreads = 512;
-constexpr uint32_t kTcCols = 128;                  // TMEM columns (FP32 accumulator 128 x 128)
+constexpr int kGrpThreads = 256;
+constexpr uint32_t kTcCols = 256;                  // TMEM columns: 128 per group (FP32 128 x 128)
 constexpr uint32_t kAtomBlock = 128 * 128;         // bytes of one 64-wide K block of a 128-row tile
 constexpr uint32_t kTcOffW1 = 0;                   // 128 x 64
 constexpr uint32_t kTcOffW2 = kTcOffW1 + kAtomBlock;       // 128 x 128
 constexpr uint32_t kTcOffW3 = kTcOffW2 + 2 * kAtomBlock;   // 128 x 128
-constexpr uint32_t kTcOffX = kTcOffW3 + 2 * kAtomBlock;    // 128 x 64
-constexpr uint32_t kTcOffH = kTcOffX + kAtomBlock;         // 128 x 128
-constexpr uint32_t kTcOffF = kTcOffH + 2 * kAtomBlock;     // floats: bias [3][128], w4 [128], red [4][128]
-constexpr uint32_t kTcOffSt = kTcOffF + (3 * 128 + 128 + 4 * 128) * 4;   // rows: St [128][33]
-constexpr uint32_t kTcOffV = kTcOffSt + 128 * 33 * 4;      // rows: the unit's voxels and events
-constexpr uint32_t kTcOffBar = kTcOffV + (32 * 2 + 32 * 8 + 128 * 2) * 4;   // mbarrier, TMEM, abort
+constexpr uint32_t kTcOffG = kTcOffW3 + 2 * kAtomBlock;    // group tiles: X (1 block) then H (2)
+constexpr uint32_t kGrpTiles = 3 * kAtomBlock;
+constexpr uint32_t kTcOffF = kTcOffG + 2 * kGrpTiles;      // floats: bias [3][128], w4 [128]
+constexpr uint32_t kTcOffGF = kTcOffF + 4 * 128 * 4;       // per group: red, St, unit data
+constexpr uint32_t kGrpRed = 0, kGrpSt = 2 * 128, kGrpV = kGrpSt + 128 * 33;   // float offsets
+constexpr uint32_t kGrpFloats = kGrpV + 32 * 2 + 32 * 8 + 128 * 2;
+constexpr uint32_t kTcOffBar = kTcOffGF + 2 * kGrpFloats * 4;   // 2 mbarriers, TMEM slot, abort
 constexpr size_t kTcSmem = kTcOffBar + 64 + 1024;          // + room to align the base to 1 KB
-static_assert(kTcOffX % 1024 == 0 && kTcOffH % 1024 == 0 && kTcOffW2 % 1024 == 0 &&
-                  kTcOffW3 % 1024 == 0, "swizzle atoms need 1 KB alignment");
+static_assert(kTcOffW2 % 1024 == 0 && kTcOffW3 % 1024 == 0 && kTcOffG % 1024 == 0 &&
+                  kGrpTiles % 1024 == 0, "swizzle atoms need 1 KB alignment");
 static_assert(kTcSmem <= 227 * 1024, "shared memory");
 // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = 128, M = 128
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
@@ -588,9 +602,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
 struct TcShared {
     unsigned char* base;   // 1 KB aligned
     uint32_t sbase;        // its shared-window address
-    uint32_t bar;          // mbarrier address
     uint32_t* tmem_slot;
-    int* abort;
+    int* abort;            // [2]: set by a group's issuing thread when its MMA wait ran out
 };
 
 __device__ __forceinline__ TcShared tc_shared(unsigned char* raw) {
@@ -599,45 +612,95 @@ __device__ __forceinline__ TcShared tc_shared(unsigned char* raw) {
     const uint32_t pad = ((a + 1023u) & ~1023u) - a;
     t.base = raw + pad;
     t.sbase = a + pad;
-    t.bar = t.sbase + kTcOffBar;
-    t.tmem_slot = reinterpret_cast<uint32_t*>(t.base + kTcOffBar + 8);
-    t.abort = reinterpret_cast<int*>(t.base + kTcOffBar + 16);
+    t.tmem_slot = reinterpret_cast<uint32_t*>(t.base + kTcOffBar + 16);
+    t.abort = reinterpret_cast<int*>(t.base + kTcOffBar + 24);
     return t;
 }
 
-// Weights into their swizzled tiles, the padding half of X zeroed, the
-// mbarrier initialised, TMEM allocated (warp 0).  Ends with a CTA barrier;
-// returns the TMEM address.
+// One of the two thread groups of the CTA and its private resources.
+struct TcGroup {
+    int g;          // 0 or 1
+    int gt;         // thread index in the group, 0..255
+    uint32_t x;     // byte offsets of the group's X and H tiles
+    uint32_t h;
+    float* f;       // the group's floats: red [2][128], St [128][33], unit data
+    uint32_t tmem;  // its 128 accumulator columns
+    uint32_t bar;   // its mbarrier
+};
+
+__device__ __forceinline__ TcGroup tc_group(const TcShared& S, uint32_t tmem_base) {
+    TcGroup G;
+    G.g = threadIdx.x >> 8;
+    G.gt = threadIdx.x & 255;
+    G.x = kTcOffG + (uint32_t)G.g * kGrpTiles;
+    G.h = G.x + kAtomBlock;
+    G.f = reinterpret_cast<float*>(S.base + kTcOffGF) + G.g * kGrpFloats;
+    G.tmem = tmem_base + (uint32_t)G.g * 128u;
+    G.bar = S.sbase + kTcOffBar + 8u * (uint32_t)G.g;
+    return G;
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, 256;" ::"r"(g + 1) : "memory");
+}
+
+// Weights into their swizzled tiles, the padding half of both X tiles zeroed,
+// the mbarriers initialised, TMEM allocated (warp 0).  Ends with a CTA
+// barrier; returns the TMEM base address.
 __device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
     const int tid = threadIdx.x;
+    // W1 with b1 in input columns 32 (BF16 high part) and 33 (the remainder), so
+    // the first layer's bias comes out of the MMA (the inputs carry 1 there)
     for (int i = tid; i < 128 * 8; i += kTcThreads) {
         const int n = i >> 3, j = i & 7;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (j < 4) v = *reinterpret_cast<const uint4*>(w.W1 + (size_t)n * kIn + j * 8);
+        if (j < 4) {
+            v = *reinterpret_cast<const uint4*>(w.W1 + (size_t)n * kIn + j * 8);
+        } else if (j == 4) {
+            const float b = w.p[kOffB1 + n];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+            const __nv_bfloat162 t = __halves2bfloat162(hi, __float2bfloat16_rn(b - __bfloat162float(hi)));
+            v.x = *reinterpret_cast<const uint32_t*>(&t);
+        }
         *reinterpret_cast<uint4*>(S.base + kTcOffW1 + sw_chunk(n, 0, j)) = v;
     }
+    // W2, W3 halved: the activations feeding them are 2 gelu
+    const __nv_bfloat162 half2 = __float2bfloat162_rn(0.5f);
     for (int i = tid; i < 128 * 16; i += kTcThreads) {
         const int n = i >> 4, c = i & 15;
-        *reinterpret_cast<uint4*>(S.base + kTcOffW2 + sw_chunk(n, c >> 3, c & 7)) =
-            *reinterpret_cast<const uint4*>(w.W2 + (size_t)n * kHid + c * 8);
-        *reinterpret_cast<uint4*>(S.base + kTcOffW3 + sw_chunk(n, c >> 3, c & 7)) =
-            *reinterpret_cast<const uint4*>(w.W3 + (size_t)n * kHid + c * 8);
+        uint4 a = *reinterpret_cast<const uint4*>(w.W2 + (size_t)n * kHid + c * 8);
+        uint4 b = *reinterpret_cast<const uint4*>(w.W3 + (size_t)n * kHid + c * 8);
+        __nv_bfloat162* pa = reinterpret_cast<__nv_bfloat162*>(&a);
+        __nv_bfloat162* pb = reinterpret_cast<__nv_bfloat162*>(&b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            pa[k] = __hmul2(pa[k], half2);
+            pb[k] = __hmul2(pb[k], half2);
+        }
+        *reinterpret_cast<uint4*>(S.base + kTcOffW2 + sw_chunk(n, c >> 3, c & 7)) = a;
+        *reinterpret_cast<uint4*>(S.base + kTcOffW3 + sw_chunk(n, c >> 3, c & 7)) = b;
     }
-    for (int i = tid; i < 128 * 4; i += kTcThreads)
-        *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(i >> 2, 0, 4 + (i & 3))) =
-            make_uint4(0u, 0u, 0u, 0u);
+    // input columns 32, 33 = 1 (the first layer's bias), 34..63 = 0
+    const __nv_bfloat162 one2 = __float2bfloat162_rn(1.f);
+    for (int i = tid; i < 2 * 128 * 4; i += kTcThreads) {
+        const int g = i >> 9, r = (i >> 2) & 127, j = 4 + (i & 3);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (j == 4) v.x = *reinterpret_cast<const uint32_t*>(&one2);
+        *reinterpret_cast<uint4*>(S.base + kTcOffG + g * kGrpTiles + sw_chunk(r, 0, j)) = v;
+    }
     float* F = reinterpret_cast<float*>(S.base + kTcOffF);
     for (int i = tid; i < 3 * kHid; i += kTcThreads) {
         const int l = i / kHid;
-        F[i] = w.p[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + i % kHid];
+        F[i] = l == 0 ? 0.f : w.p[(l == 1 ? kOffB2 : kOffB3) + i % kHid];
     }
-    for (int i = tid; i < kHid; i += kTcThreads) F[3 * kHid + i] = w.p[kOffW4 + i];
+    for (int i = tid; i < kHid; i += kTcThreads) F[3 * kHid + i] = 0.5f * w.p[kOffW4 + i];
     if (tid == 0) {
-        mbar_init(S.bar, 1);
+        mbar_init(S.sbase + kTcOffBar, 1);
+        mbar_init(S.sbase + kTcOffBar + 8, 1);
         mbar_fence_init();
-        *S.abort = 0;
+        S.abort[0] = S.abort[1] = 0;
     }
-    if (tid < 32) tc_alloc(S.sbase + kTcOffBar + 8, kTcCols);
+    if (tid < 32) tc_alloc(S.sbase + kTcOffBar + 16, kTcCols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -645,82 +708,99 @@ __device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
     return *S.tmem_slot;
 }
 
-// After an MMA wait ran out, wait once more (bounded) for the MMAs in
-// flight before the tensor memory they write is released.
-__device__ void tc_teardown(const TcShared& S, uint32_t tmem, uint32_t phase) {
+// After an MMA wait ran out, each group waits once more (bounded) for its MMAs
+// in flight before the tensor memory they write is released.
+__device__ void tc_teardown(const TcShared& S, const TcGroup& G, uint32_t tmem_base,
+                            uint32_t phase) {
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && *S.abort && phase > 0) mbar_wait_bounded(S.bar, (phase - 1) & 1);
+    if (G.gt == 0 && S.abort[G.g] && phase > 0) mbar_wait_bounded(G.bar, (phase - 1) & 1);
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32) tc_dealloc(tmem, kTcCols);
+    if (threadIdx.x < 32) tc_dealloc(tmem_base, kTcCols);
 }
 
-// The network on the 128 samples whose inputs sit in X (written, fenced and
-// followed by a CTA barrier).  Returns, in threads of warps 0..3, the output
-// of sample 32 warp + lane; false if an MMA wait ran out (the status word is
-// set and the caller stops).
-__device__ bool tc_network(const TcShared& S, uint32_t tmem, uint32_t& phase, float b4,
+// The network on the group's 128 samples whose inputs sit in its X tile
+// (written, fenced and followed by a group barrier).  Returns, in the group's
+// threads 0..127, the output of sample (group thread index); false if an MMA
+// wait ran out (the status word is set and the caller stops).
+__device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase, float b4,
                            float* out_row, int* status) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lq = warp & 3, cq = warp >> 2;
+    const int wg = G.gt >> 5, lane = G.gt & 31;
+    const int lq = wg & 3, ch = wg >> 2;
     const int row = lq * 32 + lane;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
-    float* red = reinterpret_cast<float*>(S.base + kTcOffF) + 4 * kHid;
+    float* red = G.f + kGrpRed;
     for (int layer = 0; layer < 3; ++layer) {
-        if (tid == 0) {
+        if (G.gt == 0) {
             tc_fence_after();
-            const uint32_t a0 = S.sbase + (layer == 0 ? kTcOffX : kTcOffH);
+            const uint32_t a0 = S.sbase + (layer == 0 ? G.x : G.h);
             const uint32_t b0 = S.sbase + (layer == 0 ? kTcOffW1 : layer == 1 ? kTcOffW2 : kTcOffW3);
             const int ksteps = layer == 0 ? 4 : 8;
             for (int ks = 0; ks < ksteps; ++ks) {
                 const uint32_t off = (uint32_t)(ks >> 2) * kAtomBlock + (uint32_t)(ks & 3) * 32u;
-                tc_mma(tmem, umma_desc(a0 + off), umma_desc(b0 + off), kTcIdesc, ks > 0 ? 1u : 0u);
+                tc_mma(G.tmem, umma_desc(a0 + off), umma_desc(b0 + off), kTcIdesc, ks > 0 ? 1u : 0u);
             }
-            tc_commit(S.bar);
-            if (!mbar_wait_bounded(S.bar, phase & 1)) {
-                *S.abort = 1;
+            tc_commit(G.bar);
+            if (!mbar_wait_bounded(G.bar, phase & 1)) {
+                S.abort[G.g] = 1;
                 atomicOr(status, kStatusTimeout);
             }
         }
         ++phase;
-        __syncthreads();
-        if (*S.abort) return false;
+        group_sync(G.g);
+        if (S.abort[G.g]) return false;
         tc_fence_after();
-        float v[32];
-        tc_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(cq * 32), v);
-        const float* bias = F + layer * kHid + cq * 32;
-        if (layer < 2) {
-            uint32_t hb[16];
+        float sacc = 0.f;
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-                float h0, h1;
-                upk(gelu2(add2(pk(v[i], v[i + 1]), pk(bias[i], bias[i + 1]))), h0, h1);
-                const __nv_bfloat162 t = __floats2bfloat162_rn(h0, h1);
-                hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t);
+        for (int half = 0; half < 2; ++half) {
+            const int cb = ch * 64 + half * 32;   // columns cb .. cb + 31
+            float v[32];
+            tc_ld32(G.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb, v);
+            const float4* bias4 = reinterpret_cast<const float4*>(F + layer * kHid + cb);
+            if (layer < 2) {
+                uint32_t hb[16];
+#pragma unroll
+                for (int i = 0; i < 32; i += 4) {
+                    f32x2 z0 = pk(v[i], v[i + 1]), z1 = pk(v[i + 2], v[i + 3]);
+                    if (layer > 0) {   // the first layer's bias comes out of the MMA
+                        const float4 b = bias4[i >> 2];
+                        z0 = add2(z0, pk(b.x, b.y));
+                        z1 = add2(z1, pk(b.z, b.w));
+                    }
+                    float h0, h1, h2, h3;
+                    upk(gelu2_doubled(z0), h0, h1);
+                    upk(gelu2_doubled(z1), h2, h3);
+                    const __nv_bfloat162 t0 = __floats2bfloat162_rn(h0, h1);
+                    const __nv_bfloat162 t1 = __floats2bfloat162_rn(h2, h3);
+                    hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t0);
+                    hb[(i >> 1) + 1] = *reinterpret_cast<const uint32_t*>(&t1);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, ch, half * 4 + c)) =
+                        make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
+            } else {
+                const float4* w44 = reinterpret_cast<const float4*>(F + 3 * kHid + cb);
+#pragma unroll
+                for (int i = 0; i < 32; i += 4) {
+                    const float4 b = bias4[i >> 2], ww = w44[i >> 2];
+                    float h0, h1, h2, h3;
+                    upk(gelu2_doubled(add2(pk(v[i], v[i + 1]), pk(b.x, b.y))), h0, h1);
+                    upk(gelu2_doubled(add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w))), h2, h3);
+                    sacc = fmaf(h0, ww.x, sacc);
+                    sacc = fmaf(h1, ww.y, sacc);
+                    sacc = fmaf(h2, ww.z, sacc);
+                    sacc = fmaf(h3, ww.w, sacc);
+                }
             }
-            const int kb = cq >> 1, j0 = (cq & 1) * 4;
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                *reinterpret_cast<uint4*>(S.base + kTcOffH + sw_chunk(row, kb, j0 + c)) =
-                    make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
-            fence_async_smem();
-        } else {
-            const float* w4 = F + 3 * kHid + cq * 32;
-            float sacc = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-                float h0, h1;
-                upk(gelu2(add2(pk(v[i], v[i + 1]), pk(bias[i], bias[i + 1]))), h0, h1);
-                sacc = fmaf(h0, w4[i], sacc);
-                sacc = fmaf(h1, w4[i + 1], sacc);
-            }
-            red[cq * 128 + row] = sacc;
         }
+        if (layer < 2) fence_async_smem();
+        else red[ch * 128 + row] = sacc;
         tc_fence_before();
-        __syncthreads();
+        group_sync(G.g);
     }
-    if (cq == 0) *out_row = ((red[row] + red[128 + row]) + (red[256 + row] + red[384 + row])) + b4;
+    if (ch == 0) *out_row = (red[row] + red[128 + row]) + b4;
     return true;
 }
 
@@ -729,27 +809,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const b
                                                               float* out, int* status) {
     extern __shared__ unsigned char smem_raw[];
     const TcShared S = tc_shared(smem_raw);
-    const uint32_t tmem = tc_setup(S, w);
+    const uint32_t tmem_base = tc_setup(S, w);
+    const TcGroup G = tc_group(S, tmem_base);
     const float b4 = w.p[kOffB4];
-    const int tid = threadIdx.x;
     uint32_t phase = 0;
     const int64_t n_tiles = (n + 127) / 128;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int64_t t = (int64_t)blockIdx.x * 2 + G.g; t < n_tiles; t += (int64_t)gridDim.x * 2) {
         const int64_t base = t * 128;
-        {   // 128 rows x 4 chunks of 8 inputs
-            const int r = tid >> 2, j = tid & 3;
+        for (int k = G.gt; k < 128 * 4; k += kGrpThreads) {   // 128 rows x 4 chunks of 8 inputs
+            const int r = k & 127, j = k >> 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (base + r < n) v = *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + j * 8);
-            *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(r, 0, j)) = v;
+            *reinterpret_cast<uint4*>(S.base + G.x + sw_chunk(r, 0, j)) = v;
         }
         fence_async_smem();
-        __syncthreads();
+        group_sync(G.g);
         float o = 0.f;
-        if (!tc_network(S, tmem, phase, b4, &o, status)) break;
-        const int row = (tid >> 5) * 32 + (tid & 31);
-        if (tid < 128 && base + row < n) out[base + row] = o;
+        if (!tc_network(S, G, phase, b4, &o, status)) break;
+        if (G.gt < 128 && base + G.gt < n) out[base + G.gt] = o;
     }
-    tc_teardown(S, tmem, phase);
+    tc_teardown(S, G, tmem_base, phase);
 }
 
 struct SurrogateRowParams {
@@ -778,56 +857,56 @@ struct SurrogateRowParams {
 // The surrogate inside the row pipeline: after k_row wrote the unscattered
 // part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
 // adds sum_w max(exp(net(x_w)) - eps, 0) for every (event, voxel) and writes
-// the unit's partial forward sums.  Passes of 128 samples: 4 events x 32
-// voxels, one line.
+// the unit's partial forward sums.  Each thread group takes every other unit;
+// passes of 128 samples: 4 events x 32 voxels, one line.
 __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
     extern __shared__ unsigned char smem_raw[];
     const TcShared S = tc_shared(smem_raw);
-    const uint32_t tmem = tc_setup(S, P.w);
+    const uint32_t tmem_base = tc_setup(S, P.w);
+    const TcGroup G = tc_group(S, tmem_base);
     const float b4 = P.w.p[kOffB4];
-    float* St = reinterpret_cast<float*>(S.base + kTcOffSt);   // [128 events][33]
-    float* Vxy = reinterpret_cast<float*>(S.base + kTcOffV);   // [32] voxel centre (x, y), cm
-    float* Vg8 = Vxy + 32 * 2;                                   // [32][8] rho line integrals
-    float* Eeu = Vg8 + 32 * 8;                                   // [128] (recorded energy, bin centre)
-    const int tid = threadIdx.x;
+    float* St = G.f + kGrpSt;             // [128 events][33]
+    float* Vxy = G.f + kGrpV;             // [32] voxel centre (x, y), cm
+    float* Vg8 = Vxy + 32 * 2;            // [32][8] rho line integrals
+    float* Eeu = Vg8 + 32 * 8;            // [128] (recorded energy, bin centre)
+    const int gt = G.gt;
     uint32_t phase = 0;
     const int n_tiles = P.tile_end - P.tile_begin;
     const int n_units = n_tiles * P.nqt;
     const float half_det = 0.5f * P.B * P.bin_w;
     bool ok = true;
-    for (int unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x) {
+    for (int unit = blockIdx.x * 2 + G.g; unit < n_units && ok; unit += gridDim.x * 2) {
         const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
         const int qt = unit % P.nqt;
         const int nq_here = min(32, P.nq - qt * 32);
-        __syncthreads();   // the previous unit is done with St
-        for (int i = tid; i < kET * 32; i += kTcThreads) {
+        group_sync(G.g);   // the group's previous unit is done with St and the unit data
+        for (int i = gt; i < kET * 32; i += kGrpThreads) {
             const int e = i >> 5, ql = i & 31;
             St[e * 33 + ql] = (e < T.count && ql < nq_here)
                                   ? P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql]
                                   : 0.f;
         }
-        // the unit's voxels and events, once
-        if (tid < 32 && tid < nq_here) {
-            const int pix = P.q_pix[qt * 32 + tid];
-            Vxy[2 * tid] = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
-            Vxy[2 * tid + 1] = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
+        if (gt < 32 && gt < nq_here) {
+            const int pix = P.q_pix[qt * 32 + gt];
+            Vxy[2 * gt] = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
+            Vxy[2 * gt + 1] = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
         }
-        if (tid < 32 * 8 && (tid >> 3) < nq_here)
-            Vg8[tid] = P.g8[((size_t)T.a * P.nq + qt * 32 + (tid >> 3)) * 8 + (tid & 7)];
-        if (tid < T.count) {
-            Eeu[2 * tid] = P.ev_e[T.begin + tid];
-            Eeu[2 * tid + 1] = -half_det + (P.ev_bin[T.begin + tid] + 0.5f) * P.bin_w;
+        if ((gt >> 3) < nq_here)
+            Vg8[gt] = P.g8[((size_t)T.a * P.nq + qt * 32 + (gt >> 3)) * 8 + (gt & 7)];
+        if (gt < T.count) {
+            Eeu[2 * gt] = P.ev_e[T.begin + gt];
+            Eeu[2 * gt + 1] = -half_det + (P.ev_bin[T.begin + gt] + 0.5f) * P.bin_w;
         }
-        __syncthreads();
+        group_sync(G.g);
         const float th = 6.283185307179586f * T.a / P.A;
         float ca, sa;
         sincosf(th, &sa, &ca);
         for (int c = 0; c < (T.count + 3) / 4 && ok; ++c) {
             for (int wl = 0; wl < P.W && ok; ++wl) {
-                // inputs 8 j .. 8 j + 7 of sample s = tid / 4 (event 4c + s / 32,
-                // voxel s mod 32) into chunk j = tid mod 4 of row s of X
-                {
-                    const int smp = tid >> 2, j = tid & 3;
+                // inputs 8 j .. 8 j + 7 of sample smp (event 4c + smp / 32, voxel
+                // smp mod 32) into chunk j of row smp of X
+                for (int k = gt; k < 128 * 4; k += kGrpThreads) {
+                    const int smp = k & 127, j = k >> 7;   // j is the same across a warp
                     const int e = c * 4 + (smp >> 5), ql = smp & 31;
                     float f8[8];
                     if (e < T.count && ql < nq_here) {
@@ -836,23 +915,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
                                                  P.mu_line[wl], Vg8 + ql * 8, P.rho, P.n, P.h, f8);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) f8[k] = 0.f;
+                        for (int i = 0; i < 8; ++i) f8[i] = 0.f;
                     }
                     uint32_t u[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const __nv_bfloat162 t = __floats2bfloat162_rn(f8[2 * k], f8[2 * k + 1]);
-                        u[k] = *reinterpret_cast<const uint32_t*>(&t);
+                    for (int i = 0; i < 4; ++i) {
+                        const __nv_bfloat162 t = __floats2bfloat162_rn(f8[2 * i], f8[2 * i + 1]);
+                        u[i] = *reinterpret_cast<const uint32_t*>(&t);
                     }
-                    *reinterpret_cast<uint4*>(S.base + kTcOffX + sw_chunk(smp, 0, j)) =
+                    *reinterpret_cast<uint4*>(S.base + G.x + sw_chunk(smp, 0, j)) =
                         make_uint4(u[0], u[1], u[2], u[3]);
                 }
                 fence_async_smem();
-                __syncthreads();
+                group_sync(G.g);
                 float o = 0.f;
-                ok = tc_network(S, tmem, phase, b4, &o, P.status);
-                if (ok && tid < 128) {
-                    const int e = c * 4 + (tid >> 5), ql = tid & 31;
+                ok = tc_network(S, G, phase, b4, &o, P.status);
+                if (ok && gt < 128) {
+                    const int e = c * 4 + (gt >> 5), ql = gt & 31;
                     if (e < T.count && ql < nq_here) {
                         const float v = __expf(o) - kSurrogateEps;
                         St[e * 33 + ql] += v > 0.f ? v : 0.f;
@@ -861,20 +940,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
             }
         }
         if (!ok) break;
-        __syncthreads();
-        for (int i = tid; i < kET * 32; i += kTcThreads) {
+        group_sync(G.g);
+        for (int i = gt; i < kET * 32; i += kGrpThreads) {
             const int e = i >> 5, ql = i & 31;
             if (e < T.count && ql < nq_here)
                 P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] = St[e * 33 + ql];
         }
-        if (P.lam && tid < T.count) {
+        if (P.lam && gt < T.count) {
             const float* lam = P.lam + (size_t)T.r * P.lam_stride;
             float s = 0.f;
-            for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], St[tid * 33 + ql], s);
-            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + tid - P.row_base)] = s;
+            for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], St[gt * 33 + ql], s);
+            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + gt - P.row_base)] = s;
         }
     }
-    tc_teardown(S, tmem, phase);
+    tc_teardown(S, G, tmem_base, phase);
 }
 
 }  // namespace mlp
@@ -950,7 +1029,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
         P.e_line[w] = (float)h->mc.line_e[w];
     }
     P.rho = h->d_rho;
-    const int grid = std::min(n_units, h->sm_count);
+    const int grid = std::min((n_units + 1) / 2, h->sm_count);
     mlp::k_surrogate_rows<<<grid, mlp::kTcThreads, mlp::kTcSmem, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
@@ -1186,7 +1265,7 @@ int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out,
     if (rc != LMMEW_OK) return rc;
     M::Weights w{s->W1, s->W2, s->W3, s->p};
     const int64_t tiles = (n + 127) / 128;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count());
+    const unsigned grid = (unsigned)std::min<int64_t>((tiles + 1) / 2, sm_count());
     M::k_tc_forward<<<grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status);
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -40,7 +40,7 @@ def rand_image(ph, seed):
     return (rng.uniform(0.2, 3.0, ph.rho.size) * (ph.rho.reshape(-1) > 0)).astype(np.float32)
 
 
-@pytest.mark.parametrize("name,groups", [("lmmew_64", 8), ("lmmew_128", 3)])
+@pytest.mark.parametrize("name,groups", [("lmmew_64", 8), ("lmmew_128", 3), ("lmmew_128_2m", 2)])
 def test_forward_sampled_parity_full_size(name, groups):
     sc = preset(name)
     ph = sc.make_phantom()

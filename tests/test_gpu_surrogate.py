@@ -425,3 +425,46 @@ def test_surrogate_gain_over_the_scatter_free_model():
     assert fwd_err["surrogate"] < 0.5 * fwd_err["none"], fwd_err
     assert img_err["surrogate"] < img_err["none"], img_err
     assert roi_err["surrogate"] < roi_err["none"], roi_err
+
+
+@pytest.mark.parametrize("model", ["surrogate", "none"])
+def test_batched_reconstruction_with_scatter_models_equals_single(model):
+    """lm_osem_batch under the surrogate and the scatter-free model gives every
+    realisation the image lm_osem gives it alone, bit for bit (each row value
+    is computed the same way whatever tile it lands in)."""
+    sc, ph, orc, gpu, ev, dev = _fine_model()
+    s, _ = _trained_surrogate() if model == "surrogate" else (None, None)
+    sizes = [500, 0, 333, 800]
+    rng = np.random.default_rng(9)
+    evs = [ev.subset(rng.choice(len(ev), size=n, replace=False)) for n in sizes]
+    devs = [lm.DeviceEvents.from_list(e) for e in evs]
+    lam0 = np.stack([(rng.uniform(0.5, 2.0, ph.rho.size) * (ph.rho.reshape(-1) > 0))
+                     for _ in sizes]).astype(np.float32)
+    gpu.set_scatter_model(model, s)
+    try:
+        imgs = torch.from_numpy(lam0.copy()).cuda()
+        gpu.osem_batch(devs, imgs, 4, 2)
+        for i, d in enumerate(devs):
+            one = torch.from_numpy(lam0[i].copy()).cuda()
+            gpu.osem(d, one, 4, 2)
+            assert torch.equal(imgs[i], one), f"realisation {i}"
+    finally:
+        gpu.set_scatter_model("exact")
+
+
+def test_surrogate_backprojection_uses_the_surrogate_rows():
+    """Back projection under the surrogate model is the adjoint of its forward
+    projection: <A x, w> = <x, A^T w> in FP64 to FP32 rounding."""
+    sc, ph, orc, gpu, ev, dev = _fine_model()
+    s, _ = _trained_surrogate()
+    rng = np.random.default_rng(4)
+    x = (rng.uniform(0.2, 3, ph.rho.size) * (ph.rho.reshape(-1) > 0)).astype(np.float32)
+    wv = rng.uniform(0.1, 1.0, len(ev)).astype(np.float32)
+    gpu.set_scatter_model("surrogate", s)
+    try:
+        y = gpu.forward(dev, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+        bp = gpu.backproject(dev, torch.from_numpy(wv).cuda()).cpu().numpy().astype(np.float64)
+    finally:
+        gpu.set_scatter_model("exact")
+    lhs, rhs = float(y @ wv), float(x.astype(np.float64) @ bp)
+    assert lhs == pytest.approx(rhs, rel=2e-5)

@@ -242,6 +242,25 @@ def _chunk(args):
     return _simulate_chunk(sc, ph.rho, cdf, marcher, rng, CHUNK_PHOTONS, z_plane)
 
 
+def _pool_map(fn, tasks, processes):
+    """fn over tasks in a pool of fresh interpreters (spawn).  The pool starts
+    with an empty stand-in for __main__, so the workers import only this
+    module and never re-run the caller's script (whose top level may itself
+    call simulate)."""
+    import multiprocessing as mp
+    import sys
+    import types
+    main = sys.modules.get("__main__")
+    sys.modules["__main__"] = types.ModuleType("__main__")
+    try:
+        pool = mp.get_context("spawn").Pool(processes)
+    finally:
+        if main is not None:
+            sys.modules["__main__"] = main
+    with pool:
+        return pool.map(fn, tasks)
+
+
 def _workers() -> int:
     try:
         n = len(os.sched_getaffinity(0))
@@ -255,8 +274,8 @@ def simulate(sc: Scenario, n_events: int | None = None, seed: int | None = None,
     """Draw ``n_events`` list-mode events (default: the scenario's count/seed).
 
     Chunks of CHUNK_PHOTONS candidate decays are simulated in order and
-    concatenated; with more than a few chunks they run in a process pool
-    (started with spawn), which changes nothing in the result."""
+    concatenated; with more than a few chunks they run in a pool of worker
+    processes, which changes nothing in the result."""
     n_events = sc.n_events if n_events is None else int(n_events)
     seed = sc.seed if seed is None else int(seed)
     ph = sc.make_phantom()
@@ -270,9 +289,8 @@ def simulate(sc: Scenario, n_events: int | None = None, seed: int | None = None,
         n_more = int(np.ceil((n_events - total) / per_chunk * 1.05)) + 1
         workers = _workers() if workers is None else int(workers)
         if n_more >= 3 and workers > 1:
-            import multiprocessing as mp
-            with mp.get_context("spawn").Pool(min(workers, n_more)) as pool:
-                more = pool.map(_chunk, [(sc, act, seed, i + k) for k in range(n_more)])
+            more = _pool_map(_chunk, [(sc, act, seed, i + k) for k in range(n_more)],
+                             min(workers, n_more))
             parts += more
             total += sum(len(p) for p in more)
             i += n_more

@@ -33,3 +33,22 @@ def test_event_ranges_and_spectrum():
     e0s = np.asarray(sc.line_keV)[ev.line[sca]]
     assert np.mean(ev.energy[sca] < e0s + 3 * 0.10 * np.sqrt(140.0 * e0s)) > 0.99
     assert 0.05 < sca.mean() < 0.8
+
+
+def test_pooled_generation_from_an_unguarded_script(tmp_path):
+    """A script without a main guard may call simulate at its top level: the
+    worker processes must not re-run it."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "top_level.py"
+    script.write_text(
+        "import sys\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from synthetic import preset, simulate\n"
+        "ev = simulate(preset('lmmew_32'), n_events=130_000, seed=3, workers=2)\n"
+        "print('events', len(ev))\n")
+    out = subprocess.run([sys.executable, str(script)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert "events 130000" in out.stdout

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -989,16 +990,35 @@ const void* surrogate_weights(const lm_surrogate* s, void* out_weights) {
     return out_weights;
 }
 
+// Shared-memory opt-in of the surrogate kernels.  The attribute belongs to the
+// current device, so it is set once per device the library runs on.
+int surrogate_kernel_attrs() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    LMMEW_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return LMMEW_OK;
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::kFwdSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_back_layer<mlp::kHid>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::back_smem(mlp::kHid)));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_back_layer<mlp::kIn>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::back_smem(mlp::kIn)));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::kTcSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_surrogate_rows,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::kTcSmem));
+    done.fetch_or(bit);
+    return LMMEW_OK;
+}
+
 int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
     if (n_units <= 0) return LMMEW_OK;
-    static bool attr_set = false;
-    if (!attr_set) {
-        LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_surrogate_rows,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)mlp::kTcSmem));
-        attr_set = true;
-    }
+    int rc = surrogate_kernel_attrs();
+    if (rc != LMMEW_OK) return rc;
     mlp::SurrogateRowParams P;
     surrogate_weights(h->surrogate, &P.w);
     P.tiles = L.tiles;
@@ -1060,32 +1080,14 @@ int refresh_bf16(lm_surrogate* s, cudaStream_t st) {
     return LMMEW_OK;
 }
 
-bool g_attrs = false;
-int set_attrs() {
-    if (g_attrs) return LMMEW_OK;
-    LMMEW_CUDA(cudaFuncSetAttribute(M::k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)M::kFwdSmem));
-    LMMEW_CUDA(cudaFuncSetAttribute(M::k_back_layer<M::kHid>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)M::back_smem(M::kHid)));
-    LMMEW_CUDA(cudaFuncSetAttribute(M::k_back_layer<M::kIn>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)M::back_smem(M::kIn)));
-    LMMEW_CUDA(cudaFuncSetAttribute(M::k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)M::kTcSmem));
-    g_attrs = true;
-    return LMMEW_OK;
-}
+int set_attrs() { return surrogate_kernel_attrs(); }
 
 int sm_count() {
-    static int count = 0;
-    if (count == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            count = 1;
-    }
-    return count;
+    int dev = 0, count = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return count > 0 ? count : 1;
 }
 
 // Full-batch gradient of mean squared error over n samples of BF16 inputs

@@ -500,35 +500,37 @@ __global__ void k_batch_indices(uint64_t seed, uint64_t step, int n, uint64_t n_
 // ---------------------------------------------------------------------------
 // Tensor-core (tcgen05) forward pass of the network, for inference.
 //
-// One CTA of 512 threads per SM, split into two independent groups of 256
-// threads that share the weights: W1 (K padded from 32 to 64 with zeros), W2
-// and W3 stay in shared memory in the canonical K-major layout with 128-byte
-// swizzle (8-row x 128-byte atoms, 16-byte chunk j of row r stored at chunk
-// j ^ (r mod 8), 64-element K blocks one after the other).  Each group owns an
-// input tile X (128 samples x 64), a hidden tile H (128 x 128) in the same
-// layout, 128 columns of tensor memory, an mbarrier and a named barrier, and
-// works through its own tiles of 128 samples: per layer one of its threads
-// issues the M = 128 x N = 128 x K = 16 MMAs (kind::f16, BF16 operands, FP32
-// accumulator) and commits them to the group's mbarrier; each of its warps
-// then reads TMEM lanes 32 (warp mod 4) .. + 32 (its samples) and 64 of the
-// 128 columns with tcgen05.ld, adds the bias, applies GELU and writes BF16 into
-// H (the next layer's A operand) -- or, after the last layer, its partial dot
-// with the output weights.  While one group waits for its MMAs the other
-// computes, so the tensor core and the epilogues overlap.
+// One CTA of 512 threads per SM, split into four independent groups of 128
+// threads (one warp per 32-lane quarter of tensor memory) that share the
+// weights: W1 (K padded from 32 to 64), W2 and W3 stay in shared memory in the
+// canonical K-major layout with 128-byte swizzle (8-row x 128-byte atoms,
+// 16-byte chunk j of row r stored at chunk j ^ (r mod 8), 64-element K blocks
+// one after the other).  Each group owns a hidden tile H (128 samples x 128)
+// in the same layout -- its first K block doubles as the input tile X, which
+// the layer-0 MMAs have consumed before the first epilogue overwrites it --
+// 128 columns of tensor memory, an mbarrier and a named barrier, and works
+// through its own tiles of 128 samples: per layer one of its threads issues
+// the M = 128 x N = 128 x K = 16 MMAs (kind::f16, BF16 operands, FP32
+// accumulator) and commits them to the group's mbarrier; each warp then reads
+// its 32 TMEM lanes (its samples) x 128 columns with tcgen05.ld, adds the
+// bias, applies GELU and writes BF16 into H (the next layer's A operand) --
+// or, after the last layer, the dot with the output weights.  While some
+// groups wait for their MMAs the others compute, so the tensor core and the
+// epilogues overlap.
 constexpr int kTcThreads = 512;
-constexpr int kGrpThreads = 256;
-constexpr uint32_t kTcCols = 256;                  // TMEM columns: 128 per group (FP32 128 x 128)
+constexpr int kTcGroups = 4;
+constexpr int kGrpThreads = 128;
+constexpr uint32_t kTcCols = 512;                  // TMEM columns: 128 per group (FP32 128 x 128)
 constexpr uint32_t kAtomBlock = 128 * 128;         // bytes of one 64-wide K block of a 128-row tile
 constexpr uint32_t kTcOffW1 = 0;                   // 128 x 64
 constexpr uint32_t kTcOffW2 = kTcOffW1 + kAtomBlock;       // 128 x 128
 constexpr uint32_t kTcOffW3 = kTcOffW2 + 2 * kAtomBlock;   // 128 x 128
-constexpr uint32_t kTcOffG = kTcOffW3 + 2 * kAtomBlock;    // group tiles: X (1 block) then H (2)
-constexpr uint32_t kGrpTiles = 3 * kAtomBlock;
-constexpr uint32_t kTcOffF = kTcOffG + 2 * kGrpTiles;      // floats: bias [3][128], w4 [128]
-constexpr uint32_t kTcOffGF = kTcOffF + 4 * 128 * 4;       // per group: red, St, unit data
-constexpr uint32_t kGrpRed = 0, kGrpSt = 2 * 128, kGrpV = kGrpSt + 128 * 33;   // float offsets
-constexpr uint32_t kGrpFloats = kGrpV + 32 * 2 + 32 * 8 + 128 * 2;
-constexpr uint32_t kTcOffBar = kTcOffGF + 2 * kGrpFloats * 4;   // 2 mbarriers, TMEM slot, abort
+constexpr uint32_t kTcOffG = kTcOffW3 + 2 * kAtomBlock;    // group tiles H (X = its first block)
+constexpr uint32_t kGrpTiles = 2 * kAtomBlock;
+constexpr uint32_t kTcOffF = kTcOffG + kTcGroups * kGrpTiles;   // floats: bias [3][128], w4 [128]
+constexpr uint32_t kTcOffGF = kTcOffF + 4 * 128 * 4;            // per group: unit data
+constexpr uint32_t kGrpFloats = 32 * 2 + 32 * 8 + 128 * 2;
+constexpr uint32_t kTcOffBar = kTcOffGF + kTcGroups * kGrpFloats * 4;   // mbarriers, TMEM, abort
 constexpr size_t kTcSmem = kTcOffBar + 64 + 1024;          // + room to align the base to 1 KB
 static_assert(kTcOffW2 % 1024 == 0 && kTcOffW3 % 1024 == 0 && kTcOffG % 1024 == 0 &&
                   kGrpTiles % 1024 == 0, "swizzle atoms need 1 KB alignment");
@@ -604,7 +606,7 @@ struct TcShared {
     unsigned char* base;   // 1 KB aligned
     uint32_t sbase;        // its shared-window address
     uint32_t* tmem_slot;
-    int* abort;            // [2]: set by a group's issuing thread when its MMA wait ran out
+    int* abort;            // [4]: set by a group's issuing thread when its MMA wait ran out
 };
 
 __device__ __forceinline__ TcShared tc_shared(unsigned char* raw) {
@@ -613,28 +615,26 @@ __device__ __forceinline__ TcShared tc_shared(unsigned char* raw) {
     const uint32_t pad = ((a + 1023u) & ~1023u) - a;
     t.base = raw + pad;
     t.sbase = a + pad;
-    t.tmem_slot = reinterpret_cast<uint32_t*>(t.base + kTcOffBar + 16);
-    t.abort = reinterpret_cast<int*>(t.base + kTcOffBar + 24);
+    t.tmem_slot = reinterpret_cast<uint32_t*>(t.base + kTcOffBar + 32);
+    t.abort = reinterpret_cast<int*>(t.base + kTcOffBar + 40);
     return t;
 }
 
-// One of the two thread groups of the CTA and its private resources.
+// One of the four thread groups of the CTA and its private resources.
 struct TcGroup {
-    int g;          // 0 or 1
-    int gt;         // thread index in the group, 0..255
-    uint32_t x;     // byte offsets of the group's X and H tiles
-    uint32_t h;
-    float* f;       // the group's floats: red [2][128], St [128][33], unit data
+    int g;          // 0..3
+    int gt;         // thread index in the group, 0..127 (= the sample row it owns)
+    uint32_t h;     // byte offset of the group's hidden tile; X is its first K block
+    float* f;       // the group's unit data
     uint32_t tmem;  // its 128 accumulator columns
     uint32_t bar;   // its mbarrier
 };
 
 __device__ __forceinline__ TcGroup tc_group(const TcShared& S, uint32_t tmem_base) {
     TcGroup G;
-    G.g = threadIdx.x >> 8;
-    G.gt = threadIdx.x & 255;
-    G.x = kTcOffG + (uint32_t)G.g * kGrpTiles;
-    G.h = G.x + kAtomBlock;
+    G.g = threadIdx.x >> 7;
+    G.gt = threadIdx.x & 127;
+    G.h = kTcOffG + (uint32_t)G.g * kGrpTiles;
     G.f = reinterpret_cast<float*>(S.base + kTcOffGF) + G.g * kGrpFloats;
     G.tmem = tmem_base + (uint32_t)G.g * 128u;
     G.bar = S.sbase + kTcOffBar + 8u * (uint32_t)G.g;
@@ -642,12 +642,11 @@ __device__ __forceinline__ TcGroup tc_group(const TcShared& S, uint32_t tmem_bas
 }
 
 __device__ __forceinline__ void group_sync(int g) {
-    asm volatile("bar.sync %0, 256;" ::"r"(g + 1) : "memory");
+    asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory");
 }
 
-// Weights into their swizzled tiles, the padding half of both X tiles zeroed,
-// the mbarriers initialised, TMEM allocated (warp 0).  Ends with a CTA
-// barrier; returns the TMEM base address.
+// Weights into their swizzled tiles, the mbarriers initialised, TMEM
+// allocated (warp 0).  Ends with a CTA barrier; returns the TMEM base address.
 __device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
     const int tid = threadIdx.x;
     // W1 with b1 in input columns 32 (BF16 high part) and 33 (the remainder), so
@@ -681,14 +680,6 @@ __device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
         *reinterpret_cast<uint4*>(S.base + kTcOffW2 + sw_chunk(n, c >> 3, c & 7)) = a;
         *reinterpret_cast<uint4*>(S.base + kTcOffW3 + sw_chunk(n, c >> 3, c & 7)) = b;
     }
-    // input columns 32, 33 = 1 (the first layer's bias), 34..63 = 0
-    const __nv_bfloat162 one2 = __float2bfloat162_rn(1.f);
-    for (int i = tid; i < 2 * 128 * 4; i += kTcThreads) {
-        const int g = i >> 9, r = (i >> 2) & 127, j = 4 + (i & 3);
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (j == 4) v.x = *reinterpret_cast<const uint32_t*>(&one2);
-        *reinterpret_cast<uint4*>(S.base + kTcOffG + g * kGrpTiles + sw_chunk(r, 0, j)) = v;
-    }
     float* F = reinterpret_cast<float*>(S.base + kTcOffF);
     for (int i = tid; i < 3 * kHid; i += kTcThreads) {
         const int l = i / kHid;
@@ -696,12 +687,13 @@ __device__ uint32_t tc_setup(const TcShared& S, const Weights& w) {
     }
     for (int i = tid; i < kHid; i += kTcThreads) F[3 * kHid + i] = 0.5f * w.p[kOffW4 + i];
     if (tid == 0) {
-        mbar_init(S.sbase + kTcOffBar, 1);
-        mbar_init(S.sbase + kTcOffBar + 8, 1);
+        for (int g = 0; g < kTcGroups; ++g) {
+            mbar_init(S.sbase + kTcOffBar + 8 * g, 1);
+            S.abort[g] = 0;
+        }
         mbar_fence_init();
-        S.abort[0] = S.abort[1] = 0;
     }
-    if (tid < 32) tc_alloc(S.sbase + kTcOffBar + 16, kTcCols);
+    if (tid < 32) tc_alloc(S.sbase + kTcOffBar + 32, kTcCols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -721,21 +713,33 @@ __device__ void tc_teardown(const TcShared& S, const TcGroup& G, uint32_t tmem_b
     if (threadIdx.x < 32) tc_dealloc(tmem_base, kTcCols);
 }
 
-// The network on the group's 128 samples whose inputs sit in its X tile
-// (written, fenced and followed by a group barrier).  Returns, in the group's
-// threads 0..127, the output of sample (group thread index); false if an MMA
-// wait ran out (the status word is set and the caller stops).
+// Input chunks 4..7 of every row of the group's X: columns 32, 33 carry 1
+// (the first layer's bias), 34..63 zero.  Written with the inputs each pass,
+// since the hidden layers overwrite X.
+__device__ __forceinline__ void tc_input_constants(const TcShared& S, const TcGroup& G) {
+    const __nv_bfloat162 one2 = __float2bfloat162_rn(1.f);
+    for (int k = G.gt; k < 128 * 4; k += kGrpThreads) {
+        const int r = k & 127, j = 4 + (k >> 7);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (j == 4) v.x = *reinterpret_cast<const uint32_t*>(&one2);
+        *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(r, 0, j)) = v;
+    }
+}
+
+// The network on the group's 128 samples whose inputs sit in X (written,
+// fenced and followed by a group barrier).  Returns in every thread the output
+// of sample (group thread index); false if an MMA wait ran out (the status
+// word is set and the caller stops).
 __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase, float b4,
                            float* out_row, int* status) {
-    const int wg = G.gt >> 5, lane = G.gt & 31;
-    const int lq = wg & 3, ch = wg >> 2;
-    const int row = lq * 32 + lane;
+    const int lq = G.gt >> 5;
+    const int row = G.gt;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
-    float* red = G.f + kGrpRed;
+    float sacc = 0.f;
     for (int layer = 0; layer < 3; ++layer) {
         if (G.gt == 0) {
             tc_fence_after();
-            const uint32_t a0 = S.sbase + (layer == 0 ? G.x : G.h);
+            const uint32_t a0 = S.sbase + G.h;
             const uint32_t b0 = S.sbase + (layer == 0 ? kTcOffW1 : layer == 1 ? kTcOffW2 : kTcOffW3);
             const int ksteps = layer == 0 ? 4 : 8;
             for (int ks = 0; ks < ksteps; ++ks) {
@@ -752,10 +756,9 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
         group_sync(G.g);
         if (S.abort[G.g]) return false;
         tc_fence_after();
-        float sacc = 0.f;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int cb = ch * 64 + half * 32;   // columns cb .. cb + 31
+#pragma unroll 1
+        for (int cc = 0; cc < 4; ++cc) {
+            const int cb = cc * 32;   // columns cb .. cb + 31
             float v[32];
             tc_ld32(G.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb, v);
             const float4* bias4 = reinterpret_cast<const float4*>(F + layer * kHid + cb);
@@ -779,7 +782,7 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, ch, half * 4 + c)) =
+                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, cc >> 1, (cc & 1) * 4 + c)) =
                         make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
             } else {
                 const float4* w44 = reinterpret_cast<const float4*>(F + 3 * kHid + cb);
@@ -797,11 +800,10 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
             }
         }
         if (layer < 2) fence_async_smem();
-        else red[ch * 128 + row] = sacc;
         tc_fence_before();
         group_sync(G.g);
     }
-    if (ch == 0) *out_row = (red[row] + red[128 + row]) + b4;
+    *out_row = sacc + b4;
     return true;
 }
 
@@ -815,19 +817,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const b
     const float b4 = w.p[kOffB4];
     uint32_t phase = 0;
     const int64_t n_tiles = (n + 127) / 128;
-    for (int64_t t = (int64_t)blockIdx.x * 2 + G.g; t < n_tiles; t += (int64_t)gridDim.x * 2) {
+    for (int64_t t = (int64_t)blockIdx.x * kTcGroups + G.g; t < n_tiles;
+         t += (int64_t)gridDim.x * kTcGroups) {
         const int64_t base = t * 128;
         for (int k = G.gt; k < 128 * 4; k += kGrpThreads) {   // 128 rows x 4 chunks of 8 inputs
             const int r = k & 127, j = k >> 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (base + r < n) v = *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + j * 8);
-            *reinterpret_cast<uint4*>(S.base + G.x + sw_chunk(r, 0, j)) = v;
+            *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(r, 0, j)) = v;
         }
+        tc_input_constants(S, G);
         fence_async_smem();
         group_sync(G.g);
         float o = 0.f;
         if (!tc_network(S, G, phase, b4, &o, status)) break;
-        if (G.gt < 128 && base + G.gt < n) out[base + G.gt] = o;
+        if (base + G.gt < n) out[base + G.gt] = o;
     }
     tc_teardown(S, G, tmem_base, phase);
 }
@@ -857,17 +861,17 @@ struct SurrogateRowParams {
 
 // The surrogate inside the row pipeline: after k_row wrote the unscattered
 // part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
-// adds sum_w max(exp(net(x_w)) - eps, 0) for every (event, voxel) and writes
-// the unit's partial forward sums.  Each thread group takes every other unit;
-// passes of 128 samples: 4 events x 32 voxels, one line.
+// adds sum_w max(exp(net(x_w)) - eps, 0) to every (event, voxel) and writes
+// the unit's partial forward sums.  Each thread group takes every fourth
+// unit; passes of 128 samples: 4 events x 32 voxels, one line; the thread
+// that owns a sample adds its scatter part to the row in global memory.
 __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
     extern __shared__ unsigned char smem_raw[];
     const TcShared S = tc_shared(smem_raw);
     const uint32_t tmem_base = tc_setup(S, P.w);
     const TcGroup G = tc_group(S, tmem_base);
     const float b4 = P.w.p[kOffB4];
-    float* St = G.f + kGrpSt;             // [128 events][33]
-    float* Vxy = G.f + kGrpV;             // [32] voxel centre (x, y), cm
+    float* Vxy = G.f;                     // [32] voxel centre (x, y), cm
     float* Vg8 = Vxy + 32 * 2;            // [32][8] rho line integrals
     float* Eeu = Vg8 + 32 * 8;            // [128] (recorded energy, bin centre)
     const int gt = G.gt;
@@ -876,24 +880,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
     const int n_units = n_tiles * P.nqt;
     const float half_det = 0.5f * P.B * P.bin_w;
     bool ok = true;
-    for (int unit = blockIdx.x * 2 + G.g; unit < n_units && ok; unit += gridDim.x * 2) {
+    for (int unit = blockIdx.x * kTcGroups + G.g; unit < n_units && ok;
+         unit += gridDim.x * kTcGroups) {
         const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
         const int qt = unit % P.nqt;
         const int nq_here = min(32, P.nq - qt * 32);
-        group_sync(G.g);   // the group's previous unit is done with St and the unit data
-        for (int i = gt; i < kET * 32; i += kGrpThreads) {
-            const int e = i >> 5, ql = i & 31;
-            St[e * 33 + ql] = (e < T.count && ql < nq_here)
-                                  ? P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql]
-                                  : 0.f;
-        }
+        group_sync(G.g);   // the group's previous unit is done with the unit data
         if (gt < 32 && gt < nq_here) {
             const int pix = P.q_pix[qt * 32 + gt];
             Vxy[2 * gt] = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
             Vxy[2 * gt + 1] = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
         }
-        if ((gt >> 3) < nq_here)
-            Vg8[gt] = P.g8[((size_t)T.a * P.nq + qt * 32 + (gt >> 3)) * 8 + (gt & 7)];
+        for (int i = gt; i < 32 * 8; i += kGrpThreads)
+            if ((i >> 3) < nq_here)
+                Vg8[i] = P.g8[((size_t)T.a * P.nq + qt * 32 + (i >> 3)) * 8 + (i & 7)];
         if (gt < T.count) {
             Eeu[2 * gt] = P.ev_e[T.begin + gt];
             Eeu[2 * gt + 1] = -half_det + (P.ev_bin[T.begin + gt] + 0.5f) * P.bin_w;
@@ -903,6 +903,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
         float ca, sa;
         sincosf(th, &sa, &ca);
         for (int c = 0; c < (T.count + 3) / 4 && ok; ++c) {
+            float scat = 0.f;   // scatter part of this thread's sample, summed over the lines
             for (int wl = 0; wl < P.W && ok; ++wl) {
                 // inputs 8 j .. 8 j + 7 of sample smp (event 4c + smp / 32, voxel
                 // smp mod 32) into chunk j of row smp of X
@@ -924,33 +925,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
                         const __nv_bfloat162 t = __floats2bfloat162_rn(f8[2 * i], f8[2 * i + 1]);
                         u[i] = *reinterpret_cast<const uint32_t*>(&t);
                     }
-                    *reinterpret_cast<uint4*>(S.base + G.x + sw_chunk(smp, 0, j)) =
+                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(smp, 0, j)) =
                         make_uint4(u[0], u[1], u[2], u[3]);
                 }
+                tc_input_constants(S, G);
                 fence_async_smem();
                 group_sync(G.g);
                 float o = 0.f;
                 ok = tc_network(S, G, phase, b4, &o, P.status);
-                if (ok && gt < 128) {
-                    const int e = c * 4 + (gt >> 5), ql = gt & 31;
-                    if (e < T.count && ql < nq_here) {
-                        const float v = __expf(o) - kSurrogateEps;
-                        St[e * 33 + ql] += v > 0.f ? v : 0.f;
-                    }
-                }
+                const float v = __expf(o) - kSurrogateEps;
+                scat += v > 0.f ? v : 0.f;
             }
+            const int e = c * 4 + (gt >> 5), ql = gt & 31;
+            if (ok && e < T.count && ql < nq_here)
+                P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] += scat;
         }
         if (!ok) break;
-        group_sync(G.g);
-        for (int i = gt; i < kET * 32; i += kGrpThreads) {
-            const int e = i >> 5, ql = i & 31;
-            if (e < T.count && ql < nq_here)
-                P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] = St[e * 33 + ql];
-        }
+        group_sync(G.g);   // the group's row updates are visible to the whole group
         if (P.lam && gt < T.count) {
             const float* lam = P.lam + (size_t)T.r * P.lam_stride;
+            const float* row = P.rows + (size_t)(T.begin + gt - P.row_base) * P.row_stride + qt * 32;
             float s = 0.f;
-            for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], St[gt * 33 + ql], s);
+            for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], row[ql], s);
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + gt - P.row_base)] = s;
         }
     }
@@ -1049,7 +1045,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
         P.e_line[w] = (float)h->mc.line_e[w];
     }
     P.rho = h->d_rho;
-    const int grid = std::min((n_units + 1) / 2, h->sm_count);
+    const int grid = std::min((n_units + mlp::kTcGroups - 1) / mlp::kTcGroups, h->sm_count);
     mlp::k_surrogate_rows<<<grid, mlp::kTcThreads, mlp::kTcSmem, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
@@ -1267,7 +1263,7 @@ int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out,
     if (rc != LMMEW_OK) return rc;
     M::Weights w{s->W1, s->W2, s->W3, s->p};
     const int64_t tiles = (n + 127) / 128;
-    const unsigned grid = (unsigned)std::min<int64_t>((tiles + 1) / 2, sm_count());
+    const unsigned grid = (unsigned)std::min<int64_t>((tiles + M::kTcGroups - 1) / M::kTcGroups, sm_count());
     M::k_tc_forward<<<grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status);
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -47,8 +47,8 @@ def parse_args():
                     help="override the workload's event count (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the forms section (precision, batching, comparison, surrogate)")
-    ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
+                    help="skip the forms section (precision, batching, comparison, surrogate, combined)")
+    ap.add_argument("--forms", default="precision,batching,comparison,surrogate,combined",
                     help="comma-separated forms to measure")
     ap.add_argument("--case", default=None, choices=["surrogate_rows"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
@@ -344,29 +344,17 @@ def _object_events(args):
     return simulate(sc, n_events=n_events, seed=seed * 1000 + k, workers=1)
 
 
-def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_000,
-                       object_events=20_000, iters=2, seed=5):
-    """The learned single-scatter surrogate against the exact FP32 path on the
-    same GPU, on the 128 x 128, 2 M-event workload.  The network is trained
-    on 10^7 exact single-scatter sums drawn (lm_surrogate_sample) from eight
-    random water/bone objects on the same grid -- never from the workload's
-    own object -- with the loss weighted by the square root of the scatter
-    mass.  Reported: sampling and training time, the mass-weighted error of
-    the scatter sum on samples of the workload's object, seconds per OSEM
-    iteration and network throughput, and the deviation of forward
-    projections, images and lesion activities from the exact path -- next to
-    the same deviations of the model without scatter, which is what the
-    surrogate has to beat."""
+def train_surrogate_on_random_objects(sc, n_objects, n_samples, object_events, seed):
+    """A surrogate trained on n_samples exact single-scatter sums drawn from
+    n_objects random water/bone objects on the workload's grid (never the
+    workload's own object).  Returns (surrogate, sampling s, training s,
+    schedule, batch)."""
     import multiprocessing as mp
 
-    import numpy as np
     import torch
 
     import paper_2305_17111_gb300 as lm
-    from synthetic import preset, random_water_bone_object, simulate_cached
-    sc = preset(workload)
-    ph = sc.make_phantom()
-    ev = simulate_cached(sc)
+    from synthetic import random_water_bone_object
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -380,7 +368,7 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
 
     with mp.get_context("spawn").Pool(min(n_objects, os.cpu_count() or 1)) as pool:
         obj_events = pool.map(_object_events,
-                              [(k, seed, workload, object_events) for k in range(n_objects)])
+                              [(k, seed, sc.name, object_events) for k in range(n_objects)])
     xs, ts, t_sample = [], [], 0.0
     for k in range(n_objects):
         sck = sc.with_(phantom=random_water_bone_object(seed, k))
@@ -404,7 +392,43 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
             sur.train(x, t, steps=steps, batch=batch, lr=lr, seed=seed * 10 + steps,
                       weight_power=0.5, record_loss=False)
     _, t_train = timed(train)
-    del x, t
+    return sur, t_sample, t_train, schedule, batch
+
+
+def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_000,
+                       object_events=20_000, iters=2, seed=5):
+    """The learned single-scatter surrogate against the exact FP32 path on the
+    same GPU, on the 128 x 128, 2 M-event workload.  The network is trained
+    on 10^7 exact single-scatter sums drawn (lm_surrogate_sample) from eight
+    random water/bone objects on the same grid -- never from the workload's
+    own object -- with the loss weighted by the square root of the scatter
+    mass.  Reported: sampling and training time, the mass-weighted error of
+    the scatter sum on samples of the workload's object, seconds per OSEM
+    iteration and network throughput, and the deviation of forward
+    projections, images and lesion activities from the exact path -- next to
+    the same deviations of the model without scatter, which is what the
+    surrogate has to beat."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    ev = simulate_cached(sc)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    sur, t_sample, t_train, schedule, batch = train_surrogate_on_random_objects(
+        sc, n_objects, n_samples, object_events, seed)
 
     model = lm.Model.from_scenario(sc, ph.rho)
     dev = lm.DeviceEvents.from_list(ev)
@@ -457,6 +481,77 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     sur.close()
     model.close()
     return out
+
+
+def run_combined_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, iters=2,
+                      n_objects=8, n_samples=4_000_000, seed=6):
+    """The forms together: many noise realisations of uneven size in one
+    batched call (persistent row launch per sub-iteration, one CUDA graph,
+    autotuned launch shape) with the scatter part from the BF16 tensor-core
+    surrogate (trained on random objects of the workload's grid, not its own
+    object), against the plain FP32 exact path one realisation at a time on
+    the same GPU.  Reported: the speed-up and every realisation's
+    lesion-activity deviation from its exact reconstruction."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    pool = simulate_cached(sc)
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(lo, hi + 1, size=n_real)
+    evs = [pool.subset(rng.integers(0, len(pool), size=int(k))) for k in sizes]
+    devs = [lm.DeviceEvents.from_list(e) for e in evs]
+    sur, t_sample, t_train, _, _ = train_surrogate_on_random_objects(
+        sc, n_objects, n_samples, 20_000, seed)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    # plain FP32 exact path, one realisation at a time (after a warm-up call)
+    model.osem(devs[0], lam0.clone(), sc.n_subsets, 1)
+    exact_imgs, t_exact = [], 0.0
+    for d in devs:
+        img = lam0.clone()
+        t_exact += timed(lambda: model.osem(d, img, sc.n_subsets, iters))
+        exact_imgs.append(img.cpu().numpy().astype(np.float64))
+    # the combined form (the first batched call tunes the launch shape)
+    model.set_scatter_model("surrogate", sur)
+    imgs = lam0.repeat(n_real, 1).contiguous()
+    model.osem_batch(devs, imgs, sc.n_subsets, iters)
+    imgs = lam0.repeat(n_real, 1).contiguous()
+    t_comb = timed(lambda: model.osem_batch(devs, imgs, sc.n_subsets, iters))
+    model.set_scatter_model("exact")
+    comb = imgs.cpu().numpy().astype(np.float64)
+    dev_roi = []
+    for r in range(n_real):
+        ref = roi_sums(exact_imgs[r], ph.lesion_masks)
+        got = roi_sums(comb[r], ph.lesion_masks)
+        dev_roi.append([abs(a - b) / b for a, b in zip(got, ref)])
+    dev_roi = np.asarray(dev_roi)
+    sur.close()
+    model.close()
+    return {"workload": f"{n_real} realisations of {sc.name} with U[{lo}, {hi}] events "
+                        f"({int(sizes.sum())} events, resampled from one MC pool), "
+                        f"{sc.n_subsets} subsets x {iters} iterations each",
+            "surrogate_training": {"objects": n_objects, "samples": n_samples,
+                                   "sample_s": t_sample, "train_s": t_train},
+            "exact_fp32_one_at_a_time_s": t_exact,
+            "surrogate_bf16_batched_s": t_comb,
+            "speedup_vs_exact_fp32": t_exact / t_comb,
+            "roi_rel_dev_vs_exact": {"mean": float(dev_roi.mean()), "max": float(dev_roi.max()),
+                                     "per_lesion_mean": dev_roi.mean(axis=0).tolist()}}
 
 
 def run_batch_form(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, iters=1, repeats=2,
@@ -627,6 +722,7 @@ def run_gpu(args, rank, local_rank, world):
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak = ex2_peak(sm_count, sm_max)
     achieved = prof["terms"] / (prof["ms"] / 1e3) if prof["ms"] > 0 else 0.0
+    probe = lm.probe_ex2_rate()          # measured exponential rate of this GPU
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -651,12 +747,15 @@ def run_gpu(args, rank, local_rank, world):
                                  if not args.events else None),
                      "peak_basis": f"{sm_count} SMs x {EX2_PER_SM_PER_CLK} ex2/clk x "
                                    f"{sm_max:.0f} MHz",
+                     "peak_probe": probe["f32"] * sm_count * probe["sm_mhz"] * 1e6 / 1e12,
+                     "probe_ex2_per_clk_per_sm": {k: probe[k] for k in ("f32", "f16x2", "bf16x2")},
                      "row_kernel_share": prof["ms"] / ms if ms > 0 else None},
     }
     if world == 1 and not args.no_forms and not args.events:
         model.close()
         runners = {"precision": run_precision_form, "batching": run_batch_form,
-                   "comparison": run_comparison_form, "surrogate": run_surrogate_form}
+                   "comparison": run_comparison_form, "surrogate": run_surrogate_form,
+                   "combined": run_combined_form}
         line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)

@@ -344,6 +344,15 @@ int lm_profile_read(lm_handle* h, double* out5);
  * out8[6] = bytes of device tables, out8[7] = set-up time in microseconds. */
 int lm_model_info(const lm_handle* h, int64_t* out8);
 
+/* Exponential throughput of the current GPU (an instrument of this library,
+ * not part of the paper's method): times kernels of independent dependent
+ * chains of ex2.approx.ftz.f32, ex2.approx.f16x2 and ex2.approx.ftz.bf16x2
+ * on every SM and writes out4[0..2] = exponential results per clock per SM
+ * for each (two results per packed instruction), out4[3] = the SM clock in
+ * MHz the rates refer to (the device's maximum).  Synchronises the stream;
+ * allocates and frees 1 MiB of device memory.  Errors: INVALID_ARG, CUDA. */
+int lm_probe_ex2_rate(lm_stream stream, double* out4);
+
 #ifdef __cplusplus
 }
 #endif

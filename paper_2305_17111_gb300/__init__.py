@@ -14,11 +14,19 @@ import numpy as np
 from . import _native
 from ._native import LmmewError
 
-__all__ = ["Model", "DeviceEvents", "Surrogate", "LmmewError", "library_path"]
+__all__ = ["Model", "DeviceEvents", "Surrogate", "LmmewError", "library_path", "probe_ex2_rate"]
 
 
 def library_path() -> str:
     return _native.LIB_PATH
+
+
+def probe_ex2_rate(stream=None) -> dict:
+    """Exponential results per clock per SM of the current GPU (FP32 ex2 and
+    the packed f16x2 / bf16x2 forms) and the SM clock (MHz) they refer to."""
+    out = (ctypes.c_double * 4)()
+    _native.check(_native.load().lm_probe_ex2_rate(_stream(stream), out))
+    return {"f32": out[0], "f16x2": out[1], "bf16x2": out[2], "sm_mhz": out[3]}
 
 
 def _torch():

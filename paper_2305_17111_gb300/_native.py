@@ -104,6 +104,7 @@ SYMBOLS = {
                                            ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "lm_set_scatter_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "lm_probe_ex2_rate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
 
 SCATTER_EXACT, SCATTER_SURROGATE, SCATTER_NONE = 0, 1, 2

@@ -353,6 +353,16 @@ int lm_model_info(const lm_handle* h, int64_t* out8);
  * allocates and frees 1 MiB of device memory.  Errors: INVALID_ARG, CUDA. */
 int lm_probe_ex2_rate(lm_stream stream, double* out4);
 
+/* Self-test of the bounded waits of the pipelined kernels (an instrument of
+ * this library): launches one warp that waits, through the same bounded wait
+ * the row and tensor-core kernels use, on an mbarrier nothing arrives on.
+ * The wait gives up after its limit (2 s), the kernel sets the timeout status
+ * and returns; nothing stays in flight and the context remains usable.
+ * Writes the time waited (ms) to *waited_ms and returns LMMEW_ERR_TIMEOUT (the
+ * expected outcome); any other code means the wait did not behave.
+ * Synchronises the device. */
+int lm_selftest_wait_timeout(double* waited_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,7 @@ SYMBOLS = {
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "lm_set_scatter_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "lm_probe_ex2_rate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "lm_selftest_wait_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
 }
 
 SCATTER_EXACT, SCATTER_SURROGATE, SCATTER_NONE = 0, 1, 2

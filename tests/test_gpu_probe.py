@@ -24,3 +24,25 @@ def test_ex2_rate_per_sm():
     # packed halves: no more exponential results per clock than FP32
     assert r["f16x2"] < 1.15 * r["f32"] and r["bf16x2"] < 1.15 * r["f32"], r
     assert r["sm_mhz"] > 1000.0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A wait on an mbarrier that nothing arrives on runs out after its limit
+    and is reported as a timeout; the GPU then runs a normal projection."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_2305_17111_gb300 import _native
+    from synthetic import preset, simulate
+    waited = ctypes.c_double()
+    rc = _native.load().lm_selftest_wait_timeout(ctypes.byref(waited))
+    assert rc == -5, _native.load().lm_last_error()          # LMMEW_ERR_TIMEOUT
+    assert 1500.0 < waited.value < 10000.0, waited.value     # the 2 s limit
+    sc = preset("tiny_8")
+    ph = sc.make_phantom()
+    model = lm.Model.from_scenario(sc, ph.rho)
+    ev = simulate(sc)
+    y = model.forward(lm.DeviceEvents.from_list(ev),
+                      torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda())
+    assert bool(torch.all(torch.isfinite(y))) and bool(torch.all(y > 0))

@@ -158,7 +158,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
     constexpr int kTabBytes = 3 * W * kQT * kPC * 4;
     const float* tb = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
     const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
-#pragma unroll 1
+#pragma unroll 4
     for (int pq = 0; pq < kPC / 4; ++pq) {
         f32x2 cA[kEPL], cB[kEPL];
 #pragma unroll

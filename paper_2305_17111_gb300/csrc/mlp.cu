@@ -2,10 +2,13 @@
 //   x (32, BF16) -> 128 -> 128 -> 128 (GELU, tanh form) -> 1
 // predicting ln(S_w + eps) for one (event, voxel, line), where S_w is the
 // single-scatter part of the system-matrix element for line w (Eq. s_p with
-// n = 1 summed over the scatter points).  Forward, backward and Adam run in
-// kernels written here; the matrix products use the BF16 tensor cores
-// through mma.sync m16n8k16 fragments loaded with ldmatrix, FP32
-// accumulation.  A CTA owns 128 samples; each of its 8 warps owns 16 rows.
+// n = 1 summed over the scatter points).  Two families of kernels, all
+// written here, BF16 operands with FP32 accumulation:
+//  * training (forward with stored pre-activations, backward, Adam): the
+//    matrix products use mma.sync m16n8k16 fragments loaded with ldmatrix;
+//    a CTA owns 128 samples and each of its 8 warps 16 rows;
+//  * inference (k_tc_forward and the row kernel k_surrogate_rows): tcgen05
+//    MMAs from swizzled shared memory into tensor memory, described below.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

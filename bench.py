@@ -554,6 +554,18 @@ def run_combined_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, ite
                                      "per_lesion_mean": dev_roi.mean(axis=0).tolist()}}
 
 
+def run_batch_forms():
+    """The batching form on two workloads: the scope's 256 realisations of
+    U[50k, 500k] events at 64^2 (one iteration each), and 256 realisations of
+    the paper's own study (64^2 of 4.6 mm, 120 angles, three windows,
+    U[8k, 12k] events around its ~10^4 per realisation, 4 subsets x 16
+    iterations), where every single reconstruction is too small to fill the
+    GPU."""
+    return {"lmmew_64_256": run_batch_form(),
+            "paper_study_256": run_batch_form(workload="paper_study", lo=8_000, hi=12_000,
+                                              iters=None, repeats=2, seed=31)}
+
+
 def run_batch_form(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, iters=1, repeats=2,
                    seed=3):
     """Many noise realisations with uneven event counts in one batched call
@@ -570,7 +582,7 @@ def run_batch_form(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, iters
     from synthetic import preset, simulate_cached
     sc = preset(workload)
     ph = sc.make_phantom()
-    pool = simulate_cached(sc)
+    pool = simulate_cached(sc, n_events=max(sc.n_events, 100_000))
     rng = np.random.default_rng(seed)
     sizes = rng.integers(lo, hi + 1, size=n_real)
     # realisations drawn from one iid Monte-Carlo pool (with replacement)
@@ -753,7 +765,7 @@ def run_gpu(args, rank, local_rank, world):
     }
     if world == 1 and not args.no_forms and not args.events:
         model.close()
-        runners = {"precision": run_precision_form, "batching": run_batch_form,
+        runners = {"precision": run_precision_form, "batching": run_batch_forms,
                    "comparison": run_comparison_form, "surrogate": run_surrogate_form,
                    "combined": run_combined_form}
         line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}

@@ -480,9 +480,7 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
         return set_error(LMMEW_ERR_INVALID_ARG, "at most 2^31 - 1 events per batch");
     const int R = n_real;
     const int A_s = (m.A + n_subsets - 1) / n_subsets;
-    const int64_t V = (int64_t)n_subsets * R * A_s;
-    if ((uint64_t)V * (uint64_t)m.B >= (uint64_t(1) << 32))
-        return set_error(LMMEW_ERR_INVALID_ARG, "realisations x angles x bins too large for one batch");
+    const int64_t V = (int64_t)n_subsets * A_s;
     cudaStream_t st = (cudaStream_t)stream;
     if (h->graph_exec) {   // the previous batch's graph (its launch finished before this call's sync)
         LMMEW_CUDA(cudaStreamSynchronize(st));
@@ -500,59 +498,110 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     rc = sort_events_batch(h, events, R, n_subsets, &se, arena, st);
     if (rc != LMMEW_OK) return rc;
 
-    // plan: per subset, row blocks of whole realisations; 128-event chunks
+    // plan: per subset, row blocks of whole tiles (all realisations mixed)
     const int rs = row_stride_of(h);
     const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / rs));
-    struct RowChunk { int t0, t1; int64_t e0, e1; int c0, c1; };
-    std::vector<std::vector<RowChunk>> rchunks(n_subsets);
-    std::vector<BpChunk> bp;
-    std::vector<int> bp_off(n_subsets + 1, 0), part_start((size_t)n_subsets * (R + 1), 0);
-    int64_t biggest = 1;
-    int parts_max = 1;
+    struct RowBlock { int t0, t1; int64_t e0, e1; int c0, c1; };
+    std::vector<RowBlock> blocks;
+    std::vector<int> blk_off(n_subsets + 1, 0);
     for (int s = 0; s < n_subsets; ++s) {
-        bp_off[s] = (int)bp.size();
-        RowChunk cur{-1, -1, 0, 0, 0, 0};
-        for (int r = 0; r < R; ++r) {
-            const int64_t v0 = ((int64_t)s * R + r) * A_s, v1 = v0 + A_s;
-            const int64_t e0 = se.h_angle_start[v0], e1 = se.h_angle_start[v1];
-            const int t0 = se.h_tile_start[v0], t1 = se.h_tile_start[v1];
-            if (cur.t0 >= 0 && (e1 - cur.e0) > max_ev) {
-                rchunks[s].push_back(cur);
-                cur.t0 = -1;
+        blk_off[s] = (int)blocks.size();
+        RowBlock cur{-1, -1, 0, 0, 0, 0};
+        for (int64_t v = (int64_t)s * A_s; v < (int64_t)(s + 1) * A_s; ++v) {
+            int64_t e = se.h_angle_start[v];
+            const int64_t e_end = se.h_angle_start[v + 1];
+            int t = se.h_tile_start[v];
+            for (; e < e_end; ++t) {
+                const int64_t cnt = std::min<int64_t>(kET, e_end - e);
+                if (cur.t0 >= 0 && cur.e1 - cur.e0 + cnt > max_ev) {
+                    blocks.push_back(cur);
+                    cur.t0 = -1;
+                }
+                if (cur.t0 < 0) cur = RowBlock{t, t, e, e, 0, 0};
+                cur.t1 = t + 1;
+                cur.e1 = e + cnt;
+                e += cnt;
             }
-            if (cur.t0 < 0) cur = RowChunk{t0, t0, e0, e0, (int)bp.size() - bp_off[s], 0};
-            part_start[(size_t)s * (R + 1) + r] = (int)bp.size() - bp_off[s];
-            for (int64_t e = e0; e < e1; e += 128)
-                bp.push_back(BpChunk{e - cur.e0, (int)std::min<int64_t>(128, e1 - e), r});
-            cur.t1 = t1;
-            cur.e1 = e1;
-            cur.c1 = (int)bp.size() - bp_off[s];
         }
-        if (cur.t0 >= 0) rchunks[s].push_back(cur);
-        part_start[(size_t)s * (R + 1) + R] = (int)bp.size() - bp_off[s];
-        parts_max = std::max(parts_max, (int)bp.size() - bp_off[s]);
-        for (const RowChunk& c : rchunks[s]) biggest = std::max(biggest, c.e1 - c.e0);
+        if (cur.t0 >= 0) blocks.push_back(cur);
     }
-    bp_off[n_subsets] = (int)bp.size();
+    blk_off[n_subsets] = (int)blocks.size();
+    const int n_blk = (int)blocks.size();
+    const int64_t G = (int64_t)n_blk * R;
+    if (G >= (int64_t(1) << 31))
+        return set_error(LMMEW_ERR_INVALID_ARG, "realisations x row blocks too large for one batch");
+    int64_t biggest = 1;
+    for (const RowBlock& b : blocks) biggest = std::max(biggest, b.e1 - b.e0);
+    // back-projection chunks: up to 128 events of one realisation in one block;
+    // a subset's slots run realisation-major, so each realisation's partial
+    // sums are one contiguous run of slots.  Chunks of a subset: at most its
+    // events / 128 plus one per (block, realisation) run.
+    size_t max_chunks = 1, parts_max = 1;
+    for (int s = 0; s < n_subsets; ++s) {
+        const int64_t ev_s = se.h_angle_start[(size_t)(s + 1) * A_s] - se.h_angle_start[(size_t)s * A_s];
+        const size_t c = (size_t)(ev_s / kBpChunkEvents) + (size_t)(blk_off[s + 1] - blk_off[s]) * R;
+        max_chunks += c;
+        parts_max = std::max(parts_max, c);
+    }
     const size_t need = bump_bytes(sizeof(float) * (size_t)R * m.nq) +
                         bump_bytes(sizeof(float) * (size_t)rs * biggest) +
                         bump_bytes(sizeof(float) * (size_t)m.nqt * biggest) +
-                        bump_bytes(sizeof(float) * (size_t)parts_max * m.nq) +
-                        bump_bytes(sizeof(double) * (size_t)parts_max) +
+                        bump_bytes(sizeof(float) * parts_max * m.nq) +
+                        bump_bytes(sizeof(double) * parts_max) +
                         bump_bytes(sizeof(double) * (size_t)R * m.nq) +
-                        bump_bytes(sizeof(BpChunk) * std::max<size_t>(bp.size(), 1)) +
-                        bump_bytes(sizeof(int) * part_start.size());
+                        bump_bytes(sizeof(BpChunk) * max_chunks) +
+                        bump_bytes(sizeof(int) * (size_t)n_subsets * (R + 1)) +
+                        bump_bytes(sizeof(int64_t) * (size_t)(n_blk + 1)) +
+                        bump_bytes(sizeof(int) * (size_t)(G + 1));
     rc = ensure(h, h->scratch_work, need, st);
     if (rc != LMMEW_OK) return rc;
     char* w = (char*)h->scratch_work.ptr;
     float* lam_v = bump<float>(w, (size_t)R * m.nq);
     float* rows = bump<float>(w, (size_t)rs * biggest);
     float* ypart = bump<float>(w, (size_t)m.nqt * biggest);
-    float* bpart = bump<float>(w, (size_t)parts_max * m.nq);
+    float* bpart = bump<float>(w, parts_max * m.nq);
     double* llpart = bump<double>(w, parts_max);
     double* num = bump<double>(w, (size_t)R * m.nq);
-    BpChunk* d_bp = bump<BpChunk>(w, std::max<size_t>(bp.size(), 1));
-    int* d_part = bump<int>(w, part_start.size());
+    BpChunk* d_bp = bump<BpChunk>(w, max_chunks);
+    int* d_part = bump<int>(w, (size_t)n_subsets * (R + 1));
+    int64_t* d_blk_start = bump<int64_t>(w, (size_t)n_blk + 1);
+    int* d_grp_start = bump<int>(w, (size_t)G + 1);
+    std::vector<int64_t> blk_start(n_blk + 1, se.n_total);
+    for (int b = 0; b < n_blk; ++b) blk_start[b] = blocks[b].e0;
+    if (n_blk > 0)
+        LMMEW_CUDA(cudaMemcpyAsync(d_blk_start, blk_start.data(), 8 * (size_t)(n_blk + 1),
+                                   cudaMemcpyHostToDevice, st));
+    std::vector<int> grp;   // grp[b * R + r]: first entry of (block b, realisation r)
+    rc = bp_order_batch(h, &se, R, d_blk_start, n_blk, d_grp_start, grp, st);
+    if (rc != LMMEW_OK) return rc;
+    std::vector<BpChunk> bp;
+    std::vector<int> part_start((size_t)n_subsets * (R + 1), 0);
+    for (int s = 0; s < n_subsets; ++s) {
+        // slot of each (realisation, block) run, realisation-major
+        const int b0 = blk_off[s], b1 = blk_off[s + 1];
+        std::vector<int> slot0((size_t)(b1 - b0) * R);
+        int slot = 0;
+        for (int r = 0; r < R; ++r) {
+            part_start[(size_t)s * (R + 1) + r] = slot;
+            for (int b = b0; b < b1; ++b) {
+                const int64_t cnt = grp[(size_t)b * R + r + 1] - grp[(size_t)b * R + r];
+                slot0[(size_t)(b - b0) * R + r] = slot;
+                slot += (int)((cnt + kBpChunkEvents - 1) / kBpChunkEvents);
+            }
+        }
+        part_start[(size_t)s * (R + 1) + R] = slot;
+        // chunks in block order, each block's chunks one contiguous list
+        for (int b = b0; b < b1; ++b) {
+            blocks[b].c0 = (int)bp.size();
+            for (int r = 0; r < R; ++r) {
+                const int64_t g0 = grp[(size_t)b * R + r], g1 = grp[(size_t)b * R + r + 1];
+                int sl = slot0[(size_t)(b - b0) * R + r];
+                for (int64_t e = g0; e < g1; e += kBpChunkEvents, ++sl)
+                    bp.push_back(BpChunk{e, (int)std::min<int64_t>(kBpChunkEvents, g1 - e), sl});
+            }
+            blocks[b].c1 = (int)bp.size();
+        }
+    }
     if (!bp.empty())
         LMMEW_CUDA(cudaMemcpyAsync(d_bp, bp.data(), sizeof(BpChunk) * bp.size(),
                                    cudaMemcpyHostToDevice, st));
@@ -564,10 +613,11 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     // autotune the row kernel's launch shape on this batch's first row block
     const uint64_t key = ((uint64_t)n_total << 24) ^ ((uint64_t)R << 8) ^ (uint64_t)n_subsets ^
                          ((uint64_t)h->scatter_model << 60) ^ ((uint64_t)h->prec << 62);
-    if (h->tune_key != key && !rchunks[0].empty()) {
-        const RowChunk& c = rchunks[0][0];
+    if (h->tune_key != key && n_blk > 0) {
+        const RowBlock& c = blocks[0];
         RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
                     c.e1 - c.e0, c.e1 - c.e0, m.nq};
+        L.ev_real = se.real;
         cudaEvent_t ta, tb;
         LMMEW_CUDA(cudaEventCreate(&ta));
         LMMEW_CUDA(cudaEventCreate(&tb));
@@ -612,13 +662,15 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     LMMEW_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < n_iters && rc == LMMEW_OK; ++it) {
         for (int s = 0; s < n_subsets && rc == LMMEW_OK; ++s) {
-            for (const RowChunk& c : rchunks[s]) {
+            for (int b = blk_off[s]; b < blk_off[s + 1]; ++b) {
+                const RowBlock& c = blocks[b];
                 RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
                             c.e1 - c.e0, c.e1 - c.e0, m.nq};
+                L.ev_real = se.real;
                 rc = launch_row(h, L, cs);
                 if (rc != LMMEW_OK) break;
-                rc = launch_bp_batch(h, rows, rs, ypart, c.e1 - c.e0, d_bp + bp_off[s] + c.c0,
-                                     c.c1 - c.c0, bpart, c.c0, llpart, cs);
+                rc = launch_bp_batch(h, rows, rs, ypart, c.e1 - c.e0, se.bp_idx, c.e0, d_bp + c.c0,
+                                     c.c1 - c.c0, bpart, llpart, cs);
                 if (rc != LMMEW_OK) break;
             }
             if (rc != LMMEW_OK) break;

@@ -8,7 +8,7 @@
 namespace lmmew {
 namespace {
 
-constexpr int kBpEvents = 128;    // events per back-projection partial
+constexpr int kBpEvents = kBpChunkEvents;   // events per back-projection partial
 constexpr int kBpVoxels = 256;    // voxels per back-projection block
 
 __global__ void k_forward_out(const float* ypart, int64_t stride, int nqt, int64_t count,
@@ -196,22 +196,29 @@ int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
-// Batched realisations: the same steps with every event chunk tagged by its
-// realisation, voxel sums and updates per realisation.
+// Batched realisations: the same steps with every back-projection chunk
+// holding one realisation's events, voxel sums and updates per realisation.
 namespace {
 
+// One block per (chunk, 256 voxels).  A chunk is up to 128 events of one
+// realisation inside one row block, listed by the back-projection order
+// (sorted positions); the block owns its voxels' partial sums in the chunk's
+// slot.
 __global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
     const float* rows, int row_stride, const float* ypart, int64_t ypart_stride, int nqt,
-    const BpChunk* chunks, int nq, float* bpart, int64_t row0, double* llpart) {
+    const uint32_t* bp_idx, int64_t row_base, const BpChunk* chunks, int nq, float* bpart,
+    double* llpart) {
     __shared__ float r[kBpEvents];
+    __shared__ int64_t idx[kBpEvents];
     __shared__ double ll[kBpEvents];
     const int t = threadIdx.x;
     const BpChunk C = chunks[blockIdx.x];
     if (t < kBpEvents) {
         float rv = 0.f;
         double lv = 0.0;
+        int64_t j = 0;
         if (t < C.count) {
-            const int64_t j = C.begin + t;
+            j = (int64_t)bp_idx[C.begin + t] - row_base;
             float y = 0.f;
             for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
             if (y > 0.f) {
@@ -220,6 +227,7 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
             }
         }
         r[t] = rv;
+        idx[t] = j;
         ll[t] = lv;
     }
     __syncthreads();
@@ -228,14 +236,13 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
             if (t < off) ll[t] += ll[t + off];
             __syncthreads();
         }
-        if (t == 0) llpart[row0 + blockIdx.x] = ll[0];
+        if (t == 0) llpart[C.slot] = ll[0];
     }
     const int q = blockIdx.y * kBpVoxels + t;
     if (q >= nq) return;
-    const float* rp = rows + (size_t)C.begin * row_stride + q;
     float acc = 0.f;
-    for (int e = 0; e < C.count; ++e) acc = fmaf(r[e], rp[(size_t)e * row_stride], acc);
-    bpart[(size_t)(row0 + blockIdx.x) * nq + q] = acc;
+    for (int e = 0; e < C.count; ++e) acc = fmaf(r[e], rows[(size_t)idx[e] * row_stride + q], acc);
+    bpart[(size_t)C.slot * nq + q] = acc;
 }
 
 __global__ void k_voxel_reduce_batch(const float* bpart, const int* part_start, int nq,
@@ -289,12 +296,13 @@ __global__ void k_scatter_batch(const float* lam, const int* q_pix, int nq, floa
 }  // namespace
 
 int launch_bp_batch(lm_handle* h, const float* rows, int row_stride, const float* ypart,
-                    int64_t ypart_stride, const BpChunk* chunks, int n_chunks, float* bpart,
-                    int64_t row0, double* llpart, cudaStream_t st) {
+                    int64_t ypart_stride, const uint32_t* bp_idx, int64_t row_base,
+                    const BpChunk* chunks, int n_chunks, float* bpart, double* llpart,
+                    cudaStream_t st) {
     if (n_chunks <= 0) return LMMEW_OK;
     dim3 g(n_chunks, (h->mc.nq + kBpVoxels - 1) / kBpVoxels);
-    k_bp_batch<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt, chunks,
-                                        h->mc.nq, bpart, row0, llpart);
+    k_bp_batch<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt, bp_idx,
+                                        row_base, chunks, h->mc.nq, bpart, llpart);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -377,23 +377,22 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
 }
 
 // ---------------------------------------------------------------------------
-// Batched sort: R realisations' events concatenated, keyed by (subset,
-// realisation, angle within the subset, bin), so that for every subset the
-// events of all realisations are one contiguous run and every (realisation,
-// angle) run is cut into its own tiles.
+// Batched sort: R realisations' events concatenated and keyed by (subset,
+// angle within the subset, bin) alone.  The radix sort is stable, so within
+// one (angle, bin) the events keep realisation order and, inside a
+// realisation, their input order: each realisation's events appear in the
+// order lm_osem would sort them on their own.  An angle's run, and so every
+// tile, holds the events of all realisations together, each with its
+// realisation beside it: a sub-iteration's tiles are full whatever the
+// realisations' event counts, and their bin ranges narrow as the
+// realisations add up.
 namespace {
 __global__ void k_keys_batch(const uint16_t* angle, const uint16_t* bin, const float* energy,
-                             int64_t n, const int64_t* off, int R, int A, int B, int n_subsets,
-                             int A_s, int n_win, float4 win01, float4 win23, float4 win45,
-                             float4 win67, uint32_t* keys, uint32_t* vals, int* status) {
+                             int64_t n, int A, int B, int n_subsets, int A_s, int n_win,
+                             float4 win01, float4 win23, float4 win45, float4 win67,
+                             uint32_t* keys, uint32_t* vals, int* status) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    int lo = 0, hi = R;                       // realisation: off[r] <= j < off[r+1]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] <= j) lo = mid; else hi = mid;
-    }
-    const int r = lo;
     const int a = angle[j], b = bin[j];
     const float e = energy[j];
     const float wl[8] = {win01.x, win01.z, win23.x, win23.z, win45.x, win45.z, win67.x, win67.z};
@@ -401,11 +400,63 @@ __global__ void k_keys_batch(const uint16_t* angle, const uint16_t* bin, const f
     bool inwin = false;
     for (int k = 0; k < n_win; ++k) inwin |= (e >= wl[k] && e < wh[k]);
     const bool ok = a < A && b < B && isfinite(e) && inwin;
-    const uint32_t V = (uint32_t)n_subsets * R * A_s;
-    const uint32_t v = ((uint32_t)(a % n_subsets) * R + r) * A_s + a / n_subsets;
+    const uint32_t V = (uint32_t)n_subsets * A_s;
+    const uint32_t v = (uint32_t)(a % n_subsets) * A_s + a / n_subsets;
     keys[j] = ok ? v * (uint32_t)B + (uint32_t)b : V * (uint32_t)B;
     vals[j] = (uint32_t)j;
     if (!ok) atomicOr(status, kStatusOutOfRange);
+}
+
+// Realisation of every sorted event: off[r] <= perm[i] < off[r + 1].
+__global__ void k_real_of(const uint32_t* perm, int64_t n, const int64_t* off, int R,
+                          uint16_t* real) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = perm[i];
+    int lo = 0, hi = R;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+    }
+    real[i] = (uint16_t)lo;
+}
+
+// Back-projection key of sorted event i: (row block, realisation).
+__global__ void k_bp_keys(const uint16_t* real, int64_t n, const int64_t* blk_start, int n_blk,
+                          int R, uint32_t* keys, uint32_t* vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_blk;                   // block: blk_start[k] <= i < blk_start[k + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (blk_start[mid] <= i) lo = mid; else hi = mid;
+    }
+    keys[i] = (uint32_t)lo * (uint32_t)R + real[i];
+    vals[i] = (uint32_t)i;
+}
+
+int key_bits(uint64_t kmax) {
+    int bits = 1;
+    while (bits < 32 && (kmax >> bits) != 0) ++bits;
+    return bits;
+}
+
+// Stable LSD radix sort of (keys, vals) over the ping-pong buffers; the
+// sorted pair ends in (kin, vin).
+int radix_sort_pairs(lm_handle* h, int64_t n, int bits, uint32_t*& kin, uint32_t*& kout,
+                     uint32_t*& vin, uint32_t*& vout, uint32_t* hist, cudaStream_t st) {
+    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
+        k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+        k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk, kout,
+                                                          vout);
+        LMMEW_CUDA(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    h->launches += 3 * ((bits + 7) / 8);
+    return LMMEW_OK;
 }
 }  // namespace
 
@@ -413,11 +464,11 @@ size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R) {
     const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
     size_t b = 0;
     auto add = [&](size_t bytes) { b += bump_bytes(bytes); };
-    add(4 * n); add(4 * n); add(4 * n); add(4 * n);
+    add(4 * n); add(4 * n); add(4 * n); add(4 * n);    // keys/vals ping-pong (reused by bp_order)
     add(4 * 256 * (nblk > 0 ? nblk : 1));
-    add(4 * n); add(2 * n); add(4 * n);
+    add(4 * n); add(2 * n); add(4 * n); add(2 * n);     // perm, bins, energies, realisations
     add(2 * n); add(2 * n); add(4 * n);                 // concatenated events
-    add(4 * (V + 1)); add(4 * (V + 1)); add(4 * V); add(4 * V);
+    add(4 * (V + 1)); add(4 * (V + 1)); add(4 * V);
     add(8 * (R + 1));
     add(sizeof(Tile) * (size_t)(n / kET + V + 1));
     return b;
@@ -428,33 +479,32 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     const ModelConst& m = h->mc;
     const int A = m.A, B = m.B;
     const int A_s = (A + n_subsets - 1) / n_subsets;
-    const int64_t V = (int64_t)n_subsets * R * A_s;
+    const int64_t V = (int64_t)n_subsets * A_s;
     std::vector<int64_t> off(R + 1, 0);
     for (int r = 0; r < R; ++r) off[r + 1] = off[r] + evs[r].n;
     const int64_t n = off[R];
-    std::vector<int> angle_of_v(V), real_of_v(V);
+    std::vector<int> angle_of_v(V);
     for (int64_t v = 0; v < V; ++v) {
-        const int ai = (int)(v % A_s), r = (int)((v / A_s) % R), s = (int)(v / ((int64_t)A_s * R));
+        const int ai = (int)(v % A_s), s = (int)(v / A_s);
         const int a = ai * n_subsets + s;
         angle_of_v[v] = a < A ? a : 0;
-        real_of_v[v] = r;
     }
-    uint32_t* keys0 = bump<uint32_t>(arena, n);
-    uint32_t* keys1 = bump<uint32_t>(arena, n);
-    uint32_t* vals0 = bump<uint32_t>(arena, n);
-    uint32_t* vals1 = bump<uint32_t>(arena, n);
+    out->tmp_keys0 = bump<uint32_t>(arena, n);
+    out->tmp_keys1 = bump<uint32_t>(arena, n);
+    out->tmp_vals0 = bump<uint32_t>(arena, n);
+    out->tmp_vals1 = bump<uint32_t>(arena, n);
     const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
-    uint32_t* hist = bump<uint32_t>(arena, 256 * std::max<int64_t>(nblk, 1));
+    out->tmp_hist = bump<uint32_t>(arena, 256 * std::max<int64_t>(nblk, 1));
     out->perm = bump<uint32_t>(arena, n);
     out->bin = bump<uint16_t>(arena, n);
     out->energy = bump<float>(arena, n);
+    out->real = bump<uint16_t>(arena, n);
     uint16_t* c_angle = bump<uint16_t>(arena, n);
     uint16_t* c_bin = bump<uint16_t>(arena, n);
     float* c_energy = bump<float>(arena, n);
     out->angle_start = bump<int>(arena, V + 1);
     out->tile_start = bump<int>(arena, V + 1);
     int* d_angle_of_v = bump<int>(arena, V);
-    int* d_real_of_v = bump<int>(arena, V);
     int64_t* d_off = bump<int64_t>(arena, R + 1);
     out->tiles = bump<Tile>(arena, n / kET + V + 1);
 
@@ -469,41 +519,32 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     }
     LMMEW_CUDA(cudaMemcpyAsync(d_off, off.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
     LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_v, angle_of_v.data(), 4 * V, cudaMemcpyHostToDevice, st));
-    LMMEW_CUDA(cudaMemcpyAsync(d_real_of_v, real_of_v.data(), 4 * V, cudaMemcpyHostToDevice, st));
     if (n > 0) {
         float w[8][2] = {};
         for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
+        uint32_t *kin = out->tmp_keys0, *kout = out->tmp_keys1;
+        uint32_t *vin = out->tmp_vals0, *vout = out->tmp_vals1;
         k_keys_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            c_angle, c_bin, c_energy, n, d_off, R, A, B, n_subsets, A_s, m.n_win,
+            c_angle, c_bin, c_energy, n, A, B, n_subsets, A_s, m.n_win,
             make_float4(w[0][0], w[0][1], w[1][0], w[1][1]), make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
             make_float4(w[4][0], w[4][1], w[5][0], w[5][1]), make_float4(w[6][0], w[6][1], w[7][0], w[7][1]),
-            keys0, vals0, h->d_status);
+            kin, vin, h->d_status);
         LMMEW_CUDA(cudaGetLastError());
-        const uint64_t kmax = (uint64_t)V * (uint64_t)B;
-        int bits = 1;
-        while (bits < 32 && (kmax >> bits) != 0) ++bits;
-        uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
-        for (int shift = 0; shift < bits; shift += 8) {
-            k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
-            k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
-            k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk,
-                                                              kout, vout);
-            LMMEW_CUDA(cudaGetLastError());
-            std::swap(kin, kout);
-            std::swap(vin, vout);
-        }
+        int rc = radix_sort_pairs(h, n, key_bits((uint64_t)V * (uint64_t)B), kin, kout, vin, vout,
+                                  out->tmp_hist, st);
+        if (rc != LMMEW_OK) return rc;
         k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, c_energy, n, B, out->perm,
                                                              out->bin, out->energy);
+        k_real_of<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out->perm, n, d_off, R, out->real);
         k_bounds<<<(unsigned)((V + 1 + 127) / 128), 128, 0, st>>>(kin, n, (int)V, B, out->angle_start);
-        h->launches += 3 + 3 * ((bits + 7) / 8);
+        h->launches += 4;
         LMMEW_CUDA(cudaGetLastError());
     } else {
         LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (V + 1), st));
     }
     k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, (int)V, out->tile_start);
     k_tiles<<<(unsigned)((V + 127) / 128), 128, 0, st>>>(out->angle_start, out->tile_start,
-                                                         d_angle_of_v, (int)V, out->bin, out->tiles,
-                                                         d_real_of_v);
+                                                         d_angle_of_v, (int)V, out->bin, out->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     out->h_angle_start.resize(V + 1);
@@ -523,6 +564,39 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                          "an event has an angle or bin outside the model or an energy outside "
                          "every window");
     out->n_valid = out->h_angle_start[V];
+    out->n_total = n;
+    return LMMEW_OK;
+}
+
+// The back-projection order of a batch: sorted positions stably re-sorted by
+// (row block, realisation), so that every realisation's events inside a row
+// block form one run, in sorted order.  Reuses the batch sort's ping-pong
+// buffers; blk_start [n_blk + 1] and grp_start [n_blk * R + 1] are device
+// arrays the caller provides, grp_start also copied to the host.
+int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_start, int n_blk,
+                   int* grp_start, std::vector<int>& h_grp_start, cudaStream_t st) {
+    const int64_t n = se->n_total;
+    const int64_t G = (int64_t)n_blk * R;
+    h_grp_start.assign(G + 1, 0);
+    if (n == 0) {
+        se->bp_idx = se->tmp_vals0;
+        return LMMEW_OK;
+    }
+    uint32_t *kin = se->tmp_keys0, *kout = se->tmp_keys1;
+    uint32_t *vin = se->tmp_vals0, *vout = se->tmp_vals1;
+    k_bp_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(se->real, n, blk_start, n_blk, R, kin,
+                                                           vin);
+    LMMEW_CUDA(cudaGetLastError());
+    ++h->launches;
+    int rc = radix_sort_pairs(h, n, key_bits((uint64_t)G), kin, kout, vin, vout, se->tmp_hist, st);
+    if (rc != LMMEW_OK) return rc;
+    k_bounds<<<(unsigned)((G + 1 + 127) / 128), 128, 0, st>>>(kin, n, (int)G, 1, grp_start);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    se->bp_idx = vin;
+    LMMEW_CUDA(cudaMemcpyAsync(h_grp_start.data(), grp_start, 4 * (G + 1), cudaMemcpyDeviceToHost,
+                               st));
+    LMMEW_CUDA(cudaStreamSynchronize(st));
     return LMMEW_OK;
 }
 

@@ -151,6 +151,12 @@ struct SortedEvents {
     Tile* tiles = nullptr;       // [max_tiles]
     int* tile_start = nullptr;   // [A+1] first tile of each angle rank
     int64_t n_valid = 0;
+    // batched sort only
+    uint16_t* real = nullptr;    // [n] realisation of each sorted event
+    uint32_t* bp_idx = nullptr;  // [n] back-projection order (bp_order_batch)
+    uint32_t *tmp_keys0 = nullptr, *tmp_keys1 = nullptr, *tmp_vals0 = nullptr,
+             *tmp_vals1 = nullptr, *tmp_hist = nullptr;
+    int64_t n_total = 0;
     // host copies
     std::vector<int> h_angle_start;  // [A+1]
     std::vector<int> h_tile_start;   // [A+1]
@@ -173,6 +179,8 @@ size_t sort_fixed_bytes(int64_t n, int A);
 size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R);
 int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                       SortedEvents* out, char*& arena, cudaStream_t st);
+int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_start, int n_blk,
+                   int* grp_start, std::vector<int>& h_grp_start, cudaStream_t st);
 int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
                       cudaStream_t st);
 
@@ -190,6 +198,7 @@ struct RowLaunch {
     int64_t ypart_stride;
     int64_t n_events;       // events covered by the tile range (for accounting)
     int lam_stride = 0;     // batched: image of realisation r at lam_v + r * lam_stride
+    const uint16_t* ev_real = nullptr;   // batched: realisation of each sorted event
     int skip_scatter = 0;   // unscattered terms only (the surrogate adds the rest)
 };
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
@@ -212,14 +221,16 @@ int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, doubl
                         cudaStream_t st);
 int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
                   const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st);
+constexpr int kBpChunkEvents = 128;   // events per back-projection partial sum
 struct BpChunk {
-    int64_t begin;   // first event, relative to the row block's base
-    int count;       // 1..128
-    int r;           // realisation
+    int64_t begin;   // first entry of the back-projection order
+    int count;       // 1..128 events, all of one realisation
+    int slot;        // partial-sum slot of the sub-iteration
 };
 int launch_bp_batch(lm_handle* h, const float* rows, int row_stride, const float* ypart,
-                    int64_t ypart_stride, const BpChunk* chunks, int n_chunks, float* bpart,
-                    int64_t row0, double* llpart, cudaStream_t st);
+                    int64_t ypart_stride, const uint32_t* bp_idx, int64_t row_base,
+                    const BpChunk* chunks, int n_chunks, float* bpart, double* llpart,
+                    cudaStream_t st);
 int launch_reduce_update_batch(lm_handle* h, int R, const float* bpart, const int* part_start,
                                double* num, float* lam_v, const double* sens,
                                const double* llpart, double* loglik, int ll_stride,

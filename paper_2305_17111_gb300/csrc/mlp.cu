@@ -852,6 +852,7 @@ struct SurrogateRowParams {
     int row_stride;
     const float* lam;      // may be null
     int lam_stride;
+    const uint16_t* ev_real;   // realisation of each sorted event, or null (tile's own)
     float* ypart;
     int64_t ypart_stride;
     int* status;
@@ -946,7 +947,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
         if (!ok) break;
         group_sync(G.g);   // the group's row updates are visible to the whole group
         if (P.lam && gt < T.count) {
-            const float* lam = P.lam + (size_t)T.r * P.lam_stride;
+            const int rr = P.ev_real ? (int)P.ev_real[T.begin + gt] : T.r;
+            const float* lam = P.lam + (size_t)rr * P.lam_stride;
             const float* row = P.rows + (size_t)(T.begin + gt - P.row_base) * P.row_stride + qt * 32;
             float s = 0.f;
             for (int ql = 0; ql < nq_here; ++ql) s = fmaf(lam[qt * 32 + ql], row[ql], s);
@@ -1033,6 +1035,7 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     P.row_stride = L.row_stride;
     P.lam = L.lam_v;
     P.lam_stride = L.lam_stride;
+    P.ev_real = L.ev_real;
     P.ypart = L.ypart;
     P.ypart_stride = L.ypart_stride;
     P.n = h->mc.n;

@@ -59,6 +59,7 @@ struct RowParams {
     const float* ev_e;
     const float* lam;     // [nq] (per realisation, lam_stride apart) or null
     int lam_stride;
+    const uint16_t* ev_real;   // realisation of each sorted event, or null (tile's own)
     int unit_order;       // 0: tile-major, 1: voxel-tile-major work units
     int skip_scatter;     // 1: unscattered terms only
     float* rows;          // or null
@@ -405,9 +406,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         }
         if (lam && tid < T.count) {
             const int e = tid;
+            const float* le =
+                P.ev_real ? P.lam + (size_t)P.ev_real[T.begin + e] * P.lam_stride : lam;
             float s = 0.f;
             const int qmax = min(kQT, P.nq - qt * kQT);
-            for (int ql = 0; ql < qmax; ++ql) s = fmaf(lam[qt * kQT + ql], tt[e * 33 + ql], s);
+            for (int ql = 0; ql < qmax; ++ql) s = fmaf(le[qt * kQT + ql], tt[e * 33 + ql], s);
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
         }
         __syncthreads();
@@ -465,6 +468,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     P.ev_e = L.ev_e;
     P.lam = L.lam_v;
     P.lam_stride = L.lam_stride;
+    P.ev_real = L.ev_real;
     P.skip_scatter = L.skip_scatter;
     P.unit_order = h->unit_order;
     P.rows = L.rows;

@@ -138,7 +138,7 @@ def measured_peaks():
 # groups unrolled by 4) on this workload: the mean over the 8 launches of one
 # OSEM iteration in a one-pass ncu capture of the full workload.  Emptied
 # whenever k_row changes until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 500_660_288}
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.

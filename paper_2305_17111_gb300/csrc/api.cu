@@ -197,8 +197,9 @@ int lm_create(const lm_geometry* g, const lm_attenuation* at, const lm_lines* ln
     int rc = build_tables(h, at->rho, support);
     if (rc == LMMEW_OK &&
         (cudaMalloc(&h->d_term_counter, sizeof(unsigned long long)) != cudaSuccess ||
-         cudaMemset(h->d_term_counter, 0, sizeof(unsigned long long)) != cudaSuccess))
-        rc = set_error(LMMEW_ERR_OOM, "cannot allocate the term counter");
+         cudaMemset(h->d_term_counter, 0, sizeof(unsigned long long)) != cudaSuccess ||
+         cudaMalloc(&h->d_work, sizeof(int)) != cudaSuccess))
+        rc = set_error(LMMEW_ERR_OOM, "cannot allocate the term and work counters");
     if (rc == LMMEW_OK) rc = row_kernel_occupancy(h);
     if (rc != LMMEW_OK) {
         std::string keep = g_err;
@@ -244,6 +245,7 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_tabh);
     cudaFree(h->d_tscale);
     cudaFree(h->d_term_counter);
+    cudaFree(h->d_work);
     cudaFree(h->d_cv);
     cudaFree(h->d_prim);
     cudaFree(h->d_sens_a);

@@ -125,6 +125,7 @@ struct lm_handle {
     double prof_elems = 0.0;
     int64_t launches = 0;          // kernels this library launched (all kinds)
     unsigned long long* d_term_counter = nullptr;   // exponentials evaluated while timing
+    int* d_work = nullptr;         // row kernel's next-unit counter, zeroed before each launch
 };
 
 namespace lmmew {

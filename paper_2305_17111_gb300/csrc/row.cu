@@ -5,7 +5,8 @@
 //   a_j[q] = sum_w alpha_w [ s_prim(a,w,q) C_q(b) g(E_hat; E_w)
 //                            + sum_p s(a,w,q,p) C_p(b) g(E_hat; E'(a,w,q,p)) ]
 //
-// Work unit = (tile of <= 128 events of one angle, tile of 32 voxels).  The
+// Work unit = (tile of <= 128 events of one angle, tile of 32 voxels); the
+// persistent CTAs take units from a counter as they finish the last one.  The
 // CTA streams the angle's scatter-path tables for its 32 voxels and the
 // collimator rows of the tile's bins, 32 scatter points per stage (points in
 // the angle's ascending detector-coordinate order, only the run of chunks
@@ -51,6 +52,7 @@ struct RowParams {
     const float* cs;      // [A][npc][B][kCPad]
     const int2* crange;   // [A][B] point chunks with non-zero collimator probability
     unsigned long long* term_counter;   // if set: exponentials evaluated for valid (event, voxel)
+    int* work;            // units handed out beyond the first gridDim.x (zero at launch)
     const float* cv;      // [A][B][nq]
     const float* prim;    // [A][W][nq]
     const Tile* tiles;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_abort;
+    __shared__ int s_unit;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
@@ -273,7 +276,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     constexpr uint32_t kTabBytes = kTabBlock * 4u;
     uint32_t g = 0;                                       // pipeline stages issued so far
 
-    for (int unit = blockIdx.x; unit < n_units; unit += gridDim.x) {
+    // each CTA starts on unit blockIdx.x and then takes the next unhanded
+    // unit from the counter, so CTAs that drew lighter units take more
+    for (int unit = blockIdx.x; unit < n_units;) {
         const Tile T = P.tiles[P.tile_begin + (P.unit_order ? unit % n_tiles : unit / P.nqt)];
         const int qt = P.unit_order ? unit / n_tiles : unit % P.nqt;
         const float* lam = P.lam ? P.lam + (size_t)T.r * P.lam_stride : nullptr;
@@ -413,7 +418,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             for (int ql = 0; ql < qmax; ++ql) s = fmaf(le[qt * kQT + ql], tt[e * 33 + ql], s);
             P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
         }
+        if (tid == 0) s_unit = (int)gridDim.x + atomicAdd(P.work, 1);
         __syncthreads();
+        unit = s_unit;
     }
 }
 
@@ -484,6 +491,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     P.npc = m.npc;
     P.np = m.np;
     P.term_counter = h->prof_on ? h->d_term_counter : nullptr;
+    P.work = h->d_work;
     P.tab_stage_bytes = (uint32_t)((prec == 0 ? 3 : 2) * m.W * kQT * kPC * 4);
     uint32_t stage = P.tab_stage_bytes + (uint32_t)(m.B * kCPad * 4);
     const uint32_t tr = kET * 33 * 4;   // epilogue transpose tile
@@ -539,6 +547,7 @@ int launch_row_kernel(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     const int per_sm = h->grid_per_sm > 0 ? std::min(h->grid_per_sm, h->row_blocks[prec])
                                           : h->row_blocks[prec];
     const int grid = std::min(n_units, h->sm_count * per_sm);
+    LMMEW_CUDA(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
     row_kernel_for(h->mc.W, prec)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());

@@ -68,3 +68,38 @@ def test_batch_rerun_and_retune():
     c = lam0[:1].clone()
     gpu.osem_batch(devs[:1], c, 2, 3)      # new shape: re-tuned
     assert torch.equal(c[0], a[0])
+
+
+def test_batch_with_several_row_blocks_per_subset():
+    """A batch whose sub-iterations hold more events than one row block (4 GiB
+    of rows): each realisation's events of a subset are split over two row
+    blocks, so its back-projection chunks restart at the block boundary and
+    only the FP32 rounding of those chunk sums may differ from lm_osem.  The
+    images and log-likelihoods agree to FP32 rounding."""
+    from synthetic import simulate_cached
+    sc = preset("lmmew_128")
+    ph = sc.make_phantom()
+    pool = simulate_cached(sc)
+    gpu = lm.Model.from_scenario(sc, ph.rho)
+    n_sub, n_real, per_real = 8, 8, 420_000
+    row_floats = (gpu.nq + 3) // 4 * 4
+    assert n_real * per_real // n_sub * row_floats > 2 ** 30    # > one row block per subset
+    rng = np.random.default_rng(21)
+    evs = [pool.subset(rng.integers(0, len(pool), size=per_real)) for _ in range(n_real)]
+    devs = [lm.DeviceEvents.from_list(e) for e in evs]
+    lam0 = (ph.rho.reshape(-1) > 0).astype(np.float32)
+    imgs = torch.from_numpy(np.stack([lam0] * n_real)).cuda()
+    ll = torch.zeros(n_real, n_sub, dtype=torch.float64, device="cuda")
+    gpu.osem_batch(devs, imgs, n_sub, 1, loglik=ll)
+    torch.cuda.synchronize()
+    for i, d in enumerate(devs):
+        one = torch.from_numpy(lam0.copy()).cuda()
+        l1 = torch.zeros(n_sub, dtype=torch.float64, device="cuda")
+        gpu.osem(d, one, n_sub, 1, loglik=l1)
+        a = imgs[i].double().cpu().numpy()
+        b = one.double().cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6, f"realisation {i}"
+        big = b > 1e-3 * b.max()
+        assert float(np.max(np.abs(a[big] - b[big]) / b[big])) < 1e-5, f"realisation {i}"
+        assert torch.allclose(ll[i], l1, rtol=1e-9, atol=0.0), f"realisation {i}"
+    gpu.close()

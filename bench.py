@@ -135,10 +135,11 @@ def measured_peaks():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # current k_row revision (square-root form, collimator floor 1e-12, point
-# groups unrolled by 4) on this workload: the mean over the 8 launches of one
-# OSEM iteration in a one-pass ncu capture of the full workload.  Emptied
-# whenever k_row changes until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
+# groups unrolled by 4, units taken from a counter, point runs trimmed to
+# 4-point groups) on this workload: the mean over the 8 launches of one OSEM
+# iteration in a one-pass ncu capture of the full workload.  Emptied whenever
+# k_row changes until the counters are taken again.
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 306_793_248}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.

@@ -10,7 +10,8 @@
 // CTA streams the angle's scatter-path tables for its 32 voxels and the
 // collimator rows of the tile's bins, 32 scatter points per stage (points in
 // the angle's ascending detector-coordinate order, only the run of chunks
-// whose collimator probability for the tile's bins is non-zero), from
+// whose collimator probability for the tile's bins is non-zero, and in the
+// run's first and last chunk only its 4-point groups inside the run), from
 // global memory into shared memory with bulk asynchronous copies (TMA engine,
 // cp.async.bulk + mbarrier, double buffered).  Each of the 8 warps owns 4
 // voxels; each lane owns 4 events, so a table entry read from shared memory
@@ -50,7 +51,7 @@ struct RowParams {
                           //   (lh - base, nk) halves [W][kQT][kPC/4][8]}
     const float* tscale;  // [A][nqt][npc] 2^base of each block (reduced precision)
     const float* cs;      // [A][npc][B][kCPad]
-    const int2* crange;   // [A][B] point chunks with non-zero collimator probability
+    const int2* crange;   // [A][B] run of points with non-zero collimator probability
     unsigned long long* term_counter;   // if set: exponentials evaluated for valid (event, voxel)
     int* work;            // units handed out beyond the first gridDim.x (zero at launch)
     const float* cv;      // [A][B][nq]
@@ -153,16 +154,18 @@ template <> struct Half<2> {
     }
 };
 
-// One pipeline stage of the FP32 form: 32 scatter points x 4 voxels x 4 events
+// One pipeline stage of the FP32 form: the 4-point groups [pq0, pq1) of the
+// stage's 32 scatter points (all of them when kFull) x 4 voxels x 4 events
 // per lane, all lines.
-template <int W>
+template <int W, bool kFull>
 __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, const int* bo,
-                                           const f32x2* eh2, f32x2 (*acc2)[4]) {
+                                           const f32x2* eh2, f32x2 (*acc2)[4], int pq0, int pq1) {
     constexpr int kTabBytes = 3 * W * kQT * kPC * 4;
     const float* tb = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
     const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
+    const int lo = kFull ? 0 : pq0, hi = kFull ? kPC / 4 : pq1;
 #pragma unroll 4
-    for (int pq = 0; pq < kPC / 4; ++pq) {
+    for (int pq = lo; pq < hi; ++pq) {
         f32x2 cA[kEPL], cB[kEPL];
 #pragma unroll
         for (int k = 0; k < kEPL; ++k) {
@@ -206,7 +209,8 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
 // collimator factor.
 template <int W, int PREC>
 __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, const int* bo,
-                                           const f32x2* eh2, float scale, f32x2 (*acc2)[4]) {
+                                           const f32x2* eh2, float scale, f32x2 (*acc2)[4],
+                                           int pq0, int pq1) {
     typedef Half<PREC> H;
     constexpr int kTabBytes = 2 * W * kQT * kPC * 4;
     const float* ep = reinterpret_cast<const float*>(sb) + warp * 4 * kPC;
@@ -214,7 +218,7 @@ __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, co
     const float* cr = reinterpret_cast<const float*>(sb + kTabBytes);
     const f32x2 sc2 = pk(scale, scale);
 #pragma unroll 1
-    for (int pq = 0; pq < kPC / 4; ++pq) {
+    for (int pq = pq0; pq < pq1; ++pq) {
         f32x2 cA[kEPL], cB[kEPL];
 #pragma unroll
         for (int k = 0; k < kEPL; ++k) {
@@ -304,19 +308,22 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             for (int i = 0; i < 4; ++i) acc2[k][i] = 0ull;
 
         // scatter points whose collimator probability is non-zero for some bin
-        // of the tile: a contiguous run of chunks in this angle's point order;
+        // of the tile: a contiguous run [p_lo, p_hi) in this angle's point
+        // order, staged as whole chunks and evaluated in groups of 4 points;
         // every other term is an exact zero and is not evaluated
-        int pc_lo = P.npc, pc_hi = 0;
+        int p_lo = P.np, p_hi = 0;
         for (int b = b_lo; b <= b_hi && !P.skip_scatter; ++b) {
             const int2 r = P.crange[(size_t)T.a * P.B + b];
             if (r.y > r.x) {
-                pc_lo = min(pc_lo, r.x);
-                pc_hi = max(pc_hi, r.y);
+                p_lo = min(p_lo, r.x);
+                p_hi = max(p_hi, r.y);
             }
         }
+        const int pc_lo = p_lo < p_hi ? p_lo / kPC : 0;
+        const int pc_hi = p_lo < p_hi ? (p_hi + kPC - 1) / kPC : 0;
         if (P.term_counter && tid == 0) {
             const int nq_here = min(kQT, P.nq - qt * kQT);
-            const int np_here = pc_lo < pc_hi ? min(pc_hi * kPC, P.np) - pc_lo * kPC : 0;
+            const int np_here = p_lo < p_hi ? min((p_hi + 3) & ~3, P.np) - (p_lo & ~3) : 0;
             atomicAdd(P.term_counter,
                       (unsigned long long)T.count * nq_here * W * (unsigned long long)(np_here + 1));
         }
@@ -341,10 +348,18 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 if (!ok) s_abort = 1;
                 if (ok) {
                     const unsigned char* sb = smem + buf * P.stage_bytes;
-                    if (PREC == 0)
-                        stage_fp32<W>(sb, warp, bo, eh2, acc2);
-                    else
-                        stage_half<W, (PREC == 0 ? 1 : PREC)>(sb, warp, bo, eh2, scale_u[pc], acc2);
+                    // 4-point groups of this chunk inside the run
+                    const int pq0 = pc == pc_lo ? (p_lo - pc * kPC) >> 2 : 0;
+                    const int pq1 = pc == pc_hi - 1 ? (p_hi - pc * kPC + 3) >> 2 : kPC / 4;
+                    if (PREC == 0) {
+                        if (pq0 == 0 && pq1 == kPC / 4)
+                            stage_fp32<W, true>(sb, warp, bo, eh2, acc2, 0, kPC / 4);
+                        else
+                            stage_fp32<W, false>(sb, warp, bo, eh2, acc2, pq0, pq1);
+                    } else {
+                        stage_half<W, (PREC == 0 ? 1 : PREC)>(sb, warp, bo, eh2, scale_u[pc], acc2,
+                                                              pq0, pq1);
+                    }
                 }
                 __syncthreads();
                 if (s_abort) {

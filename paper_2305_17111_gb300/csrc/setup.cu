@@ -284,7 +284,7 @@ __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
     }
 }
 
-// For every (angle, bin): the chunks of ordered points whose collimator
+// For every (angle, bin): the run of ordered points whose collimator
 // probability for that bin is non-zero, as [first, last + 1) (0, 0 if none).
 __global__ void k_chunk_range(ModelConst m, const float* csp, int2* range) {
     const int a = blockIdx.y;
@@ -298,7 +298,7 @@ __global__ void k_chunk_range(ModelConst m, const float* csp, int2* range) {
             last = r;
         }
     }
-    range[(size_t)a * m.B + b] = first < 0 ? make_int2(0, 0) : make_int2(first / kPC, last / kPC + 1);
+    range[(size_t)a * m.B + b] = first < 0 ? make_int2(0, 0) : make_int2(first, last + 1);
 }
 
 // Unscattered paths: prim[a][w][q] = alpha_w exp(-mu_w(E_w) gamma_det) and the

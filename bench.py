@@ -134,12 +134,10 @@ def measured_peaks():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# current k_row revision (square-root form, collimator floor 1e-12, point
-# groups unrolled by 4, units taken from a counter, point runs trimmed to
-# 4-point groups) on this workload: the mean over the 8 launches of one OSEM
-# iteration in a one-pass ncu capture of the full workload.  Emptied whenever
-# k_row changes until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 306_793_248}
+# current k_row revision on this workload: the mean over the 8 launches of
+# one OSEM iteration in a one-pass ncu capture of the full workload.  Emptied
+# whenever k_row changes until the counters are taken again.
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.
@@ -715,6 +713,7 @@ def run_gpu(args, rank, local_rank, world):
     ms = e0.elapsed_time(e1)
     prof = model.profile_read()
     model.profile_enable(False)
+    row_tuning = model.batch_tuning()           # the launch shape the timed steps ran
     ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     elems_step = J * nq
@@ -762,7 +761,8 @@ def run_gpu(args, rank, local_rank, world):
                                    f"{sm_max:.0f} MHz",
                      "peak_probe": probe["f32"] * sm_count * probe["sm_mhz"] * 1e6 / 1e12,
                      "probe_ex2_per_clk_per_sm": {k: probe[k] for k in ("f32", "f16x2", "bf16x2")},
-                     "row_kernel_share": prof["ms"] / ms if ms > 0 else None},
+                     "row_kernel_share": prof["ms"] / ms if ms > 0 else None,
+                     "row_tuning": row_tuning},
     }
     if world == 1 and not args.no_forms and not args.events:
         model.close()

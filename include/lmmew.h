@@ -168,7 +168,7 @@ int lm_forward(lm_handle* h, const lm_events* events, const float* image, float*
  * all of its scratch in one 16 MiB array in the library's static device
  * memory, which every GPU that loads the library holds until the process
  * exits.  The call rejects, with LMMEW_ERR_INVALID_ARG and a message, event
- * counts whose scratch would exceed 16 MiB (about 26 + 4*ceil(nq/32) bytes
+ * counts whose scratch would exceed 16 MiB (about 27 + 4*ceil(nq/32) bytes
  * per event, nq = support voxels: some 180 000 events for a 32x32 model of
  * 484 voxels, 36 000 for a 128x128 model of 3 464); use lm_forward for
  * those.  Its first call on a device looks up the array's
@@ -200,7 +200,9 @@ int lm_backproject(lm_handle* h, const lm_events* events, const float* weight,
  * sum_q lambda_q sens_s[q] at the image entering that sub-iteration
  * (Eq. lll_med without J log T - log J!).  Resuming with the image returned
  * by an earlier call and the next (start_iter, start_subset) reproduces an
- * uninterrupted run bit for bit.  Errors: as lm_forward. */
+ * uninterrupted run bit for bit.  The row kernel's launch shape is chosen by
+ * the autotuner described at lm_batch_tuning before the first sub-iteration.
+ * Errors: as lm_forward. */
 int lm_osem(lm_handle* h, const lm_events* events, int n_subsets, int n_iters,
             int start_iter, int start_subset, float* image, double* loglik,
             lm_stream stream);
@@ -225,10 +227,9 @@ int lm_set_scatter_precision(lm_handle* h, int precision);
  * sub-iteration runs as one persistent row-kernel launch over the events of
  * every realisation (plus per-realisation back projection, FP64 log-likelihood
  * and update), and the whole n_iters x n_subsets sequence is captured once as
- * a CUDA graph and replayed on the caller's stream.  Before the capture an
- * autotuner times the row kernel's launch shapes (work-unit order x CTAs per
- * SM) on the batch's first row block and keeps the fastest; it re-tunes when
- * the batch shape (events, realisations, subsets) changes.
+ * a CUDA graph and replayed on the caller's stream.  Before the capture the
+ * autotuner described at lm_batch_tuning chooses the row kernel's launch
+ * shape.
  * events: HOST array of n_real lm_events (device pointers inside); images:
  * DEVICE float[n_real][n*n], lambda^0 in, lambda out; loglik: NULL or DEVICE
  * double[n_real][n_iters*n_subsets].  Every realisation's result equals
@@ -236,11 +237,27 @@ int lm_set_scatter_precision(lm_handle* h, int precision);
 int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subsets, int n_iters,
                   float* images, double* loglik, lm_stream stream);
 
-/* The row-kernel launch shape chosen by the last batch autotune: out4[0] =
- * work-unit order (0 tile-major, 1 voxel-tile-major), out4[1] = CTAs per SM,
- * out4[2] = 1 if tuned, out4[3] = the chosen shape's time on the tuning block
- * (ms).  Not part of the paper's method.  Errors: INVALID_ARG. */
-int lm_batch_tuning(const lm_handle* h, double* out4);
+/* The row-kernel launch shape chosen by the last autotune.  lm_osem and
+ * lm_osem_batch time, before their first sub-iteration, every candidate
+ * shape on a sample of their events (whole angles of the first subset, about
+ * 16 384 events): events per tile (32, 64 or 128 for the FP32 form with at
+ * most 4 lines, else 128) x work-unit order x CTAs per SM.  The fastest
+ * shape is stored on the handle for the workload class (log2 of the sample's
+ * mean events per angle, the scatter model and the precision): each class is
+ * timed once per handle, and a call of a class met before takes its stored
+ * shape.  Every shape gives bit-identical results.  lm_forward and
+ * lm_backproject use the last chosen shape.  out5[0] = work-unit order
+ * (0 tile-major, 1 voxel-tile-major), out5[1] = CTAs per SM (0: the
+ * occupancy limit), out5[2] = 1 if tuned, out5[3] = the chosen shape's time
+ * on the sample (ms), out5[4] = events per tile.  Not part of the paper's
+ * method.  Errors: INVALID_ARG. */
+int lm_batch_tuning(const lm_handle* h, double* out5);
+
+/* Sets the events per row-kernel tile (32, 64 or 128) for the following
+ * calls, until an autotune replaces it; lm_osem and lm_osem_batch keep it
+ * while their workload class stays the one last tuned.  Results do not
+ * depend on it.  Not part of the paper's method.  Errors: INVALID_ARG. */
+int lm_set_tile_events(lm_handle* h, int tile_events);
 
 /* ---------------------------------------------------------------------
  * Learned surrogate of the single-scatter term (not in the paper: the

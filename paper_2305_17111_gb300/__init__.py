@@ -214,10 +214,14 @@ class Model:
         return images
 
     def batch_tuning(self) -> dict:
-        out = (ctypes.c_double * 4)()
+        out = (ctypes.c_double * 5)()
         _native.check(_native.load().lm_batch_tuning(self._h, out))
         return {"unit_order": int(out[0]), "ctas_per_sm": int(out[1]), "tuned": bool(out[2]),
-                "tuned_ms": out[3]}
+                "tuned_ms": out[3], "tile_events": int(out[4])}
+
+    def set_tile_events(self, tile_events: int):
+        """Events per row-kernel tile (32, 64 or 128) until the next autotune."""
+        _native.check(_native.load().lm_set_tile_events(self._h, int(tile_events)))
 
     PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 

@@ -47,6 +47,114 @@ int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
     return LMMEW_OK;
 }
 
+// Row-kernel autotuner.  It times, with CUDA events on the caller's stream,
+// every candidate launch shape on a sample of the workload: whole angles of
+// the first subset, taken until they hold kTuneEvents events.  The
+// candidates are the events per tile (32, 64 or 128 where the FP32 form has
+// the small-tile kernels), the work-unit order and the CTAs per SM.  The
+// sample runs without forward sums or stored rows.  The choice is kept per
+// handle for each workload class: log2 of the sample's mean events per
+// angle, the scatter model and the precision.  The sorted events leave re-cut into
+// tiles of the chosen size.  Every choice gives bit-identical results: a
+// tile's size changes only which exact-zero terms it skips.
+constexpr int64_t kTuneEvents = 16384;
+
+int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t st) {
+    int g1 = 0, ng = 0;
+    int64_t ev = 0;
+    while (g1 < first_groups && ev < kTuneEvents) {
+        const int64_t c = se.h_angle_start[g1 + 1] - se.h_angle_start[g1];
+        ev += c;
+        ng += c > 0;
+        ++g1;
+    }
+    if (ev == 0) return recut_tiles(h, &se, h->tile_ev, st);
+    int bucket = 0;
+    while (bucket < 40 && (int64_t(2) << bucket) <= ev / ng) ++bucket;
+    const uint64_t key = 1ull | ((uint64_t)bucket << 8) | ((uint64_t)h->scatter_model << 4) |
+                         ((uint64_t)h->prec << 2);
+    // the class in use keeps the current shape (it may have been set by
+    // lm_set_tile_events); a class tuned before gets its stored shape back
+    if (h->tune_key == key) return recut_tiles(h, &se, h->tile_ev, st);
+    const auto hit = h->tune_cache.find(key);
+    if (hit != h->tune_cache.end()) {
+        h->tile_ev = hit->second.tile_ev;
+        h->unit_order = hit->second.unit_order;
+        h->grid_per_sm = hit->second.grid_per_sm;
+        h->tune_ms = hit->second.ms;
+        h->tune_key = key;
+        return recut_tiles(h, &se, h->tile_ev, st);
+    }
+    if (h->scatter_model == LMMEW_SCATTER_SURROGATE) {
+        // the network kernel dominates and has its own launch shape
+        h->tile_ev = kET;
+        h->unit_order = 0;
+        h->grid_per_sm = 0;
+        h->tune_key = key;
+        h->tune_ms = 0.f;
+        return recut_tiles(h, &se, kET, st);
+    }
+    const bool small_tiles = h->prec == 0 && h->mc.W <= 4;
+    const int sizes[3] = {kET, 64, 32};
+    const int n_sizes = small_tiles ? 3 : 1;
+    const int prof = h->prof_on;
+    h->prof_on = 0;   // the trial launches are not part of any timed work
+    cudaEvent_t ta, tb;
+    LMMEW_CUDA(cudaEventCreate(&ta));
+    LMMEW_CUDA(cudaEventCreate(&tb));
+    float best = 3.0e38f;
+    int best_size = kET, best_order = 0, best_grid = 0;
+    int rc = LMMEW_OK;
+    const int max_grid = h->row_blocks[h->prec];
+    for (int si = 0; si < n_sizes && rc == LMMEW_OK; ++si) {
+        rc = recut_tiles(h, &se, sizes[si], st);
+        if (rc != LMMEW_OK) break;
+        RowLaunch L{se.tiles, se.h_tile_start[0], se.h_tile_start[g1], se.bin, se.energy,
+                    nullptr, nullptr, 0, 0, nullptr, 0, ev};
+        L.tile_ev = se.tile_ev;
+        for (int order = 0; order < 2 && rc == LMMEW_OK; ++order) {
+            for (int grid = 1; grid <= max_grid && rc == LMMEW_OK; ++grid) {
+                h->unit_order = order;
+                h->grid_per_sm = grid;
+                float tmin = 3.0e38f;
+                for (int rep = 0; rep < 2 && rc == LMMEW_OK; ++rep) {
+                    cudaError_t e = cudaEventRecord(ta, st);
+                    if (e == cudaSuccess) {
+                        rc = launch_row(h, L, st);
+                        if (rc != LMMEW_OK) break;
+                        e = cudaEventRecord(tb, st);
+                    }
+                    if (e == cudaSuccess) e = cudaEventSynchronize(tb);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ta, tb);
+                    if (e != cudaSuccess) {
+                        rc = cuda_error(e, "timing a trial row launch");
+                        break;
+                    }
+                    tmin = std::min(tmin, ms);
+                }
+                if (rc == LMMEW_OK && tmin < best) {
+                    best = tmin;
+                    best_size = sizes[si];
+                    best_order = order;
+                    best_grid = grid;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(ta);
+    cudaEventDestroy(tb);
+    h->prof_on = prof;
+    if (rc != LMMEW_OK) return rc;
+    h->tile_ev = best_size;
+    h->unit_order = best_order;
+    h->grid_per_sm = best_grid;
+    h->tune_key = key;
+    h->tune_ms = best;
+    h->tune_cache[key] = lm_handle::TuneChoice{best_size, best_order, best_grid, best};
+    return recut_tiles(h, &se, best_size, st);
+}
+
 struct Chunk {
     int t0, t1;         // tile range
     int64_t e0, e1;     // sorted event range
@@ -58,8 +166,8 @@ std::vector<Chunk> plan_chunks(const SortedEvents& se, int r0, int r1, int64_t m
     Chunk cur{-1, -1, 0, 0};
     for (int r = r0; r < r1; ++r) {
         for (int t = se.h_tile_start[r]; t < se.h_tile_start[r + 1]; ++t) {
-            const int64_t b = se.h_angle_start[r] + (int64_t)(t - se.h_tile_start[r]) * kET;
-            const int64_t e = std::min<int64_t>(b + kET, se.h_angle_start[r + 1]);
+            const int64_t b = se.h_angle_start[r] + (int64_t)(t - se.h_tile_start[r]) * se.tile_ev;
+            const int64_t e = std::min<int64_t>(b + se.tile_ev, se.h_angle_start[r + 1]);
             if (cur.t0 >= 0 && (e - cur.e0) > max_events) {
                 out.push_back(cur);
                 cur.t0 = -1;
@@ -320,6 +428,7 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     for (const Chunk& c : chunks) {
         RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, keep_rows ? rs : 0,
                     ypart, c.e1 - c.e0, c.e1 - c.e0};
+        L.tile_ev = se.tile_ev;
         rc = launch_row_profiled(h, L, st);
         if (rc != LMMEW_OK) return rc;
         rc = launch_forward_out(h, ypart, c.e1 - c.e0, c.e0, c.e1 - c.e0, se.perm, out_y, st);
@@ -367,6 +476,7 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
     for (const Chunk& c : chunks) {
         RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, nullptr, rows, c.e0, rs, nullptr, 0,
                     c.e1 - c.e0};
+        L.tile_ev = se.tile_ev;
         rc = launch_row_profiled(h, L, st);
         if (rc != LMMEW_OK) return rc;
         rc = launch_bp_partial(h, rows, rs, nullptr, 0, c.e1 - c.e0, se.perm + c.e0, weight, bpart,
@@ -398,6 +508,8 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
     char* arena = (char*)h->scratch_sort.ptr;
     SortedEvents se;
     rc = sort_events(h, ev, n_subsets, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    rc = autotune_row(h, se, (m.A + n_subsets - 1) / n_subsets, st);
     if (rc != LMMEW_OK) return rc;
 
     // angle ranks of each subset and the chunks of its events
@@ -443,6 +555,7 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
                 const int64_t cnt = c.e1 - c.e0;
                 RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
                             cnt, cnt};
+                L.tile_ev = se.tile_ev;
                 rc = launch_row_profiled(h, L, st);
                 if (rc != LMMEW_OK) return rc;
                 rc = launch_bp_partial(h, rows, rs, ypart, cnt, cnt, nullptr, nullptr, bpart, row0,
@@ -499,6 +612,8 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     SortedEvents se;
     rc = sort_events_batch(h, events, R, n_subsets, &se, arena, st);
     if (rc != LMMEW_OK) return rc;
+    rc = autotune_row(h, se, A_s, st);
+    if (rc != LMMEW_OK) return rc;
 
     // plan: per subset, row blocks of whole tiles (all realisations mixed)
     const int rs = row_stride_of(h);
@@ -514,7 +629,7 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
             const int64_t e_end = se.h_angle_start[v + 1];
             int t = se.h_tile_start[v];
             for (; e < e_end; ++t) {
-                const int64_t cnt = std::min<int64_t>(kET, e_end - e);
+                const int64_t cnt = std::min<int64_t>(se.tile_ev, e_end - e);
                 if (cur.t0 >= 0 && cur.e1 - cur.e0 + cnt > max_ev) {
                     blocks.push_back(cur);
                     cur.t0 = -1;
@@ -612,50 +727,6 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     rc = launch_images_batch(h, R, images, lam_v, true, st);
     if (rc != LMMEW_OK) return rc;
 
-    // autotune the row kernel's launch shape on this batch's first row block
-    const uint64_t key = ((uint64_t)n_total << 24) ^ ((uint64_t)R << 8) ^ (uint64_t)n_subsets ^
-                         ((uint64_t)h->scatter_model << 60) ^ ((uint64_t)h->prec << 62);
-    if (h->tune_key != key && n_blk > 0) {
-        const RowBlock& c = blocks[0];
-        RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
-                    c.e1 - c.e0, c.e1 - c.e0, m.nq};
-        L.ev_real = se.real;
-        cudaEvent_t ta, tb;
-        LMMEW_CUDA(cudaEventCreate(&ta));
-        LMMEW_CUDA(cudaEventCreate(&tb));
-        float best = 3.0e38f;
-        int best_order = 0, best_grid = 0;
-        const int max_grid = h->row_blocks[h->prec];
-        for (int order = 0; order < 2; ++order) {
-            for (int grid = 1; grid <= max_grid; ++grid) {
-                h->unit_order = order;
-                h->grid_per_sm = grid;
-                float tmin = 3.0e38f;
-                for (int rep = 0; rep < 2; ++rep) {
-                    LMMEW_CUDA(cudaEventRecord(ta, st));
-                    rc = launch_row(h, L, st);
-                    if (rc != LMMEW_OK) return rc;
-                    LMMEW_CUDA(cudaEventRecord(tb, st));
-                    LMMEW_CUDA(cudaEventSynchronize(tb));
-                    float ms = 0.f;
-                    LMMEW_CUDA(cudaEventElapsedTime(&ms, ta, tb));
-                    tmin = std::min(tmin, ms);
-                }
-                if (tmin < best) {
-                    best = tmin;
-                    best_order = order;
-                    best_grid = grid;
-                }
-            }
-        }
-        cudaEventDestroy(ta);
-        cudaEventDestroy(tb);
-        h->unit_order = best_order;
-        h->grid_per_sm = best_grid;
-        h->tune_key = key;
-        h->tune_ms = best;
-    }
-
     if (n_iters == 0) return launch_images_batch(h, R, images, lam_v, false, st);
 
     // the whole reconstruction as one CUDA graph, replayed on the caller's stream
@@ -668,6 +739,7 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
                 const RowBlock& c = blocks[b];
                 RowLaunch L{se.tiles, c.t0, c.t1, se.bin, se.energy, lam_v, rows, c.e0, rs, ypart,
                             c.e1 - c.e0, c.e1 - c.e0, m.nq};
+                L.tile_ev = se.tile_ev;
                 L.ev_real = se.real;
                 rc = launch_row(h, L, cs);
                 if (rc != LMMEW_OK) break;
@@ -701,12 +773,21 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     return launch_images_batch(h, R, images, lam_v, false, st);
 }
 
-int lm_batch_tuning(const lm_handle* h, double* out4) {
-    if (!h || !out4) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
-    out4[0] = h->unit_order;
-    out4[1] = h->grid_per_sm;
-    out4[2] = h->tune_key != 0 ? 1.0 : 0.0;
-    out4[3] = h->tune_ms;
+int lm_batch_tuning(const lm_handle* h, double* out5) {
+    if (!h || !out5) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    out5[0] = h->unit_order;
+    out5[1] = h->grid_per_sm;
+    out5[2] = h->tune_key != 0 ? 1.0 : 0.0;
+    out5[3] = h->tune_ms;
+    out5[4] = h->tile_ev;
+    return LMMEW_OK;
+}
+
+int lm_set_tile_events(lm_handle* h, int tile_events) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    if (tile_events != 32 && tile_events != 64 && tile_events != kET)
+        return set_error(LMMEW_ERR_INVALID_ARG, "tile_events must be 32, 64 or 128");
+    h->tile_ev = tile_events;
     return LMMEW_OK;
 }
 

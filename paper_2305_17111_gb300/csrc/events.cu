@@ -4,7 +4,7 @@
 // per-block histograms, one global scan, stable per-block scatter by warp
 // match).  The sorted order groups each angle's events contiguously, subsets
 // in ascending order (subset(a) = a mod n_subsets, paper Sec. LM-OSEM), and
-// cuts every angle's run into tiles of up to kET events for the row kernel.
+// cuts every angle's run into tiles of up to tile_ev events for the row kernel.
 #include <algorithm>
 #include <vector>
 
@@ -139,14 +139,15 @@ __global__ void k_bounds(const uint32_t* keys, int64_t n, int A, int B, int* sta
     start[r] = (int)lo;
 }
 
-// tile_start[r] = sum over ranks < r of ceil(count / kET); one block.
-__global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int* tile_start) {
+// tile_start[r] = sum over ranks < r of ceil(count / tile_ev); one block.
+__global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int tile_ev,
+                                                    int* tile_start) {
     __shared__ int part[1024];
     const int t = threadIdx.x;
     const int per = (A + 1023) / 1024;
     const int lo = t * per, hi = min(A, lo + per);
     int s = 0;
-    for (int r = lo; r < hi; ++r) s += (start[r + 1] - start[r] + kET - 1) / kET;
+    for (int r = lo; r < hi; ++r) s += (start[r + 1] - start[r] + tile_ev - 1) / tile_ev;
     part[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -158,19 +159,20 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int
     int run = part[t] - s;
     for (int r = lo; r < hi; ++r) {
         tile_start[r] = run;
-        run += (start[r + 1] - start[r] + kET - 1) / kET;
+        run += (start[r + 1] - start[r] + tile_ev - 1) / tile_ev;
     }
     if (t == 1023) tile_start[A] = part[1023];
 }
 
 __global__ void k_tiles(const int* start, const int* tile_start, const int* angle_of_rank, int A,
-                        const uint16_t* bin_s, Tile* tiles, const int* real_of_rank = nullptr) {
+                        int tile_ev, const uint16_t* bin_s, Tile* tiles,
+                        const int* real_of_rank = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A) return;
     const int b0 = start[r], b1 = start[r + 1];
     int t = tile_start[r];
-    for (int e = b0; e < b1; e += kET, ++t) {
-        const int cnt = min(kET, b1 - e);
+    for (int e = b0; e < b1; e += tile_ev, ++t) {
+        const int cnt = min(tile_ev, b1 - e);
         Tile T;
         T.a = angle_of_rank[r];
         T.begin = e;
@@ -193,7 +195,7 @@ size_t sort_scratch_bytes(int64_t n, int A) {
     add(4 * n); add(2 * n); add(4 * n);                 // perm, bins, energies
     add(4 * (A + 1)); add(4 * (A + 1)); add(4 * A);     // angle_start, tile_start, angle_of_rank
     add(4 * A);                                         // rank_of_angle
-    add(sizeof(Tile) * (size_t)(n / kET + A + 1));      // tiles
+    add(sizeof(Tile) * (size_t)(n / kETMin + A + 1));   // tiles (smallest tile size)
     return b;
 }
 
@@ -222,7 +224,10 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
     out->tile_start = bump<int>(arena, A + 1);
     int* d_angle_of_rank = bump<int>(arena, A);
     int* d_rank_of_angle = bump<int>(arena, A);
-    out->tiles = bump<Tile>(arena, n / kET + A + 1);
+    out->tiles = bump<Tile>(arena, n / kETMin + A + 1);
+    out->tile_ev = h->tile_ev;
+    out->n_groups = A;
+    out->angle_of_group = d_angle_of_rank;
 
     LMMEW_CUDA(cudaMemcpyAsync(d_rank_of_angle, rank_of_angle.data(), sizeof(int) * A,
                                cudaMemcpyHostToDevice, st));
@@ -265,10 +270,10 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
     } else {
         LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (A + 1), st));
     }
-    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, A, out->tile_start);
+    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, A, out->tile_ev, out->tile_start);
     ++h->launches;
     k_tiles<<<(A + 127) / 128, 128, 0, st>>>(out->angle_start, out->tile_start, d_angle_of_rank, A,
-                                             out->bin, out->tiles);
+                                             out->tile_ev, out->bin, out->tiles);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     // one synchronisation: validation status and the work sizes
@@ -324,7 +329,8 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
     int* tile_start = bump<int>(arena, A + 1);
     int* d_angle_of_rank = bump<int>(arena, A);
     int* d_rank_of_angle = bump<int>(arena, A);
-    out->tiles = bump<Tile>(arena, n / kET + A + 1);
+    out->tiles = bump<Tile>(arena, n / kETMin + A + 1);
+    out->tile_ev = h->tile_ev;
 
     k_identity<<<(A + 255) / 256, 256, 0, st>>>(d_rank_of_angle, d_angle_of_rank, A);
     float w[8][2] = {};
@@ -351,9 +357,9 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
     k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B, out->perm,
                                                          out->bin, out->energy);
     k_bounds<<<(A + 1 + 127) / 128, 128, 0, st>>>(kin, n, A, B, angle_start);
-    k_tile_scan<<<1, 1024, 0, st>>>(angle_start, A, tile_start);
-    k_tiles<<<(A + 127) / 128, 128, 0, st>>>(angle_start, tile_start, d_angle_of_rank, A, out->bin,
-                                             out->tiles);
+    k_tile_scan<<<1, 1024, 0, st>>>(angle_start, A, out->tile_ev, tile_start);
+    k_tiles<<<(A + 127) / 128, 128, 0, st>>>(angle_start, tile_start, d_angle_of_rank, A,
+                                             out->tile_ev, out->bin, out->tiles);
     LMMEW_CUDA(cudaGetLastError());
     h->launches += 6 + 3 * ((bits + 7) / 8);
     int host3[3] = {0, 0, 0};   // tiles, valid events, status
@@ -470,7 +476,7 @@ size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R) {
     add(2 * n); add(2 * n); add(4 * n);                 // concatenated events
     add(4 * (V + 1)); add(4 * (V + 1)); add(4 * V);
     add(8 * (R + 1));
-    add(sizeof(Tile) * (size_t)(n / kET + V + 1));
+    add(sizeof(Tile) * (size_t)(n / kETMin + V + 1));
     return b;
 }
 
@@ -506,7 +512,10 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     out->tile_start = bump<int>(arena, V + 1);
     int* d_angle_of_v = bump<int>(arena, V);
     int64_t* d_off = bump<int64_t>(arena, R + 1);
-    out->tiles = bump<Tile>(arena, n / kET + V + 1);
+    out->tiles = bump<Tile>(arena, n / kETMin + V + 1);
+    out->tile_ev = h->tile_ev;
+    out->n_groups = (int)V;
+    out->angle_of_group = d_angle_of_v;
 
     for (int r = 0; r < R; ++r) {
         if (evs[r].n == 0) continue;
@@ -542,9 +551,10 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     } else {
         LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (V + 1), st));
     }
-    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, (int)V, out->tile_start);
+    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, (int)V, out->tile_ev, out->tile_start);
     k_tiles<<<(unsigned)((V + 127) / 128), 128, 0, st>>>(out->angle_start, out->tile_start,
-                                                         d_angle_of_v, (int)V, out->bin, out->tiles);
+                                                         d_angle_of_v, (int)V, out->tile_ev,
+                                                         out->bin, out->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     out->h_angle_start.resize(V + 1);
@@ -597,6 +607,27 @@ int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_sta
     LMMEW_CUDA(cudaMemcpyAsync(h_grp_start.data(), grp_start, 4 * (G + 1), cudaMemcpyDeviceToHost,
                                st));
     LMMEW_CUDA(cudaStreamSynchronize(st));
+    return LMMEW_OK;
+}
+
+// Re-cut the sorted groups into tiles of tile_ev events: the tile array was
+// sized for the smallest tile, so every size fits.
+int recut_tiles(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st) {
+    if (tile_ev != 32 && tile_ev != 64 && tile_ev != kET)
+        return set_error(LMMEW_ERR_INVALID_ARG, "tile size must be 32, 64 or 128 events");
+    if (se->tile_ev == tile_ev) return LMMEW_OK;
+    const int G = se->n_groups;
+    k_tile_scan<<<1, 1024, 0, st>>>(se->angle_start, G, tile_ev, se->tile_start);
+    k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->angle_start, se->tile_start,
+                                                         se->angle_of_group, G, tile_ev, se->bin,
+                                                         se->tiles);
+    h->launches += 2;
+    LMMEW_CUDA(cudaGetLastError());
+    se->h_tile_start.resize(G + 1);
+    LMMEW_CUDA(cudaMemcpyAsync(se->h_tile_start.data(), se->tile_start, 4 * (size_t)(G + 1),
+                               cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    se->tile_ev = tile_ev;
     return LMMEW_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <map>
 #include <vector>
 
 #include "lmmew.h"
@@ -14,8 +15,9 @@ namespace lmmew {
 // ---------------------------------------------------------------- tiling
 constexpr int kQT = 32;     // voxels per q-tile of the row kernel
 constexpr int kPC = 32;     // scatter points per pipeline stage
-constexpr int kET = 128;    // events per tile (kEPL per lane, 32 lanes)
+constexpr int kET = 128;    // largest tile: events per tile (kEPL per lane, 32 lanes)
 constexpr int kEPL = kET / 32;
+constexpr int kETMin = 32;  // smallest tile (one event per lane); tile arrays are sized for it
 constexpr int kCPad = 36;   // floats per staged collimator row (32 + 4 pad)
 constexpr int kRowThreads = 256;
 constexpr float kNegHuge = -1.0e30f;   // log2 weight of an absent path
@@ -52,11 +54,11 @@ struct LineConst {
     float norm[LMMEW_MAX_LINES];   // 1 / (sqrt(2 pi) sigma_E(E))
 };
 
-// One tile of events: one angle, up to kET consecutive sorted events.
+// One tile of events: one angle, up to tile_ev (<= kET) consecutive sorted events.
 struct Tile {
     int a;          // detector angle
     int begin;      // first sorted event (index into the sorted arrays)
-    int count;      // 1..kET
+    int count;      // 1..tile_ev
     int b_lo_hi;    // (b_lo << 16) | b_hi: bin range of the tile's events
     int r;          // realisation (0 outside batched reconstruction)
 };
@@ -98,7 +100,13 @@ struct lm_handle {
     cudaStream_t cap_stream = nullptr;     // private stream for CUDA-graph capture
     cudaGraphExec_t graph_exec = nullptr;  // last batched reconstruction graph
     cudaGraph_t graph = nullptr;
-    uint64_t tune_key = 0;         // batch shape the launch shape was tuned for
+    uint64_t tune_key = 0;         // workload class the current launch shape belongs to
+    struct TuneChoice {
+        int tile_ev, unit_order, grid_per_sm;
+        float ms;
+    };
+    std::map<uint64_t, TuneChoice> tune_cache;   // every workload class tuned on this handle
+    int tile_ev = lmmew::kET;      // events per tile of the row kernel: 32, 64 or 128 (tuned)
     float tune_ms = 0.f;           // the tuned row launch's time
     // scatter-term precision: 0 FP32, 1 FP16, 2 BF16 (reduced-precision form)
     int prec = 0;
@@ -152,6 +160,9 @@ struct SortedEvents {
     Tile* tiles = nullptr;       // [max_tiles]
     int* tile_start = nullptr;   // [A+1] first tile of each angle rank
     int64_t n_valid = 0;
+    int tile_ev = kET;           // events per tile the tiles were cut with
+    int n_groups = 0;            // angle groups (ranks) the tiles are cut in
+    const int* angle_of_group = nullptr;   // device [n_groups]: angle of each group
     // batched sort only
     uint16_t* real = nullptr;    // [n] realisation of each sorted event
     uint32_t* bp_idx = nullptr;  // [n] back-projection order (bp_order_batch)
@@ -175,6 +186,7 @@ struct SortedFixed {
     Tile* tiles = nullptr;
     int n_tiles = 0;
     int64_t n_valid = 0;
+    int tile_ev = kET;
 };
 size_t sort_fixed_bytes(int64_t n, int A);
 size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R);
@@ -182,6 +194,8 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                       SortedEvents* out, char*& arena, cudaStream_t st);
 int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_start, int n_blk,
                    int* grp_start, std::vector<int>& h_grp_start, cudaStream_t st);
+// Re-cut the sorted groups into tiles of tile_ev events (h_tile_start updated).
+int recut_tiles(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st);
 int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
                       cudaStream_t st);
 
@@ -199,6 +213,7 @@ struct RowLaunch {
     int64_t ypart_stride;
     int64_t n_events;       // events covered by the tile range (for accounting)
     int lam_stride = 0;     // batched: image of realisation r at lam_v + r * lam_stride
+    int tile_ev = kET;      // events per tile the tiles were cut with (32, 64 or 128)
     const uint16_t* ev_real = nullptr;   // batched: realisation of each sorted event
     int skip_scatter = 0;   // unscattered terms only (the surrogate adds the rest)
 };

@@ -73,6 +73,7 @@ extern "C" int lm_forward_noalloc(lm_handle* h, const lm_events* ev, const float
     if (rc != LMMEW_OK) return rc;
     RowLaunch L{se.tiles, 0, se.n_tiles, se.bin, se.energy, lam_v, nullptr, 0, 0, ypart, n,
                 se.n_valid};
+    L.tile_ev = se.tile_ev;
     rc = launch_row(h, L, st);
     if (rc != LMMEW_OK) return rc;
     return launch_forward_out(h, ypart, n, 0, se.n_valid, se.perm, out_y, st);

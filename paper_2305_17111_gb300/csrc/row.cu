@@ -157,7 +157,7 @@ template <> struct Half<2> {
 // One pipeline stage of the FP32 form: the 4-point groups [pq0, pq1) of the
 // stage's 32 scatter points (all of them when kFull) x 4 voxels x 4 events
 // per lane, all lines.
-template <int W, bool kFull>
+template <int W, bool kFull, int EPL>
 __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, const int* bo,
                                            const f32x2* eh2, f32x2 (*acc2)[4], int pq0, int pq1) {
     constexpr int kTabBytes = 3 * W * kQT * kPC * 4;
@@ -166,9 +166,9 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
     const int lo = kFull ? 0 : pq0, hi = kFull ? kPC / 4 : pq1;
 #pragma unroll 4
     for (int pq = lo; pq < hi; ++pq) {
-        f32x2 cA[kEPL], cB[kEPL];
+        f32x2 cA[EPL], cB[EPL];
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k) {
+        for (int k = 0; k < EPL; ++k) {
             const float4 c4 = *reinterpret_cast<const float4*>(cr + bo[k] * kCPad + pq * 4);
             cA[k] = pk(c4.x, c4.y);
             cB[k] = pk(c4.z, c4.w);
@@ -176,7 +176,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
 #pragma unroll
         for (int qi = 0; qi < 4; ++qi) {
             const float* tq = tb + qi * kPC + pq * 4;
-            f32x2 inA[kEPL], inB[kEPL];
+            f32x2 inA[EPL], inB[EPL];
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 const float4 nl = *reinterpret_cast<const float4*>(tq + (0 * W + w) * kQT * kPC);
@@ -186,7 +186,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
                 const f32x2 srA = pk(sr.x, sr.y), srB = pk(sr.z, sr.w);
                 const f32x2 mA = pk(mm.x, mm.y), mB = pk(mm.z, mm.w);
 #pragma unroll
-                for (int k = 0; k < kEPL; ++k) {
+                for (int k = 0; k < EPL; ++k) {
                     const f32x2 tA = term2(eh2[k], srA, mA, nlA);
                     const f32x2 tB = term2(eh2[k], srB, mB, nlB);
                     inA[k] = (w == 0) ? tA : add2(inA[k], tA);
@@ -194,7 +194,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, int warp, co
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kEPL; ++k) {
+            for (int k = 0; k < EPL; ++k) {
                 acc2[k][qi] = fma2(cA[k], inA[k], acc2[k][qi]);
                 acc2[k][qi] = fma2(cB[k], inB[k], acc2[k][qi]);
             }
@@ -257,7 +257,7 @@ __device__ __forceinline__ void stage_half(const unsigned char* sb, int warp, co
     }
 }
 
-template <int W, int PREC>
+template <int W, int PREC, int EPL>
 __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
@@ -289,11 +289,11 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         const int b_lo = T.b_lo_hi >> 16, b_hi = T.b_lo_hi & 0xffff;
         const uint32_t c_bytes = (uint32_t)(b_hi - b_lo + 1) * kCPad * 4u;
 
-        float eh[kEPL];
-        f32x2 eh2[kEPL];
-        int bo[kEPL];
+        float eh[EPL];
+        f32x2 eh2[EPL];
+        int bo[EPL];
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k) {
+        for (int k = 0; k < EPL; ++k) {
             const int e = k * 32 + lane;
             const bool v = e < T.count;
             eh[k] = v ? P.ev_e[T.begin + e] : 0.f;
@@ -301,9 +301,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             bo[k] = v ? (int)P.ev_bin[T.begin + e] - b_lo : 0;
         }
         // two partial sums per (event, voxel): even and odd scatter points
-        f32x2 acc2[kEPL][4];
+        f32x2 acc2[EPL][4];
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k)
+        for (int k = 0; k < EPL; ++k)
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc2[k][i] = 0ull;
 
@@ -351,14 +351,14 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                     // 4-point groups of this chunk inside the run
                     const int pq0 = pc == pc_lo ? (p_lo - pc * kPC) >> 2 : 0;
                     const int pq1 = pc == pc_hi - 1 ? (p_hi - pc * kPC + 3) >> 2 : kPC / 4;
-                    if (PREC == 0) {
+                    if constexpr (PREC == 0) {
                         if (pq0 == 0 && pq1 == kPC / 4)
-                            stage_fp32<W, true>(sb, warp, bo, eh2, acc2, 0, kPC / 4);
+                            stage_fp32<W, true, EPL>(sb, warp, bo, eh2, acc2, 0, kPC / 4);
                         else
-                            stage_fp32<W, false>(sb, warp, bo, eh2, acc2, pq0, pq1);
+                            stage_fp32<W, false, EPL>(sb, warp, bo, eh2, acc2, pq0, pq1);
                     } else {
-                        stage_half<W, (PREC == 0 ? 1 : PREC)>(sb, warp, bo, eh2, scale_u[pc], acc2,
-                                                              pq0, pq1);
+                        static_assert(PREC == 0 || EPL == kEPL, "reduced precision uses 128-event tiles");
+                        stage_half<W, PREC>(sb, warp, bo, eh2, scale_u[pc], acc2, pq0, pq1);
                     }
                 }
                 __syncthreads();
@@ -375,9 +375,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             }
         }
 
-        float acc[kEPL][4];
+        float acc[EPL][4];
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k)
+        for (int k = 0; k < EPL; ++k)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 float lo, hi;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 const int q = qt * kQT + warp * 4 + qi;
                 if (q < P.nq) {
 #pragma unroll
-                    for (int k = 0; k < kEPL; ++k) {
+                    for (int k = 0; k < EPL; ++k) {
                         if (k * 32 + lane < T.count) {
                             float s = 0.f;
 #pragma unroll
@@ -412,12 +412,12 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         // transpose through shared memory: tile [128 events][32 voxels]
         float* tt = reinterpret_cast<float*>(smem);
 #pragma unroll
-        for (int k = 0; k < kEPL; ++k)
+        for (int k = 0; k < EPL; ++k)
 #pragma unroll
             for (int qi = 0; qi < 4; ++qi) tt[(k * 32 + lane) * 33 + warp * 4 + qi] = acc[k][qi];
         __syncthreads();
         if (P.rows) {
-            for (int i = tid; i < kET * kQT; i += kRowThreads) {
+            for (int i = tid; i < 32 * EPL * kQT; i += kRowThreads) {
                 const int e = i >> 5, ql = i & 31;
                 const int q = qt * kQT + ql;
                 if (e < T.count && q < P.nq)
@@ -440,34 +440,53 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 }
 
 typedef void (*RowKernel)(const RowParams);
-RowKernel row_kernel_for(int W, int prec) {
+// Kernel for W lines, scatter precision prec and epl events per lane (tiles
+// of 32 epl events).  Tiles of 32 and 64 events exist for the FP32 form with
+// up to 4 lines; everything else runs 128-event tiles.
+RowKernel row_kernel_for(int W, int prec, int epl = kEPL) {
+    if (prec == 0 && W <= 4 && epl == 1) {
+        switch (W) {
+            case 1: return k_row<1, 0, 1>;
+            case 2: return k_row<2, 0, 1>;
+            case 3: return k_row<3, 0, 1>;
+            default: return k_row<4, 0, 1>;
+        }
+    }
+    if (prec == 0 && W <= 4 && epl == 2) {
+        switch (W) {
+            case 1: return k_row<1, 0, 2>;
+            case 2: return k_row<2, 0, 2>;
+            case 3: return k_row<3, 0, 2>;
+            default: return k_row<4, 0, 2>;
+        }
+    }
     if (prec == 1) {
         switch (W) {
-            case 1: return k_row<1, 1>;
-            case 2: return k_row<2, 1>;
-            case 3: return k_row<3, 1>;
-            case 4: return k_row<4, 1>;
+            case 1: return k_row<1, 1, kEPL>;
+            case 2: return k_row<2, 1, kEPL>;
+            case 3: return k_row<3, 1, kEPL>;
+            case 4: return k_row<4, 1, kEPL>;
             default: return nullptr;
         }
     }
     if (prec == 2) {
         switch (W) {
-            case 1: return k_row<1, 2>;
-            case 2: return k_row<2, 2>;
-            case 3: return k_row<3, 2>;
-            case 4: return k_row<4, 2>;
+            case 1: return k_row<1, 2, kEPL>;
+            case 2: return k_row<2, 2, kEPL>;
+            case 3: return k_row<3, 2, kEPL>;
+            case 4: return k_row<4, 2, kEPL>;
             default: return nullptr;
         }
     }
     switch (W) {
-        case 1: return k_row<1, 0>;
-        case 2: return k_row<2, 0>;
-        case 3: return k_row<3, 0>;
-        case 4: return k_row<4, 0>;
-        case 5: return k_row<5, 0>;
-        case 6: return k_row<6, 0>;
-        case 7: return k_row<7, 0>;
-        default: return k_row<8, 0>;
+        case 1: return k_row<1, 0, kEPL>;
+        case 2: return k_row<2, 0, kEPL>;
+        case 3: return k_row<3, 0, kEPL>;
+        case 4: return k_row<4, 0, kEPL>;
+        case 5: return k_row<5, 0, kEPL>;
+        case 6: return k_row<6, 0, kEPL>;
+        case 7: return k_row<7, 0, kEPL>;
+        default: return k_row<8, 0, kEPL>;
     }
 }
 
@@ -544,6 +563,15 @@ int row_kernel_occupancy(lm_handle* h) {
             continue;
         }
         LMMEW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        // the 32- and 64-event tile kernels of the FP32 form (same stages)
+        for (int epl = 1; prec == 0 && epl < kEPL; epl *= 2) {
+            RowKernel small = row_kernel_for(h->mc.W, 0, epl);
+            if (small == kern) continue;
+            cudaFuncAttributes fs;
+            LMMEW_CUDA(cudaFuncGetAttributes(&fs, small));
+            LMMEW_CUDA(cudaFuncSetAttribute(small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            max_optin - (int)fs.sharedSizeBytes));
+        }
         int blocks = 0;
         LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kRowThreads, smem));
         h->row_blocks[prec] = blocks > 0 ? blocks : 1;
@@ -562,8 +590,11 @@ int launch_row_kernel(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     const int per_sm = h->grid_per_sm > 0 ? std::min(h->grid_per_sm, h->row_blocks[prec])
                                           : h->row_blocks[prec];
     const int grid = std::min(n_units, h->sm_count * per_sm);
+    // events per lane: the tiles were cut with L.tile_ev events; the
+    // 128-event kernel serves any tile (and every form without small tiles)
+    const int epl = L.tile_ev == 32 ? 1 : (L.tile_ev == 64 ? 2 : kEPL);
     LMMEW_CUDA(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
-    row_kernel_for(h->mc.W, prec)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    row_kernel_for(h->mc.W, prec, epl)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

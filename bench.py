@@ -134,10 +134,11 @@ def measured_peaks():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# current k_row revision on this workload: the mean over the 8 launches of
+# current k_row revision on this workload, in the tile size the autotuner
+# picks for it (64 events: k_row<3, 0, 2>): the mean over the 8 launches of
 # one OSEM iteration in a one-pass ncu capture of the full workload.  Emptied
 # whenever k_row changes until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {}
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 308_060_544}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.

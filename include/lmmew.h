@@ -238,10 +238,11 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
                   float* images, double* loglik, lm_stream stream);
 
 /* The row-kernel launch shape chosen by the last autotune.  lm_osem and
- * lm_osem_batch time, before their first sub-iteration, every candidate
- * shape on a sample of their events (whole angles of the first subset, about
- * 16 384 events): events per tile (32, 64 or 128 for the FP32 form with at
- * most 4 lines, else 128) x work-unit order x CTAs per SM.  The fastest
+ * lm_osem_batch time, before their first sub-iteration, launch shapes on a
+ * sample of their events (whole angles of the first subset, about 16 384
+ * events): every events-per-tile size (32, 64 or 128 for the FP32 form with
+ * at most 4 lines, else 128) x work-unit order at the occupancy limit of
+ * CTAs per SM, then the best of those with one CTA per SM fewer.  The fastest
  * shape is stored on the handle for the workload class (log2 of the sample's
  * mean events per angle, the scatter model and the precision): each class is
  * timed once per handle, and a call of a class met before takes its stored

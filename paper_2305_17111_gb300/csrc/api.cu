@@ -48,10 +48,12 @@ int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
 }
 
 // Row-kernel autotuner.  It times, with CUDA events on the caller's stream,
-// every candidate launch shape on a sample of the workload: whole angles of
-// the first subset, taken until they hold kTuneEvents events.  The
-// candidates are the events per tile (32, 64 or 128 where the FP32 form has
-// the small-tile kernels), the work-unit order and the CTAs per SM.  The
+// candidate launch shapes on a sample of the workload: whole angles of the
+// first subset, taken until they hold kTuneEvents events.  After one
+// warm-up launch it tries every events-per-tile size (32, 64 or 128 where
+// the FP32 form has the small-tile kernels) x work-unit order at the
+// occupancy limit of CTAs per SM, then the best of those with one CTA per SM
+// fewer.  The
 // sample runs without forward sums or stored rows.  The choice is kept per
 // handle for each workload class: log2 of the sample's mean events per
 // angle, the scatter model and the precision.  The sorted events leave re-cut into
@@ -102,44 +104,59 @@ int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t 
     cudaEvent_t ta, tb;
     LMMEW_CUDA(cudaEventCreate(&ta));
     LMMEW_CUDA(cudaEventCreate(&tb));
-    float best = 3.0e38f;
-    int best_size = kET, best_order = 0, best_grid = 0;
     int rc = LMMEW_OK;
-    const int max_grid = h->row_blocks[h->prec];
-    for (int si = 0; si < n_sizes && rc == LMMEW_OK; ++si) {
-        rc = recut_tiles(h, &se, sizes[si], st);
-        if (rc != LMMEW_OK) break;
+    int reps = 1;
+    // one trial: the sample in tiles of `size` events, unit order, CTAs per SM;
+    // the shortest of `reps` launches (two when a launch is under 2 ms)
+    auto trial = [&](int size, int order, int grid, float* ms_out) -> int {
+        int r = recut_tiles(h, &se, size, st);
+        if (r != LMMEW_OK) return r;
         RowLaunch L{se.tiles, se.h_tile_start[0], se.h_tile_start[g1], se.bin, se.energy,
                     nullptr, nullptr, 0, 0, nullptr, 0, ev};
         L.tile_ev = se.tile_ev;
-        for (int order = 0; order < 2 && rc == LMMEW_OK; ++order) {
-            for (int grid = 1; grid <= max_grid && rc == LMMEW_OK; ++grid) {
-                h->unit_order = order;
-                h->grid_per_sm = grid;
-                float tmin = 3.0e38f;
-                for (int rep = 0; rep < 2 && rc == LMMEW_OK; ++rep) {
-                    cudaError_t e = cudaEventRecord(ta, st);
-                    if (e == cudaSuccess) {
-                        rc = launch_row(h, L, st);
-                        if (rc != LMMEW_OK) break;
-                        e = cudaEventRecord(tb, st);
-                    }
-                    if (e == cudaSuccess) e = cudaEventSynchronize(tb);
-                    float ms = 0.f;
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ta, tb);
-                    if (e != cudaSuccess) {
-                        rc = cuda_error(e, "timing a trial row launch");
-                        break;
-                    }
-                    tmin = std::min(tmin, ms);
-                }
-                if (rc == LMMEW_OK && tmin < best) {
-                    best = tmin;
-                    best_size = sizes[si];
-                    best_order = order;
-                    best_grid = grid;
-                }
+        h->unit_order = order;
+        h->grid_per_sm = grid;
+        float tmin = 3.0e38f;
+        for (int rep = 0; rep < reps; ++rep) {
+            cudaError_t e = cudaEventRecord(ta, st);
+            if (e == cudaSuccess) {
+                r = launch_row(h, L, st);
+                if (r != LMMEW_OK) return r;
+                e = cudaEventRecord(tb, st);
             }
+            if (e == cudaSuccess) e = cudaEventSynchronize(tb);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ta, tb);
+            if (e != cudaSuccess) return cuda_error(e, "timing a trial row launch");
+            tmin = std::min(tmin, ms);
+        }
+        *ms_out = tmin;
+        return LMMEW_OK;
+    };
+    const int max_grid = h->row_blocks[h->prec];
+    float best = 3.0e38f, warm = 0.f;
+    int best_size = kET, best_order = 0, best_grid = max_grid;
+    rc = trial(kET, 0, max_grid, &warm);          // warm-up; sets the repeat count
+    if (rc == LMMEW_OK && warm < 2.0f) reps = 2;
+    // tile size x unit order at the occupancy limit, then the best of those
+    // with one CTA per SM fewer
+    for (int si = 0; si < n_sizes && rc == LMMEW_OK; ++si) {
+        for (int order = 0; order < 2 && rc == LMMEW_OK; ++order) {
+            float ms = 0.f;
+            rc = trial(sizes[si], order, max_grid, &ms);
+            if (rc == LMMEW_OK && ms < best) {
+                best = ms;
+                best_size = sizes[si];
+                best_order = order;
+            }
+        }
+    }
+    if (rc == LMMEW_OK && max_grid > 1) {
+        float ms = 0.f;
+        rc = trial(best_size, best_order, max_grid - 1, &ms);
+        if (rc == LMMEW_OK && ms < best) {
+            best = ms;
+            best_grid = max_grid - 1;
         }
     }
     cudaEventDestroy(ta);

@@ -452,7 +452,19 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     model.set_scatter_model("exact")
     ex = res["exact"]
     roi_ex = roi_sums(ex["img"], ph.lesion_masks)
-    samples_per_iter = len(ev) * model.nq * len(sc.line_keV)
+    # samples the network evaluates: (event, voxel, line) with the recorded
+    # energy inside the line's single-scatter reach (backscatter energy to
+    # E_w, widened by 8 energy-resolution sigmas; the library's rule)
+    def sigma_e(e):
+        return sc.fwhm_frac * e * (e / sc.e_ref_keV) ** sc.fwhm_exponent / (2 * np.sqrt(2 * np.log(2)))
+    e_hat = np.asarray(ev.energy, dtype=np.float64)
+    reachable = 0
+    for e_w in sc.line_keV:
+        e_back = e_w / (1 + 2 * e_w / 510.99895)
+        reachable += int(np.count_nonzero((e_hat >= e_back - 8 * sigma_e(e_back))
+                                          & (e_hat <= e_w + 8 * sigma_e(e_w))))
+    samples_per_iter = reachable * model.nq
+    dense_samples_per_iter = len(ev) * model.nq * len(sc.line_keV)
     flop_per_sample = 2 * (32 * 128 + 2 * 128 * 128) + 2 * 128
     out = {"workload": f"{sc.name}: {sc.n}x{sc.n}, {sc.n_angles} angles, {sc.n_bins} bins, "
                        f"{sc.scatter_n}x{sc.scatter_n} scatter grid, {len(ev)} events, "
@@ -476,6 +488,8 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
                      "image_rel_l2_vs_exact": float(np.linalg.norm(r["img"] - ex["img"])
                                                     / np.linalg.norm(ex["img"])),
                      "roi_rel_dev_vs_exact": [abs(a - b) / b for a, b in zip(roi, roi_ex)]}
+    out["surrogate"]["network_samples_per_iter"] = samples_per_iter
+    out["surrogate"]["samples_in_reach_fraction"] = samples_per_iter / dense_samples_per_iter
     out["surrogate"]["network_samples_per_s"] = samples_per_iter / res["surrogate"]["s_per_iter"]
     out["surrogate"]["network_tflops"] = (samples_per_iter * flop_per_sample
                                           / res["surrogate"]["s_per_iter"] / 1e12)

@@ -37,6 +37,8 @@ Parity status and pins (tests/test_oracle_mlp.py):
                       parameter by lr |g| / (|g| + eps) against g
   init_params       - the published SplitMix64 generator (Steele, Lea and
                       Flood, 2014) checked against its reference outputs
+  scatter_reach     - the oracle's exact single-scatter sum of a line just
+                      outside the range is below 1e-9 of its value inside
 """
 from __future__ import annotations
 
@@ -189,6 +191,19 @@ def compton_kappa(e_hat, e_line):
     """1 - cos(phi) of the single scatter that takes e_line to e_hat
     (Compton: 1/E' - 1/E = (1 - cos phi) / m_e c^2)."""
     return ELECTRON_REST_KEV * (1.0 / e_hat - 1.0 / e_line)
+
+
+def scatter_reach(e_line, fwhm_frac, e_ref, exponent, n_sigma=8.0):
+    """(lo, hi): the recorded energies that one Compton scatter of a photon of
+    energy e_line can produce, widened by n_sigma energy-resolution sigmas.
+    A single scatter gives E' between the backscatter energy
+    e_line / (1 + 2 e_line / m_e c^2) and e_line; the detector blurs E' with a
+    Gaussian of FWHM = fwhm_frac E (E / e_ref)^exponent.  The surrogate's
+    scatter part of line w is zero outside (lo, hi)."""
+    def sigma(e):
+        return fwhm_frac * e * (e / e_ref) ** exponent / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    e_back = e_line / (1.0 + 2.0 * e_line / ELECTRON_REST_KEV)
+    return e_back - n_sigma * sigma(e_back), e_line + n_sigma * sigma(e_line)
 
 
 def features(x, y, theta, u_b, e_hat, w, e_line, optical_depth8, rho_map, pixel_cm):

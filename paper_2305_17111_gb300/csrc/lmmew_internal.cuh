@@ -273,6 +273,11 @@ int launch_num_to_image(lm_handle* h, const double* num, float* image, cudaStrea
 //   27 [kappa < 0]   28 rho(p*)   29-31 zero
 constexpr int kSurrogateIn = 32;
 constexpr float kSurrogateEps = 1e-8f;   // target = ln(S + eps)
+// The surrogate is evaluated only for recorded energies within this many
+// energy-resolution sigmas of the energies single scatter of the line can
+// have (backscatter energy to E_w): outside, the exact term is below
+// exp(-32) of its largest value and the surrogate's part is 0.
+constexpr float kSurrogateReachSigmas = 8.0f;
 constexpr float kElectronRestKeV = 510.99895f;
 // Inputs 8 j .. 8 j + 7 (j = 0..3) of one (event, voxel, line); g8 holds the
 // 8 rho line integrals of the voxel at this angle.  Four threads can build

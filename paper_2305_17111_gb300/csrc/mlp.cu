@@ -532,7 +532,12 @@ constexpr uint32_t kTcOffG = kTcOffW3 + 2 * kAtomBlock;    // group tiles H (X =
 constexpr uint32_t kGrpTiles = 2 * kAtomBlock;
 constexpr uint32_t kTcOffF = kTcOffG + kTcGroups * kGrpTiles;   // floats: bias [3][128], w4 [128]
 constexpr uint32_t kTcOffGF = kTcOffF + 4 * 128 * 4;            // per group: unit data
-constexpr uint32_t kGrpFloats = 32 * 2 + 32 * 8 + 128 * 2;
+// unit data per group: voxel centres, voxel line integrals, event (energy,
+// bin centre); then, for the surrogate rows, per line the number of events
+// its single scatter can reach, per-warp counts and the events' indices
+constexpr uint32_t kGrpUnitFloats = 32 * 2 + 32 * 8 + 128 * 2;
+constexpr uint32_t kGrpFloats =
+    kGrpUnitFloats + LMMEW_MAX_LINES + 4 * LMMEW_MAX_LINES + LMMEW_MAX_LINES * 128 / 4;
 constexpr uint32_t kTcOffBar = kTcOffGF + kTcGroups * kGrpFloats * 4;   // mbarriers, TMEM, abort
 constexpr size_t kTcSmem = kTcOffBar + 64 + 1024;          // + room to align the base to 1 KB
 static_assert(kTcOffW2 % 1024 == 0 && kTcOffW3 % 1024 == 0 && kTcOffG % 1024 == 0 &&
@@ -860,15 +865,22 @@ struct SurrogateRowParams {
     float h, bin_w;
     float mu_line[LMMEW_MAX_LINES];
     float e_line[LMMEW_MAX_LINES];
+    // recorded energies that single scatter of line w can reach: between its
+    // backscatter energy and E_w, widened by 8 energy-resolution sigmas
+    float reach_lo[LMMEW_MAX_LINES], reach_hi[LMMEW_MAX_LINES];
     const float* rho;
 };
 
 // The surrogate inside the row pipeline: after k_row wrote the unscattered
-// part of every row of a (128-event tile, 32-voxel tile) unit, this kernel
-// adds sum_w max(exp(net(x_w)) - eps, 0) to every (event, voxel) and writes
-// the unit's partial forward sums.  Each thread group takes every fourth
-// unit; passes of 128 samples: 4 events x 32 voxels, one line; the thread
-// that owns a sample adds its scatter part to the row in global memory.
+// part of every row of a (tile of up to 128 events, 32-voxel tile) unit,
+// this kernel adds sum_w max(exp(net(x_w)) - eps, 0) to every (event, voxel)
+// and writes the unit's partial forward sums.  Line w's term is evaluated
+// only for events whose recorded energy its single scatter can reach (the
+// backscatter energy to E_w, widened by kSurrogateReachSigmas energy-
+// resolution sigmas); elsewhere it is 0.  Each thread group takes every
+// fourth unit; passes of 128 samples: 4 reachable events x 32 voxels, one
+// line; the thread that owns a sample adds its part to the row in global
+// memory.
 __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const SurrogateRowParams P) {
     extern __shared__ unsigned char smem_raw[];
     const TcShared S = tc_shared(smem_raw);
@@ -878,6 +890,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
     float* Vxy = G.f;                     // [32] voxel centre (x, y), cm
     float* Vg8 = Vxy + 32 * 2;            // [32][8] rho line integrals
     float* Eeu = Vg8 + 32 * 8;            // [128] (recorded energy, bin centre)
+    int* Cnt = reinterpret_cast<int*>(G.f + kGrpUnitFloats);   // [W] events per line list
+    int* Wcnt = Cnt + LMMEW_MAX_LINES;                          // [W][4] per-warp counts
+    uint8_t* Act = reinterpret_cast<uint8_t*>(Wcnt + 4 * LMMEW_MAX_LINES);   // [W][128]
     const int gt = G.gt;
     uint32_t phase = 0;
     const int n_tiles = P.tile_end - P.tile_begin;
@@ -902,20 +917,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
             Eeu[2 * gt] = P.ev_e[T.begin + gt];
             Eeu[2 * gt + 1] = -half_det + (P.ev_bin[T.begin + gt] + 0.5f) * P.bin_w;
         }
+        // per line, the unit's events whose recorded energy its single
+        // scatter can reach, as a compact list (warp ballots + prefix)
+        {
+            const int lane = gt & 31, wq = gt >> 5;
+            const float eh = gt < T.count ? P.ev_e[T.begin + gt] : 0.f;
+            for (int wl = 0; wl < P.W; ++wl) {
+                const bool f = gt < T.count && eh >= P.reach_lo[wl] && eh <= P.reach_hi[wl];
+                const unsigned m = __ballot_sync(0xffffffffu, f);
+                if (lane == 0) Wcnt[wl * 4 + wq] = __popc(m);
+            }
+            group_sync(G.g);
+            for (int wl = 0; wl < P.W; ++wl) {
+                const bool f = gt < T.count && eh >= P.reach_lo[wl] && eh <= P.reach_hi[wl];
+                const unsigned m = __ballot_sync(0xffffffffu, f);
+                int off = 0;
+                for (int i = 0; i < wq; ++i) off += Wcnt[wl * 4 + i];
+                if (f) Act[wl * 128 + off + __popc(m & ((1u << lane) - 1u))] = (uint8_t)gt;
+                if (gt == 0)
+                    Cnt[wl] = Wcnt[wl * 4] + Wcnt[wl * 4 + 1] + Wcnt[wl * 4 + 2] + Wcnt[wl * 4 + 3];
+            }
+        }
         group_sync(G.g);
         const float th = 6.283185307179586f * T.a / P.A;
         float ca, sa;
         sincosf(th, &sa, &ca);
-        for (int c = 0; c < (T.count + 3) / 4 && ok; ++c) {
-            float scat = 0.f;   // scatter part of this thread's sample, summed over the lines
-            for (int wl = 0; wl < P.W && ok; ++wl) {
-                // inputs 8 j .. 8 j + 7 of sample smp (event 4c + smp / 32, voxel
-                // smp mod 32) into chunk j of row smp of X
+        // passes of 4 listed events x 32 voxels, one line at a time; the
+        // thread that owns a sample adds its scatter part to the row (passes
+        // are ordered by the group barriers inside each network evaluation)
+        for (int wl = 0; wl < P.W && ok; ++wl) {
+            const int n_act = Cnt[wl];
+            const uint8_t* act = Act + wl * 128;
+            for (int c = 0; c < (n_act + 3) / 4 && ok; ++c) {
+                // inputs 8 j .. 8 j + 7 of sample smp (listed event 4c + smp / 32,
+                // voxel smp mod 32) into chunk j of row smp of X
                 for (int k = gt; k < 128 * 4; k += kGrpThreads) {
                     const int smp = k & 127, j = k >> 7;   // j is the same across a warp
-                    const int e = c * 4 + (smp >> 5), ql = smp & 31;
+                    const int slot = c * 4 + (smp >> 5), ql = smp & 31;
                     float f8[8];
-                    if (e < T.count && ql < nq_here) {
+                    if (slot < n_act && ql < nq_here) {
+                        const int e = act[slot];
                         surrogate_features_chunk(j, Vxy[2 * ql], Vxy[2 * ql + 1], ca, sa,
                                                  Eeu[2 * e + 1], Eeu[2 * e], wl, P.e_line[wl],
                                                  P.mu_line[wl], Vg8 + ql * 8, P.rho, P.n, P.h, f8);
@@ -937,12 +978,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
                 group_sync(G.g);
                 float o = 0.f;
                 ok = tc_network(S, G, phase, b4, &o, P.status);
-                const float v = __expf(o) - kSurrogateEps;
-                scat += v > 0.f ? v : 0.f;
+                const int slot = c * 4 + (gt >> 5), ql = gt & 31;
+                if (ok && slot < n_act && ql < nq_here) {
+                    const float v = __expf(o) - kSurrogateEps;
+                    if (v > 0.f)
+                        P.rows[(size_t)(T.begin + act[slot] - P.row_base) * P.row_stride +
+                               qt * 32 + ql] += v;
+                }
             }
-            const int e = c * 4 + (gt >> 5), ql = gt & 31;
-            if (ok && e < T.count && ql < nq_here)
-                P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + qt * 32 + ql] += scat;
         }
         if (!ok) break;
         group_sync(G.g);   // the group's row updates are visible to the whole group
@@ -1046,9 +1089,18 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     P.nqt = h->mc.nqt;
     P.h = (float)h->mc.h;
     P.bin_w = (float)h->mc.bin_w;
+    const ModelConst& m = h->mc;
+    const double fwhm_to_sigma = 1.0 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    auto sigma_e = [&](double e) {
+        return m.fwhm_frac * e * std::pow(e / m.e_ref, m.expo) * fwhm_to_sigma;
+    };
     for (int w = 0; w < LMMEW_MAX_LINES; ++w) {
         P.mu_line[w] = (float)h->mu_line[w];
-        P.e_line[w] = (float)h->mc.line_e[w];
+        P.e_line[w] = (float)m.line_e[w];
+        const double ew = m.line_e[w] > 0.0 ? m.line_e[w] : 1.0;
+        const double e_back = ew / (1.0 + 2.0 * ew / kElectronRestKeV);   // Compton, 180 degrees
+        P.reach_lo[w] = (float)(e_back - kSurrogateReachSigmas * sigma_e(e_back));
+        P.reach_hi[w] = (float)(ew + kSurrogateReachSigmas * sigma_e(ew));
     }
     P.rho = h->d_rho;
     const int grid = std::min((n_units + mlp::kTcGroups - 1) / mlp::kTcGroups, h->sm_count);

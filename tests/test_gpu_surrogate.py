@@ -394,7 +394,12 @@ def test_surrogate_rows_match_primary_plus_oracle_network():
         feats = np.stack([_features(sc, ph, orc, a, b, e, q, w) for w in range(W)
                           for q in range(orc.nq)])
         out = omlp.forward(_rounded(p), bf16(feats.astype(np.float32))).reshape(W, orc.nq)
-        scat = np.maximum(np.exp(out) - omlp.EPS_TARGET, 0.0).sum(axis=0)
+        # line w's part is zero where its single scatter cannot reach e
+        reach = np.array([lo <= e <= hi for lo, hi in
+                          (omlp.scatter_reach(float(np.float32(sc.line_keV[w])), sc.fwhm_frac,
+                                              sc.e_ref_keV, sc.fwhm_exponent)
+                           for w in range(W))])
+        scat = (np.maximum(np.exp(out) - omlp.EPS_TARGET, 0.0) * reach[:, None]).sum(axis=0)
         want = float(lam_q @ (prim + scat))
         # BF16 network: outputs within ~1e-2 in log space, i.e. ~1e-2 of the
         # scatter part (3e-2 allowed), plus the primary part's 1e-5

@@ -234,3 +234,33 @@ def test_features_scatter_point_geometry():
         assert f[28] == (rho[gy, gx] if inside else 0.0)
         assert f[27] == (1.0 if e_hat > e0 else 0.0)
     assert checked > 50
+
+
+def test_scatter_reach_bounds_the_oracles_single_scatter():
+    """Outside scatter_reach(line) the oracle's exact single-scatter sum of
+    that line is negligible next to its value inside: the surrogate may set it
+    to zero there.  The range itself: backscatter (Compton at 180 degrees) to
+    the line energy, widened by 8 sigmas."""
+    import oracle
+    from synthetic import preset
+    sc = preset("small_16")
+    ph = sc.make_phantom()
+    orc = oracle.Model.from_scenario(sc, ph.rho)
+    rng = np.random.default_rng(3)
+    checked = 0
+    for w, e0 in enumerate(sc.line_keV):
+        lo, hi = mlp.scatter_reach(e0, sc.fwhm_frac, sc.e_ref_keV, sc.fwhm_exponent)
+        e_back = oracle.compton_energy(e0, -1.0)
+        assert lo < e_back < e0 < hi
+        for _ in range(3):
+            a, b = int(rng.integers(sc.n_angles)), int(rng.integers(sc.n_bins))
+            inside = max(float(orc.scatter_line_row(a, b, e, w).sum())
+                         for e in np.linspace(e_back, e0, 9))
+            if inside <= 0.0:
+                continue
+            for e in (lo - 0.5, hi + 0.5):
+                if 1.0 < e < 2000.0:
+                    out = float(orc.scatter_line_row(a, b, e, w).sum())
+                    assert out <= 1e-9 * inside, (w, a, b, e, out, inside)
+                    checked += 1
+    assert checked >= 8

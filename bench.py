@@ -452,18 +452,7 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     model.set_scatter_model("exact")
     ex = res["exact"]
     roi_ex = roi_sums(ex["img"], ph.lesion_masks)
-    # samples the network evaluates: (event, voxel, line) with the recorded
-    # energy inside the line's single-scatter reach (backscatter energy to
-    # E_w, widened by 8 energy-resolution sigmas; the library's rule)
-    def sigma_e(e):
-        return sc.fwhm_frac * e * (e / sc.e_ref_keV) ** sc.fwhm_exponent / (2 * np.sqrt(2 * np.log(2)))
-    e_hat = np.asarray(ev.energy, dtype=np.float64)
-    reachable = 0
-    for e_w in sc.line_keV:
-        e_back = e_w / (1 + 2 * e_w / 510.99895)
-        reachable += int(np.count_nonzero((e_hat >= e_back - 8 * sigma_e(e_back))
-                                          & (e_hat <= e_w + 8 * sigma_e(e_w))))
-    samples_per_iter = reachable * model.nq
+    samples_per_iter = surrogate_samples_in_reach(sc, ev.energy, model.nq)
     dense_samples_per_iter = len(ev) * model.nq * len(sc.line_keV)
     flop_per_sample = 2 * (32 * 128 + 2 * 128 * 128) + 2 * 128
     out = {"workload": f"{sc.name}: {sc.n}x{sc.n}, {sc.n_angles} angles, {sc.n_bins} bins, "
@@ -801,6 +790,24 @@ def run_gpu(args, rank, local_rank, world):
     return 0
 
 
+def surrogate_samples_in_reach(sc, energies, nq):
+    """(event, voxel, line) samples the surrogate evaluates: the recorded
+    energy inside the line's single-scatter reach (backscatter energy to E_w,
+    widened by 8 energy-resolution sigmas, the library's rule), times nq."""
+    import numpy as np
+
+    def sigma_e(e):
+        return (sc.fwhm_frac * e * (e / sc.e_ref_keV) ** sc.fwhm_exponent
+                / (2 * np.sqrt(2 * np.log(2))))
+    e_hat = np.asarray(energies, dtype=np.float64)
+    reachable = 0
+    for e_w in sc.line_keV:
+        e_back = e_w / (1 + 2 * e_w / 510.99895)
+        reachable += int(np.count_nonzero((e_hat >= e_back - 8 * sigma_e(e_back))
+                                          & (e_hat <= e_w + 8 * sigma_e(e_w))))
+    return reachable * nq
+
+
 def run_surrogate_rows_case(n_events=20_000, repeats=3):
     """Small case for profiling the surrogate row kernel: the 64 x 64 object,
     20 000 MC events, lm_forward with the surrogate scatter model (untrained
@@ -829,9 +836,10 @@ def run_surrogate_rows_case(n_events=20_000, repeats=3):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     model.set_scatter_model("exact")
-    samples = len(ev) * model.nq * len(sc.line_keV)
+    samples = surrogate_samples_in_reach(sc, ev.energy, model.nq)
     ms = min(times)
     print(json.dumps({"case": "surrogate_rows", "events": len(ev), "samples": samples,
+                      "samples_dense": len(ev) * model.nq * len(sc.line_keV),
                       "ms": ms, "samples_per_s": samples / ms * 1e3,
                       "tflops": samples * (2 * (32 * 128 + 2 * 128 * 128) + 256) / ms / 1e9}),
           flush=True)

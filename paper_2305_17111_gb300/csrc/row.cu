@@ -5,7 +5,8 @@
 //   a_j[q] = sum_w alpha_w [ s_prim(a,w,q) C_q(b) g(E_hat; E_w)
 //                            + sum_p s(a,w,q,p) C_p(b) g(E_hat; E'(a,w,q,p)) ]
 //
-// Work unit = (tile of <= 128 events of one angle, tile of 32 voxels); the
+// Work unit = (tile of up to 32 EPL events of one angle, tile of 32 voxels),
+// EPL = 1, 2 or 4 events per lane (the tile size is autotuned); the
 // persistent CTAs take units from a counter as they finish the last one.  The
 // CTA streams the angle's scatter-path tables for its 32 voxels and the
 // collimator rows of the tile's bins, 32 scatter points per stage (points in
@@ -14,8 +15,8 @@
 // run's first and last chunk only its 4-point groups inside the run), from
 // global memory into shared memory with bulk asynchronous copies (TMA engine,
 // cp.async.bulk + mbarrier, double buffered).  Each of the 8 warps owns 4
-// voxels; each lane owns 4 events, so a table entry read from shared memory
-// is a broadcast that feeds 4 events, and the collimator value of an
+// voxels; each lane owns EPL events, so a table entry read from shared memory
+// is a broadcast that feeds EPL events, and the collimator value of an
 // (event, point) pair feeds every voxel and line.  Per scatter term, in the
 // square-root form of the energy Gaussian:
 //   d = sr E_hat + m;  arg = d d + nlh;  term = ex2(-arg)   (FMA, FMA, MUFU)
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             }
         }
 
-        // transpose through shared memory: tile [128 events][32 voxels]
+        // transpose through shared memory: tile [32 EPL events][32 voxels]
         float* tt = reinterpret_cast<float*>(smem);
 #pragma unroll
         for (int k = 0; k < EPL; ++k)

@@ -46,11 +46,14 @@ __device__ __forceinline__ double gauss_mass(double lo, double hi, double mean, 
     return 0.5 * (erf(b) - erf(a));
 }
 
-__device__ __forceinline__ double window_mass(const ModelConst& m, double e) {
-    const double s = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e);
+// Mass of the energy response to E (sigma s) inside the windows.
+__device__ __forceinline__ double window_mass(const ModelConst& m, double e, double s) {
     double t = 0.0;
     for (int k = 0; k < m.n_win; ++k) t += gauss_mass(m.win_lo[k], m.win_hi[k], e, s);
     return t;
+}
+__device__ __forceinline__ double window_mass(const ModelConst& m, double e) {
+    return window_mass(m, e, sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e));
 }
 
 // Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E.
@@ -330,12 +333,28 @@ __global__ void k_primary(ModelConst m, const double* cs_a, const int* q_pix, co
 // (sr and m rounded once from FP64, so sr E_hat + m in one FMA carries the
 // same error as E_hat - E' with E' rounded), and adds sum_w alpha_w sum_p s(P) Prob(detector) Prob(window | E') to the
 // per-angle sensitivity.
+// Collimator mass on the whole detector of every scatter point at every
+// angle (it does not depend on the emission voxel): on_det[a][p].
+__global__ void k_on_detector(ModelConst m, const double* cs_a, const int* p_cell, double* on_det) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.y;
+    if (p >= m.np) return;
+    const double c = cs_a[2 * a], s = cs_a[2 * a + 1];
+    const int cell = p_cell[p];
+    const double xp = ((cell % m.S) + 0.5) * m.f, yp = ((cell / m.S) + 0.5) * m.f;
+    const double xpc = (xp - 0.5 * m.n) * m.h, ypc = (yp - 0.5 * m.n) * m.h;
+    const double half_det = 0.5 * m.B * m.bin_w;
+    on_det[(size_t)a * m.np + p] =
+        gauss_mass(-half_det, half_det, -xpc * s + ypc * c,
+                   sigma_coll(m, m.r_det - (xpc * c + ypc * s)));
+}
+
 __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_a,
                                                  const int* q_pix, const int* p_cell,
                                                  const double* p_rho, const double* g_qp,
                                                  const double* d_qp, const double* g_p,
                                                  const double* mu_line, const int* inv,
-                                                 float* tab, double* sens_a) {
+                                                 const double* on_det, float* tab, double* sens_a) {
     const int a = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.x * 8 + warp;
@@ -346,7 +365,6 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
     const int own_cell = (qy / m.f) * m.S + (qx / m.f);
     const double xq = qx + 0.5, yq = qy + 0.5;
     const int qt = q / kQT, ql = q % kQT;
-    const double half_det = 0.5 * m.B * m.bin_w;
     double sens = 0.0;
     for (int pc = 0; pc < m.npc; ++pc) {
         const int r = pc * kPC + lane;   // slot in this angle's point order
@@ -374,10 +392,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
         const double d = d_qp[k];
         const double ux = (xp - xq) * m.h / d, uy = (yp - yq) * m.h / d;
         const double cos_t = ux * c + uy * s;
-        const double xpc = (xp - 0.5 * m.n) * m.h, ypc = (yp - 0.5 * m.n) * m.h;
-        const double u = -xpc * s + ypc * c;
-        const double on_det = gauss_mass(-half_det, half_det, u,
-                                         sigma_coll(m, m.r_det - (xpc * c + ypc * s)));
+        const double od = on_det[(size_t)a * m.np + p];
         const double gqp = g_qp[k], gp = g_p[(size_t)a * m.np + p];
         const double inter = p_rho[p] * m.cell_area / (2.0 * kPi * d);
         for (int w = 0; w < m.W; ++w) {
@@ -392,7 +407,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-log2(wgt)) : kPosHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
             base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
-            if (path > 0.0) sens += m.alpha[w] * path * on_det * window_mass(m, e1);
+            if (path > 0.0) sens += m.alpha[w] * path * od * window_mass(m, e1, sg);
         }
     }
     for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);
@@ -640,11 +655,16 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
             return set_error(LMMEW_ERR_OOM, "cannot allocate scatter tables (" +
                                                 std::to_string(h->tab_bytes >> 20) + " MiB)");
         LMMEW_CUDA(cudaMemset(h->d_tab, 0, h->tab_bytes));
+        DevBuf d_on_det;
+        LMMEW_CUDA(cudaMalloc(&d_on_det.p, sizeof(double) * (size_t)m.A * m.np));
+        k_on_detector<<<dim3((m.np + 127) / 128, m.A), 128>>>(m, dcs, (const int*)d_p_cell.p,
+                                                               (double*)d_on_det.p);
         dim3 g((m.nq + 7) / 8, m.A);
         k_scatter<<<g, 256>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
                               (const double*)d_gqp.p, (const double*)d_dqp.p,
-                              (const double*)d_gp.p, mu_line, inv, h->d_tab, h->d_sens_a);
-        ++h->launches;
+                              (const double*)d_gp.p, mu_line, inv, (const double*)d_on_det.p,
+                              h->d_tab, h->d_sens_a);
+        h->launches += 2;
         LMMEW_CUDA(cudaGetLastError());
     }
     LMMEW_CUDA(cudaMalloc(&h->d_status, sizeof(int)));

@@ -113,3 +113,34 @@ def test_each_workload_class_is_tuned_once():
             assert t == seen[name], name
         seen[name] = t
     gpu.close()
+
+
+@pytest.mark.parametrize("lines,yields", [
+    ((140.0,), (1.0,)),
+    ((82.0, 154.0), (0.7, 0.3)),
+    ((82.0, 154.0, 270.0, 300.0), (0.4, 0.2, 0.2, 0.2)),
+    ((82.0, 120.0, 154.0, 200.0, 270.0), (0.3, 0.2, 0.2, 0.1, 0.2)),
+])
+def test_every_line_count_and_tile_size_against_the_oracle(lines, yields):
+    """The small-tile kernels exist for 1 to 4 lines; 5 lines run the
+    128-event kernel on any tile.  Every combination matches the FP64 oracle
+    and the 128-event result bit for bit."""
+    sc = preset("small_16").with_(line_keV=lines, yields=yields)
+    ph = sc.make_phantom()
+    ev = simulate(sc, n_events=900, seed=31)
+    lam = (np.random.default_rng(32).uniform(0.2, 3.0, ph.rho.size)
+           * (ph.rho.reshape(-1) > 0)).astype(np.float32)
+    gpu = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    x = torch.from_numpy(lam).cuda()
+    fwd = {}
+    for ts in SIZES:
+        gpu.set_tile_events(ts)
+        fwd[ts] = gpu.forward(dev, x).cpu()
+    for ts in SIZES[1:]:
+        assert torch.equal(fwd[ts], fwd[128]), f"{len(lines)} lines, {ts}-event tiles"
+    idx = np.arange(0, len(ev), 11)
+    ref = oracle.Model.from_scenario(sc, ph.rho).forward(ev.subset(idx), lam.astype(np.float64))
+    rel = np.abs(fwd[32].numpy()[idx].astype(np.float64) - ref) / ref
+    assert float(rel.max()) < FWD_RTOL, f"{len(lines)} lines: max rel {rel.max():.3e}"
+    gpu.close()

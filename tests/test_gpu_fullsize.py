@@ -97,3 +97,41 @@ def test_osem_full_size_invariants_64():
     gpu.osem(dev, img3, 1, 3, loglik=ll3)
     v = ll3.cpu().numpy()
     assert v[1] > v[0] and v[2] > v[1]
+
+
+def test_batching_workload_full_size():
+    """The batching workload in the launch configuration bench.py times:
+    256 realisations of the 64 x 64 object with U[50k, 500k] events each,
+    resampled from one MC pool, one OSEM iteration of 8 subsets in one
+    lm_osem_batch call (71 M events, several row blocks per subset).  Sampled
+    realisations equal their own lm_osem runs to FP32 rounding (only the
+    back-projection chunk boundaries at row-block edges differ), and the
+    first one's forward projections match the FP64 oracle."""
+    sc = preset("lmmew_64")
+    ph = sc.make_phantom()
+    pool = simulate_cached(sc)
+    rng = np.random.default_rng(3)
+    sizes = rng.integers(50_000, 500_001, size=256)
+    evs = [pool.subset(rng.integers(0, len(pool), size=int(k))) for k in sizes]
+    devs = [lm.DeviceEvents.from_list(e) for e in evs]
+    gpu = lm.Model.from_scenario(sc, ph.rho)
+    lam0 = (ph.rho.reshape(-1) > 0).astype(np.float32)
+    imgs = torch.from_numpy(np.stack([lam0] * len(devs))).cuda()
+    gpu.osem_batch(devs, imgs, sc.n_subsets, 1)
+    torch.cuda.synchronize()
+    for i in (0, 97, 255):
+        one = torch.from_numpy(lam0.copy()).cuda()
+        gpu.osem(devs[i], one, sc.n_subsets, 1)
+        a = imgs[i].double().cpu().numpy()
+        b = one.double().cpu().numpy()
+        assert np.all(np.isfinite(a)) and np.all(a >= 0)
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6, f"realisation {i}"
+    # forward projections of realisation 0 at its reconstructed image
+    img0 = imgs[0].contiguous()
+    y = gpu.forward(devs[0], img0).cpu().numpy()
+    idx = sample_indices(evs[0], sc.n_angles, 4, seed=5)
+    orc = oracle.Model.from_scenario(sc, ph.rho)
+    ref = orc.forward(evs[0].subset(idx), img0.cpu().numpy().astype(np.float64))
+    rel = np.abs(y[idx].astype(np.float64) - ref) / ref
+    assert float(rel.max()) < FWD_RTOL, f"max rel {rel.max():.3e}"
+    gpu.close()

@@ -4,11 +4,11 @@
 // single-scatter part of the system-matrix element for line w (Eq. s_p with
 // n = 1 summed over the scatter points).  Two families of kernels, all
 // written here, BF16 operands with FP32 accumulation:
-//  * training (forward with stored pre-activations, backward, Adam): the
-//    matrix products use mma.sync m16n8k16 fragments loaded with ldmatrix;
-//    a CTA owns 128 samples and each of its 8 warps 16 rows;
-//  * inference (k_tc_forward and the row kernel k_surrogate_rows): tcgen05
-//    MMAs from swizzled shared memory into tensor memory, described below.
+//  * inference (k_tc_forward and the row kernel k_surrogate_rows) and the
+//    training forward (k_tc_forward with stored pre-activations): tcgen05
+//    MMAs from swizzled shared memory into tensor memory, described below;
+//  * training backward (k_tc_back_layer per hidden layer, tcgen05; the
+//    output layer k_back_out and the Adam update on the CUDA cores).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -24,8 +24,6 @@ namespace lmmew {
 namespace mlp {
 
 constexpr int kIn = 32, kHid = 128;
-constexpr int kLdX = kIn + 8;    // padded rows keep ldmatrix conflict-free
-constexpr int kLdH = kHid + 8;
 constexpr int kTile = 128;       // samples per CTA
 constexpr int kThreads = 256;
 // parameter vector (FP32 masters): W1[128][32] b1 W2[128][128] b2 W3 b3 w4[128] b4
@@ -36,31 +34,10 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
 
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void ldsm4(uint32_t* r, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(saddr(p)));
-}
-__device__ __forceinline__ void ldsm4t(uint32_t* r, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(saddr(p)));
-}
-__device__ __forceinline__ void mma(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // GELU, tanh form: 0.5 z (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3),
 // evaluated as u = z (c + c k z^2), h = hz tanh(u) + hz with hz = z / 2.  The
-// scalar and the packed (f32x2) forms perform the same IEEE operations in the
-// same order, so every kernel produces the same activations.
+// packed doubled form below performs the same IEEE operations scaled by the
+// exact factor 2, so every kernel produces the same activations.
 constexpr float kGeluC = 0.7978845608028654f;
 constexpr float kGeluCK = 0.7978845608028654f * 0.044715f;
 __device__ __forceinline__ float tanh_fast(float x) {
@@ -82,89 +59,11 @@ __device__ __forceinline__ f32x2 gelu2_doubled(f32x2 z) {
     upk(u, u0, u1);
     return fma2(z, pk(tanh_fast(u0), tanh_fast(u1)), z);
 }
-__device__ __forceinline__ f32x2 gelu2(f32x2 z) {
-    const f32x2 u = mul2(z, fma2(mul2(z, z), pk(kGeluCK, kGeluCK), pk(kGeluC, kGeluC)));
-    float u0, u1;
-    upk(u, u0, u1);
-    const f32x2 hz = mul2(z, pk(0.5f, 0.5f));
-    return fma2(hz, pk(tanh_fast(u0), tanh_fast(u1)), hz);
-}
 __device__ __forceinline__ float gelu_grad(float z) {
     const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
     const float t = tanh_fast(u);
     return 0.5f * (1.f + t) +
            0.5f * z * (1.f - t * t) * 0.7978845608028654f * (1.f + 3.f * 0.044715f * z * z);
-}
-
-// acc[16 rows m0.. of this warp][N] += A[m][k] * W[n][k]   (A, W row-major in smem)
-template <int K, int N>
-__device__ __forceinline__ void gemm_nt(float (*acc)[4], const bf16* A, int lda, int m0,
-                                        const bf16* W, int ldw, int lane) {
-#pragma unroll
-    for (int kk = 0; kk < K; kk += 16) {
-        uint32_t a[4];
-        ldsm4(a, A + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * lda + kk + (lane >> 4) * 8);
-#pragma unroll
-        for (int n0 = 0; n0 < N; n0 += 16) {
-            uint32_t b[4];
-            ldsm4(b, W + (n0 + (lane & 7) + (lane >> 4) * 8) * ldw + kk + ((lane >> 3) & 1) * 8);
-            mma(acc[n0 / 8], a, b[0], b[1]);
-            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
-        }
-    }
-}
-
-// acc[16 rows][N] += A[m][k] * Bm[k][n]   (Bm row-major [K][N])
-template <int K, int N>
-__device__ __forceinline__ void gemm_nn(float (*acc)[4], const bf16* A, int lda, int m0,
-                                        const bf16* Bm, int ldb, int lane) {
-#pragma unroll
-    for (int kk = 0; kk < K; kk += 16) {
-        uint32_t a[4];
-        ldsm4(a, A + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * lda + kk + (lane >> 4) * 8);
-#pragma unroll
-        for (int n0 = 0; n0 < N; n0 += 16) {
-            uint32_t b[4];
-            ldsm4t(b, Bm + (kk + (lane & 7) + ((lane >> 3) & 1) * 8) * ldb + n0 + (lane >> 4) * 8);
-            mma(acc[n0 / 8], a, b[0], b[1]);
-            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
-        }
-    }
-}
-
-// acc[16 rows i0..][N] += sum_m P[m][i] * Q[m][j]   (P, Q row-major [M][.]), M = 128
-template <int N>
-__device__ __forceinline__ void gemm_tn(float (*acc)[4], const bf16* P, int ldp, int i0,
-                                        const bf16* Q, int ldq, int lane) {
-#pragma unroll 2
-    for (int m0 = 0; m0 < kTile; m0 += 16) {
-        uint32_t a[4];
-        ldsm4t(a, P + (m0 + (lane & 7) + (lane >> 4) * 8) * ldp + i0 + ((lane >> 3) & 1) * 8);
-#pragma unroll
-        for (int n0 = 0; n0 < N; n0 += 16) {
-            uint32_t b[4];
-            ldsm4t(b, Q + (m0 + (lane & 7) + ((lane >> 3) & 1) * 8) * ldq + n0 + (lane >> 4) * 8);
-            mma(acc[n0 / 8], a, b[0], b[1]);
-            mma(acc[n0 / 8 + 1], a, b[2], b[3]);
-        }
-    }
-}
-
-template <int N>
-__device__ __forceinline__ void zero(float (*acc)[4]) {
-#pragma unroll
-    for (int i = 0; i < N / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-}
-
-__device__ __forceinline__ void copy_rows(bf16* dst, int ldd, const bf16* src, int lds, int rows,
-                                          int cols) {
-    // 16-byte chunks
-    const int per_row = cols / 8;
-    for (int i = threadIdx.x; i < rows * per_row; i += blockDim.x) {
-        const int r = i / per_row, c = (i % per_row) * 8;
-        *reinterpret_cast<uint4*>(dst + r * ldd + c) =
-            *reinterpret_cast<const uint4*>(src + (size_t)r * lds + c);
-    }
 }
 
 struct Weights {
@@ -173,89 +72,6 @@ struct Weights {
     const bf16* W3;
     const float* p;    // FP32 parameters (biases, w4, b4)
 };
-
-constexpr size_t kFwdSmem = sizeof(bf16) * (kTile * kLdX + kHid * kLdX + 2 * kHid * kLdH + kTile * kLdH);
-
-// Forward for n samples; out[i] = network output.  If z_out is set (training),
-// the pre-activations of the three hidden layers are stored, BF16 [3][n][128].
-__global__ void __launch_bounds__(kThreads) k_forward(Weights w, const bf16* x, int64_t n,
-                                                      float* out, bf16* z_out) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    bf16* Xs = reinterpret_cast<bf16*>(sm);
-    bf16* W1s = Xs + kTile * kLdX;
-    bf16* W2s = W1s + kHid * kLdX;
-    bf16* W3s = W2s + kHid * kLdH;
-    bf16* Hs = W3s + kHid * kLdH;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    const int rows = (n - base) < kTile ? (int)(n - base) : kTile;
-    copy_rows(W1s, kLdX, w.W1, kIn, kHid, kIn);
-    copy_rows(W2s, kLdH, w.W2, kHid, kHid, kHid);
-    copy_rows(W3s, kLdH, w.W3, kHid, kHid, kHid);
-    for (int i = threadIdx.x; i < kTile * (kIn / 8); i += kThreads) {
-        const int r = i / (kIn / 8), c = (i % (kIn / 8)) * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (r < rows) v = *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + c);
-        *reinterpret_cast<uint4*>(Xs + r * kLdX + c) = v;
-    }
-    __syncthreads();
-    const int m0 = warp * 16;
-    const int g = lane >> 2, cpair = (lane & 3) * 2;
-    float acc[16][4];
-    // hidden layers
-    for (int layer = 0; layer < 3; ++layer) {
-        zero<kHid>(acc);
-        if (layer == 0) gemm_nt<kIn, kHid>(acc, Xs, kLdX, m0, W1s, kLdX, lane);
-        else if (layer == 1) gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W2s, kLdH, lane);
-        else gemm_nt<kHid, kHid>(acc, Hs, kLdH, m0, W3s, kLdH, lane);
-        const float* bias = w.p + (layer == 0 ? kOffB1 : layer == 1 ? kOffB2 : kOffB3);
-        if (layer < 2) __syncwarp();
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const int col = nt * 8 + cpair;
-            const f32x2 b2 = pk(bias[col], bias[col + 1]);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = m0 + g + h * 8;
-                const f32x2 z = add2(pk(acc[nt][2 * h], acc[nt][2 * h + 1]), b2);
-                float z0, z1;
-                upk(z, z0, z1);
-                if (z_out && row < rows) {
-                    bf16* zp = z_out + ((size_t)layer * n + base + row) * kHid + col;
-                    *reinterpret_cast<__nv_bfloat162*>(zp) = __floats2bfloat162_rn(z0, z1);
-                }
-                float h0, h1;
-                upk(gelu2(z), h0, h1);
-                if (layer < 2) {
-                    *reinterpret_cast<__nv_bfloat162*>(Hs + row * kLdH + col) =
-                        __floats2bfloat162_rn(h0, h1);
-                } else {
-                    acc[nt][2 * h] = h0;
-                    acc[nt][2 * h + 1] = h1;
-                }
-            }
-        }
-        __syncwarp();
-    }
-    // output layer: dot with w4
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-        const int col = nt * 8 + cpair;
-        const float w0 = w.p[kOffW4 + col], w1 = w.p[kOffW4 + col + 1];
-        s0 += acc[nt][0] * w0 + acc[nt][1] * w1;
-        s1 += acc[nt][2] * w0 + acc[nt][3] * w1;
-    }
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    if ((lane & 3) == 0) {
-        const float b4 = w.p[kOffB4];
-        if (m0 + g < rows) out[base + m0 + g] = s0 + b4;
-        if (m0 + g + 8 < rows) out[base + m0 + g + 8] = s1 + b4;
-    }
-}
 
 // Output layer backward.  loss = (1/n) sum_i v_i (out_i - t_i)^2 with sample
 // weights v_i (1 when weight is null).  dZ3 = dout w4 gelu'(Z3); per-CTA
@@ -277,107 +93,44 @@ __global__ void __launch_bounds__(kThreads) k_back_out(const float* p, const flo
         dout[threadIdx.x] = d;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kTile * kHid; i += kThreads) {
-        const int r = i / kHid, c = i % kHid;
-        float v = 0.f;
-        if (r < rows) {
-            const float z = __bfloat162float(z3[(size_t)(base + r) * kHid + c]);
-            v = dout[r] * p[kOffW4 + c] * gelu_grad(z);
+    // each thread keeps one column c; its partial of dL/dw4[c] over the rows
+    // it visits is combined with the other thread of that column at the end
+    __shared__ float colsum[kThreads];
+    float s = 0.f;
+    const int c = threadIdx.x % kHid;
+    const float w4c = p[kOffW4 + c];
+    constexpr int kRowsPerThread = kTile * kHid / kThreads;   // rows r0 + 2 k
+    constexpr int kBatch = 8;                                  // loads in flight together
+    for (int k0 = 0; k0 < kRowsPerThread; k0 += kBatch) {
+        float z[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int r = (threadIdx.x + (k0 + k) * kThreads) / kHid;
+            z[k] = r < rows ? __bfloat162float(z3[(size_t)(base + r) * kHid + c]) : 0.f;
         }
-        dz3[(size_t)(base + r) * kHid + c] = __float2bfloat16_rn(v);
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int r = (threadIdx.x + (k0 + k) * kThreads) / kHid;
+            float v = 0.f;
+            if (r < rows) {
+                v = dout[r] * w4c * gelu_grad(z[k]);
+                s += dout[r] * gelu(z[k]);
+            }
+            dz3[(size_t)(base + r) * kHid + c] = __float2bfloat16_rn(v);
+        }
     }
+    colsum[threadIdx.x] = s;
+    __syncthreads();
+    static_assert(kThreads % kHid == 0, "whole columns per thread");
     if (threadIdx.x < kHid) {
-        const int c = threadIdx.x;
-        float s = 0.f;
-        for (int r = 0; r < rows; ++r)
-            s += dout[r] * gelu(__bfloat162float(z3[(size_t)(base + r) * kHid + c]));
-        part[(size_t)blockIdx.x * (kHid + 1) + c] = s;
+        float tot = 0.f;
+        for (int k = threadIdx.x; k < kThreads; k += kHid) tot += colsum[k];
+        part[(size_t)blockIdx.x * (kHid + 1) + threadIdx.x] = tot;
     }
     if (threadIdx.x == kHid) {
-        float s = 0.f;
-        for (int r = 0; r < rows; ++r) s += dout[r];
-        part[(size_t)blockIdx.x * (kHid + 1) + kHid] = s;
-    }
-}
-
-constexpr size_t back_smem(int K) {
-    return sizeof(bf16) * (kTile * kLdH + kTile * (K + 8) + kHid * (K + 8));
-}
-
-// Backward through one hidden layer l with input width K (32 for l = 1).
-//   gW[i][j] = sum_m dZ[m][i] H[m][j],  gb[i] = sum_m dZ[m][i]       (per CTA)
-//   dZprev[m][j] = (sum_i dZ[m][i] W[i][j]) gelu'(Zprev[m][j])        (l > 1)
-// H = gelu(Zprev) for l > 1, the input x for l = 1.
-template <int K>
-__global__ void __launch_bounds__(kThreads) k_back_layer(const bf16* dz, const bf16* zprev,
-                                                         const bf16* x, const bf16* W, int64_t n,
-                                                         float* part_w /* [cta][128][K] */,
-                                                         float* part_b /* [cta][128] */,
-                                                         bf16* dzprev) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    constexpr int ldk = K + 8;
-    bf16* Ds = reinterpret_cast<bf16*>(sm);        // [128][kLdH] dZ
-    bf16* Hs = Ds + kTile * kLdH;                  // [128][ldk]  layer input
-    bf16* Ws = Hs + kTile * ldk;                   // [128][ldk]  W (out x in)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    const int rows = (n - base) < kTile ? (int)(n - base) : kTile;
-    for (int i = threadIdx.x; i < kTile * (kHid / 8); i += kThreads) {
-        const int r = i / (kHid / 8), c = (i % (kHid / 8)) * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (r < rows) v = *reinterpret_cast<const uint4*>(dz + (size_t)(base + r) * kHid + c);
-        *reinterpret_cast<uint4*>(Ds + r * kLdH + c) = v;
-    }
-    for (int i = threadIdx.x; i < kTile * K; i += kThreads) {
-        const int r = i / K, c = i % K;
-        float h = 0.f;
-        if (r < rows) {
-            if (zprev) h = gelu(__bfloat162float(zprev[(size_t)(base + r) * kHid + c]));
-            else h = __bfloat162float(x[(size_t)(base + r) * kIn + c]);
-        }
-        Hs[r * ldk + c] = __float2bfloat16_rn(h);
-    }
-    copy_rows(Ws, ldk, W, K, kHid, K);
-    __syncthreads();
-    const int i0 = warp * 16;
-    const int g = lane >> 2, cpair = (lane & 3) * 2;
-    {
-        float acc[K / 8][4];
-        zero<K>(acc);
-        gemm_tn<K>(acc, Ds, kLdH, i0, Hs, ldk, lane);
-        float* pw = part_w + (size_t)blockIdx.x * kHid * K;
-#pragma unroll
-        for (int nt = 0; nt < K / 8; ++nt) {
-            const int col = nt * 8 + cpair;
-            pw[(size_t)(i0 + g) * K + col] = acc[nt][0];
-            pw[(size_t)(i0 + g) * K + col + 1] = acc[nt][1];
-            pw[(size_t)(i0 + g + 8) * K + col] = acc[nt][2];
-            pw[(size_t)(i0 + g + 8) * K + col + 1] = acc[nt][3];
-        }
-    }
-    if (threadIdx.x < kHid) {
-        float s = 0.f;
-        for (int r = 0; r < rows; ++r) s += __bfloat162float(Ds[r * kLdH + threadIdx.x]);
-        part_b[(size_t)blockIdx.x * kHid + threadIdx.x] = s;
-    }
-    if (dzprev) {
-        float acc[16][4];
-        zero<kHid>(acc);
-        gemm_nn<kHid, kHid>(acc, Ds, kLdH, i0, Ws, ldk, lane);
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const int col = nt * 8 + cpair;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = i0 + g + h * 8;
-                if (row < rows) {
-                    const size_t o = (size_t)(base + row) * kHid + col;
-                    const float d0 = acc[nt][2 * h] * gelu_grad(__bfloat162float(zprev[o]));
-                    const float d1 = acc[nt][2 * h + 1] * gelu_grad(__bfloat162float(zprev[o + 1]));
-                    *reinterpret_cast<__nv_bfloat162*>(dzprev + o) = __floats2bfloat162_rn(d0, d1);
-                }
-            }
-        }
+        float sb = 0.f;
+        for (int r = 0; r < rows; ++r) sb += dout[r];
+        part[(size_t)blockIdx.x * (kHid + 1) + kHid] = sb;
     }
 }
 
@@ -737,9 +490,13 @@ __device__ __forceinline__ void tc_input_constants(const TcShared& S, const TcGr
 // The network on the group's 128 samples whose inputs sit in X (written,
 // fenced and followed by a group barrier).  Returns in every thread the output
 // of sample (group thread index); false if an MMA wait ran out (the status
-// word is set and the caller stops).
+// word is set and the caller stops).  With kStoreZ (training) the thread also
+// stores its sample's pre-activations of the three hidden layers, BF16, at
+// z_row + layer * z_stride (z_row null: a padding sample, nothing stored).
+template <bool kStoreZ>
 __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase, float b4,
-                           float* out_row, int* status) {
+                           float* out_row, int* status, bf16* z_row = nullptr,
+                           size_t z_stride = 0) {
     const int lq = G.gt >> 5;
     const int row = G.gt;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
@@ -780,6 +537,15 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                         z0 = add2(z0, pk(b.x, b.y));
                         z1 = add2(z1, pk(b.z, b.w));
                     }
+                    if (kStoreZ && z_row) {
+                        float a0, a1, a2, a3;
+                        upk(z0, a0, a1);
+                        upk(z1, a2, a3);
+                        __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
+                            z_row + layer * z_stride + cb + i);
+                        zp[0] = __floats2bfloat162_rn(a0, a1);
+                        zp[1] = __floats2bfloat162_rn(a2, a3);
+                    }
                     float h0, h1, h2, h3;
                     upk(gelu2_doubled(z0), h0, h1);
                     upk(gelu2_doubled(z1), h2, h3);
@@ -797,9 +563,20 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
 #pragma unroll
                 for (int i = 0; i < 32; i += 4) {
                     const float4 b = bias4[i >> 2], ww = w44[i >> 2];
+                    const f32x2 z0 = add2(pk(v[i], v[i + 1]), pk(b.x, b.y));
+                    const f32x2 z1 = add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w));
+                    if (kStoreZ && z_row) {
+                        float a0, a1, a2, a3;
+                        upk(z0, a0, a1);
+                        upk(z1, a2, a3);
+                        __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
+                            z_row + layer * z_stride + cb + i);
+                        zp[0] = __floats2bfloat162_rn(a0, a1);
+                        zp[1] = __floats2bfloat162_rn(a2, a3);
+                    }
                     float h0, h1, h2, h3;
-                    upk(gelu2_doubled(add2(pk(v[i], v[i + 1]), pk(b.x, b.y))), h0, h1);
-                    upk(gelu2_doubled(add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w))), h2, h3);
+                    upk(gelu2_doubled(z0), h0, h1);
+                    upk(gelu2_doubled(z1), h2, h3);
                     sacc = fmaf(h0, ww.x, sacc);
                     sacc = fmaf(h1, ww.y, sacc);
                     sacc = fmaf(h2, ww.z, sacc);
@@ -815,9 +592,12 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
     return true;
 }
 
-// Network outputs for n BF16 input rows.
+// Network outputs for n BF16 input rows; with kTrain also the pre-activations
+// of the three hidden layers, BF16 [3][n][128] at z (the training forward).
+template <bool kTrain>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const bf16* x, int64_t n,
-                                                              float* out, int* status) {
+                                                              float* out, int* status,
+                                                              bf16* z = nullptr) {
     extern __shared__ unsigned char smem_raw[];
     const TcShared S = tc_shared(smem_raw);
     const uint32_t tmem_base = tc_setup(S, w);
@@ -825,7 +605,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const b
     const float b4 = w.p[kOffB4];
     uint32_t phase = 0;
     const int64_t n_tiles = (n + 127) / 128;
-    for (int64_t t = (int64_t)blockIdx.x * kTcGroups + G.g; t < n_tiles;
+    // tiles group-major across the CTAs, so that few tiles still use many SMs
+    for (int64_t t = (int64_t)G.g * gridDim.x + blockIdx.x; t < n_tiles;
          t += (int64_t)gridDim.x * kTcGroups) {
         const int64_t base = t * 128;
         for (int k = G.gt; k < 128 * 4; k += kGrpThreads) {   // 128 rows x 4 chunks of 8 inputs
@@ -838,10 +619,242 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_forward(Weights w, const b
         fence_async_smem();
         group_sync(G.g);
         float o = 0.f;
-        if (!tc_network(S, G, phase, b4, &o, status)) break;
+        bf16* z_row = (kTrain && base + G.gt < n) ? z + (size_t)(base + G.gt) * kHid : nullptr;
+        if (!tc_network<kTrain>(S, G, phase, b4, &o, status, z_row, (size_t)n * kHid)) break;
         if (base + G.gt < n) out[base + G.gt] = o;
     }
     tc_teardown(S, G, tmem_base, phase);
+}
+
+// ---------------------------------------------------------------------------
+// Training backward on the tensor cores.  One hidden layer l with input
+// width K (32 for the first layer, 128 otherwise); one CTA of 128 threads per
+// tile of 128 samples:
+//   gW[i][j] = sum_s dZ[s][i] H[s][j]        M = 128 outputs, N = K, K-dim = samples
+//   dZprev[s][j] = (sum_i dZ[s][i] W[i][j]) gelu'(Zprev[s][j])      (l > 1)
+//                                            M = 128 samples, N = 128, K-dim = outputs
+// H = gelu(Zprev) for l > 1, the input x for l = 1.  Every operand is staged
+// K-major in 128-byte-swizzled shared memory; the transposes (W^T, dZ^T,
+// H^T) happen while staging from global memory.  Each CTA writes its partial
+// sums of gW and of the bias gradient; k_reduce_grad adds them in CTA order.
+constexpr uint32_t kBkBlock = 128 * 128;   // bytes of one 64-wide K block of a 128-row operand
+template <int K>
+struct BackTc {
+    static constexpr uint32_t kADx = 0;                  // dZ   [128 samples][128 outputs]
+    static constexpr uint32_t kBDx = 2 * kBkBlock;       // W^T  [128 inputs][128 outputs]
+    static constexpr uint32_t kADw = 4 * kBkBlock;       // dZ^T [128 outputs][128 samples]
+    static constexpr uint32_t kBDw = 6 * kBkBlock;       // H^T  [K inputs][128 samples]
+    static constexpr uint32_t kBDwBlock = (uint32_t)K * 128u;
+    static constexpr uint32_t kBar = kBDw + 2 * kBDwBlock;
+    static constexpr size_t kSmem = kBar + 64 + 1024;     // + room to align the base to 1 KB
+    static constexpr uint32_t kIdescDx = (1u << 4) | (1u << 7) | (1u << 10) |
+                                         ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr uint32_t kIdescDw = (1u << 4) | (1u << 7) | (1u << 10) |
+                                         (((uint32_t)K >> 3) << 17) | ((128u >> 4) << 24);
+    static_assert(K % 32 == 0 && K >= 32 && K <= 128, "N of the weight-gradient MMA");
+    static_assert(kBDwBlock % 1024 == 0 && kSmem <= 227 * 1024, "shared memory");
+};
+
+// Byte offset of 16-byte chunk j (0..7) of K block kb of row r, blocks of
+// `block` bytes (rows x 128 B).
+__device__ __forceinline__ uint32_t sw_off(int r, int kb, int j, uint32_t block) {
+    return (uint32_t)kb * block + (uint32_t)r * 128u + ((uint32_t)(j ^ (r & 7)) << 4);
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&t);
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_tc_back_layer(const bf16* dz, const bf16* zprev,
+                                                       const bf16* x, const bf16* W, int64_t n,
+                                                       float* part_w /* [cta][128][K] */,
+                                                       float* part_b /* [cta][128] */,
+                                                       bf16* dzprev, int* status) {
+    typedef BackTc<K> L;
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t pad = ((a0 + 1023u) & ~1023u) - a0;
+    unsigned char* sm = smem_raw + pad;
+    const uint32_t sb = a0 + pad;
+    const uint32_t bar = sb + L::kBar;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + L::kBar + 16);
+    int* abort_flag = reinterpret_cast<int*>(sm + L::kBar + 24);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int64_t base = (int64_t)blockIdx.x * 128;
+    const int rows = (n - base) < 128 ? (int)(n - base) : 128;
+    // the previous layer's dZ exists only above the first layer (K = 128)
+    const bool want_dx = K == kHid && dzprev != nullptr;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 0) tc_alloc(sb + L::kBar + 16, 256);
+    // Transposed operands are built from coalesced 16-byte row loads: 8
+    // consecutive elements of one source row go to 8 rows of the tile, each
+    // into its 2-byte slot of the sample (or output) column.
+    auto put_t = [&](uint32_t region, uint32_t block, int row, int col, uint16_t v) {
+        *reinterpret_cast<uint16_t*>(sm + region + sw_off(row, col >> 6, (col & 63) >> 3, block) +
+                                     (col & 7) * 2) = v;
+    };
+    // Every staging loop first loads all of its 16-byte vectors (independent
+    // loads in flight together), then stores them.
+    if (K == kHid && want_dx) {
+        // dZ rows, K-major over the outputs; dZ^T [output][sample] from the same rows
+        uint4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, r = i >> 4, c = i & 15;
+            v[k] = r < rows ? *reinterpret_cast<const uint4*>(dz + (size_t)(base + r) * kHid + c * 8)
+                            : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, r = i >> 4, c = i & 15;
+            *reinterpret_cast<uint4*>(sm + L::kADx + sw_off(r, c >> 3, c & 7, kBkBlock)) = v[k];
+        }
+        // W^T [input j][output o] from the rows of W [output o][input j]
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, o = i / (K / 8), jc = i % (K / 8);
+            v[k] = *reinterpret_cast<const uint4*>(W + (size_t)o * K + jc * 8);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, o = i / (K / 8), jc = i % (K / 8);
+            const uint16_t* e = reinterpret_cast<const uint16_t*>(&v[k]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) put_t(L::kBDx, kBkBlock, jc * 8 + q, o, e[q]);
+        }
+    }
+    {
+        // dZ^T [output i][sample s] from the rows of dZ [sample s][output i]
+        uint4 v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, r = i >> 4, c = i & 15;
+            v[k] = r < rows ? *reinterpret_cast<const uint4*>(dz + (size_t)(base + r) * kHid + c * 8)
+                            : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int i = t + k * 128, r = i >> 4, c = i & 15;
+            const uint16_t* e = reinterpret_cast<const uint16_t*>(&v[k]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) put_t(L::kADw, kBkBlock, c * 8 + q, r, e[q]);
+        }
+    }
+    {
+        // H^T [input j][sample s]; H = gelu(Zprev) above the first layer, else x
+        constexpr int kLoads = K / 8;   // 16-byte vectors per thread
+        uint4 v[kLoads];
+#pragma unroll
+        for (int k = 0; k < kLoads; ++k) {
+            const int i = t + k * 128, r = i / (K / 8), jc = i % (K / 8);
+            v[k] = r >= rows ? make_uint4(0u, 0u, 0u, 0u)
+                   : zprev   ? *reinterpret_cast<const uint4*>(zprev + (size_t)(base + r) * kHid + jc * 8)
+                             : *reinterpret_cast<const uint4*>(x + (size_t)(base + r) * kIn + jc * 8);
+        }
+#pragma unroll
+        for (int k = 0; k < kLoads; ++k) {
+            const int i = t + k * 128, r = i / (K / 8), jc = i % (K / 8);
+            const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v[k]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(e[q]);
+                // padding rows are zero, and gelu(0) = 0
+                const __nv_bfloat16 b0 = __float2bfloat16_rn(zprev ? gelu(f.x) : f.x);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn(zprev ? gelu(f.y) : f.y);
+                put_t(L::kBDw, L::kBDwBlock, jc * 8 + 2 * q, r, *reinterpret_cast<const uint16_t*>(&b0));
+                put_t(L::kBDw, L::kBDwBlock, jc * 8 + 2 * q + 1, r, *reinterpret_cast<const uint16_t*>(&b1));
+            }
+        }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    if (t == 0) {
+        if (want_dx) {
+            for (int ks = 0; ks < 8; ++ks) {
+                const uint32_t off = (uint32_t)(ks >> 2) * kBkBlock + (uint32_t)(ks & 3) * 32u;
+                tc_mma(tmem, umma_desc(sb + L::kADx + off), umma_desc(sb + L::kBDx + off),
+                       L::kIdescDx, ks > 0 ? 1u : 0u);
+            }
+        }
+        for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t oa = (uint32_t)(ks >> 2) * kBkBlock + (uint32_t)(ks & 3) * 32u;
+            const uint32_t ob = (uint32_t)(ks >> 2) * L::kBDwBlock + (uint32_t)(ks & 3) * 32u;
+            tc_mma(tmem + 128u, umma_desc(sb + L::kADw + oa), umma_desc(sb + L::kBDw + ob),
+                   L::kIdescDw, ks > 0 ? 1u : 0u);
+        }
+        tc_commit(bar);
+        if (!mbar_wait_bounded(bar, 0)) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+        }
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (!*abort_flag) {
+        // this thread's TMEM lane: output i = t of gW, sample t of dZprev
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        float* pw = part_w + ((size_t)blockIdx.x * kHid + t) * K;
+#pragma unroll 1
+        for (int cb = 0; cb < K; cb += 32) {
+            float v[32];
+            tc_ld32(lane_base + 128u + (uint32_t)cb, v);
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+                *reinterpret_cast<float4*>(pw + cb + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
+        // bias gradient: the samples of row t of dZ^T, in sample order
+        float sbias = 0.f;
+        for (int c = 0; c < 16; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(sm + L::kADw + sw_off(t, c >> 3, c & 7, kBkBlock));
+            const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(e[q]);
+                sbias += f.x;
+                sbias += f.y;
+            }
+        }
+        part_b[(size_t)blockIdx.x * kHid + t] = sbias;
+        if (want_dx) {
+            const size_t o = (size_t)(base + t) * kHid;
+#pragma unroll 1
+            for (int cb = 0; cb < 128; cb += 32) {
+                float v[32];
+                tc_ld32(lane_base + (uint32_t)cb, v);   // every lane of the warp takes part
+                if (t < rows) {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 8) {
+                        const uint4 zv = *reinterpret_cast<const uint4*>(zprev + o + cb + q);
+                        const __nv_bfloat162* ze = reinterpret_cast<const __nv_bfloat162*>(&zv);
+                        uint32_t u[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float2 zf = __bfloat1622float2(ze[k]);
+                            u[k] = bf16_pair(v[q + 2 * k] * gelu_grad(zf.x),
+                                             v[q + 2 * k + 1] * gelu_grad(zf.y));
+                        }
+                        *reinterpret_cast<uint4*>(dzprev + o + cb + q) = make_uint4(u[0], u[1], u[2], u[3]);
+                    }
+                }
+            }
+        }
+    }
+    // the MMAs of an aborted CTA may still write TMEM: wait once more (bounded)
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0 && *abort_flag) mbar_wait_bounded(bar, 0);
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, 256);
 }
 
 struct SurrogateRowParams {
@@ -977,7 +990,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
                 fence_async_smem();
                 group_sync(G.g);
                 float o = 0.f;
-                ok = tc_network(S, G, phase, b4, &o, P.status);
+                ok = tc_network<false>(S, G, phase, b4, &o, P.status);
                 const int slot = c * 4 + (gt >> 5), ql = gt & 31;
                 if (ok && slot < n_act && ql < nq_here) {
                     const float v = __expf(o) - kSurrogateEps;
@@ -1042,18 +1055,18 @@ int surrogate_kernel_attrs() {
     LMMEW_CUDA(cudaGetDevice(&dev));
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return LMMEW_OK;
-    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mlp::kFwdSmem));
-    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_back_layer<mlp::kHid>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mlp::back_smem(mlp::kHid)));
-    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_back_layer<mlp::kIn>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mlp::back_smem(mlp::kIn)));
-    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)mlp::kTcSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_forward<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::kTcSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_forward<true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::kTcSmem));
     LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_surrogate_rows,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp::kTcSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_back_layer<mlp::kHid>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::BackTc<mlp::kHid>::kSmem));
+    LMMEW_CUDA(cudaFuncSetAttribute(mlp::k_tc_back_layer<mlp::kIn>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)mlp::BackTc<mlp::kIn>::kSmem));
     done.fetch_or(bit);
     return LMMEW_OK;
 }
@@ -1176,15 +1189,21 @@ int gradient(lm_surrogate* s, const bf16* xb, const float* t, const float* v, in
     bf16* d2 = (bf16*)(base + o_d2);
     bf16* d1 = (bf16*)(base + o_d1);
     M::Weights w{s->W1, s->W2, s->W3, s->p};
-    M::k_forward<<<(unsigned)n_cta, M::kThreads, M::kFwdSmem, st>>>(w, xb, n, out, z);
+    // forward on the tensor cores, keeping the hidden pre-activations
+    // one 128-sample tile per group; as many CTAs as SMs allow
+    const int fwd_grid = (int)std::min<int64_t>(n_cta, sm_count());
+    M::k_tc_forward<true><<<fwd_grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status, z);
     M::k_back_out<<<(unsigned)n_cta, M::kThreads, 0, st>>>(s->p, out, t, v, z + 2 * n * M::kHid, n,
                                                           1.f / (float)n, d3, (float*)(base + o_po));
-    M::k_back_layer<M::kHid><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kHid), st>>>(
-        d3, z + n * M::kHid, nullptr, s->W3, n, (float*)(base + o_pw3), (float*)(base + o_pb3), d2);
-    M::k_back_layer<M::kHid><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kHid), st>>>(
-        d2, z, nullptr, s->W2, n, (float*)(base + o_pw2), (float*)(base + o_pb2), d1);
-    M::k_back_layer<M::kIn><<<(unsigned)n_cta, M::kThreads, M::back_smem(M::kIn), st>>>(
-        d1, nullptr, xb, s->W1, n, (float*)(base + o_pw1), (float*)(base + o_pb1), nullptr);
+    // hidden layers 3, 2, 1 on the tensor cores
+    M::k_tc_back_layer<M::kHid><<<(unsigned)n_cta, 128, M::BackTc<M::kHid>::kSmem, st>>>(
+        d3, z + n * M::kHid, nullptr, s->W3, n, (float*)(base + o_pw3), (float*)(base + o_pb3), d2,
+        s->status);
+    M::k_tc_back_layer<M::kHid><<<(unsigned)n_cta, 128, M::BackTc<M::kHid>::kSmem, st>>>(
+        d2, z, nullptr, s->W2, n, (float*)(base + o_pw2), (float*)(base + o_pb2), d1, s->status);
+    M::k_tc_back_layer<M::kIn><<<(unsigned)n_cta, 128, M::BackTc<M::kIn>::kSmem, st>>>(
+        d1, nullptr, xb, s->W1, n, (float*)(base + o_pw1), (float*)(base + o_pb1), nullptr,
+        s->status);
     M::k_reduce_grad<<<(M::kParams + 255) / 256, 256, 0, st>>>(
         (float*)(base + o_pw1), (float*)(base + o_pb1), (float*)(base + o_pw2), (float*)(base + o_pb2),
         (float*)(base + o_pw3), (float*)(base + o_pb3), (float*)(base + o_po), (int)n_cta, s->grad);
@@ -1322,7 +1341,7 @@ int lm_surrogate_forward(lm_surrogate* s, const float* x, int64_t n, float* out,
     M::Weights w{s->W1, s->W2, s->W3, s->p};
     const int64_t tiles = (n + 127) / 128;
     const unsigned grid = (unsigned)std::min<int64_t>((tiles + M::kTcGroups - 1) / M::kTcGroups, sm_count());
-    M::k_tc_forward<<<grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status);
+    M::k_tc_forward<false><<<grid, M::kTcThreads, M::kTcSmem, st>>>(w, xb, n, out, s->status);
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
 }

@@ -50,7 +50,7 @@ def parse_args():
                     help="skip the forms section (precision, batching, comparison, surrogate, combined)")
     ap.add_argument("--forms", default="precision,batching,comparison,surrogate,combined",
                     help="comma-separated forms to measure")
-    ap.add_argument("--case", default=None, choices=["surrogate_rows"],
+    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
     return ap.parse_args()
 
@@ -848,11 +848,39 @@ def run_surrogate_rows_case(n_events=20_000, repeats=3):
     return 0
 
 
+def run_surrogate_train_case(steps=10, batch=16_384, n=200_000):
+    """Small case for profiling one surrogate training step: Adam on
+    minibatches of 16 384 of 200 000 random inputs (2 warm-up steps, then
+    `steps` steps without per-step loss read-back).  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    rng = np.random.default_rng(0)
+    x = torch.from_numpy(rng.normal(0, 1, (n, 32)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(-10, 2, n).astype(np.float32)).cuda()
+    sur = lm.Surrogate(seed=3)
+    sur.train(x, t, steps=2, batch=batch, lr=1e-3, record_loss=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sur.train(x, t, steps=steps, batch=batch, lr=1e-3, record_loss=False)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "surrogate_train", "batch": batch, "steps": steps,
+                      "ms_per_step": e0.elapsed_time(e1) / steps}), flush=True)
+    sur.close()
+    return 0
+
+
 def main():
     args = parse_args()
     rank, local_rank, world = dist_env()
     if args.case == "surrogate_rows":
         return run_surrogate_rows_case()
+    if args.case == "surrogate_train":
+        return run_surrogate_train_case()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_gpu(args, rank, local_rank, world)

@@ -53,12 +53,12 @@ int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
 // warm-up launch it tries every events-per-tile size (32, 64 or 128 where
 // the FP32 form has the small-tile kernels) x work-unit order at the
 // occupancy limit of CTAs per SM, then the best of those with one CTA per SM
-// fewer.  The
-// sample runs without forward sums or stored rows.  The choice is kept per
-// handle for each workload class: log2 of the sample's mean events per
-// angle, the scatter model and the precision.  The sorted events leave re-cut into
-// tiles of the chosen size.  Every choice gives bit-identical results: a
-// tile's size changes only which exact-zero terms it skips.
+// fewer.  The sample runs without forward sums or stored rows.  The choice
+// is kept per handle for each workload class: log2 of the sample's mean
+// events per angle, the scatter model and the precision.  The sorted events
+// leave re-cut into tiles of the chosen size.  Every choice gives
+// bit-identical results: a tile's size changes only which exact-zero terms
+// it skips.
 constexpr int64_t kTuneEvents = 16384;
 
 int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t st) {
@@ -99,11 +99,15 @@ int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t 
     const bool small_tiles = h->prec == 0 && h->mc.W <= 4;
     const int sizes[3] = {kET, 64, 32};
     const int n_sizes = small_tiles ? 3 : 1;
+    cudaEvent_t ta = nullptr, tb = nullptr;
+    LMMEW_CUDA(cudaEventCreate(&ta));
+    const cudaError_t ce = cudaEventCreate(&tb);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(ta);
+        return cuda_error(ce, "cudaEventCreate");
+    }
     const int prof = h->prof_on;
     h->prof_on = 0;   // the trial launches are not part of any timed work
-    cudaEvent_t ta, tb;
-    LMMEW_CUDA(cudaEventCreate(&ta));
-    LMMEW_CUDA(cudaEventCreate(&tb));
     int rc = LMMEW_OK;
     int reps = 1;
     // one trial: the sample in tiles of `size` events, unit order, CTAs per SM;

@@ -442,8 +442,8 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
     res = {}
-    for kind in ("exact", "surrogate", "none"):
-        model.set_scatter_model(kind, sur if kind == "surrogate" else None)
+    for kind in ("exact", "surrogate", "surrogate_coarse", "none"):
+        model.set_scatter_model(kind, sur if kind.startswith("surrogate") else None)
         y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)   # also warms up
         model.osem(dev, lam0.clone(), sc.n_subsets, 0)   # untimed: the row-kernel autotune
         img = lam0.clone()
@@ -467,7 +467,7 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
                         "heldout_object_mass_rel_err": mass_err,
                         "heldout_object_mass_ratio": mass_ratio},
            "exact": {"s_per_iter": ex["s_per_iter"], "roi_activity": roi_ex}}
-    for kind in ("surrogate", "none"):
+    for kind in ("surrogate", "surrogate_coarse", "none"):
         r = res[kind]
         roi = roi_sums(r["img"], ph.lesion_masks)
         out[kind] = {"s_per_iter": r["s_per_iter"],
@@ -533,32 +533,36 @@ def run_combined_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, ite
         img = lam0.clone()
         t_exact += timed(lambda: model.osem(d, img, sc.n_subsets, iters))
         exact_imgs.append(img.cpu().numpy().astype(np.float64))
-    # the combined form (the first batched call tunes the launch shape)
-    model.set_scatter_model("surrogate", sur)
-    imgs = lam0.repeat(n_real, 1).contiguous()
-    model.osem_batch(devs, imgs, sc.n_subsets, iters)
-    imgs = lam0.repeat(n_real, 1).contiguous()
-    t_comb = timed(lambda: model.osem_batch(devs, imgs, sc.n_subsets, iters))
-    model.set_scatter_model("exact")
-    comb = imgs.cpu().numpy().astype(np.float64)
-    dev_roi = []
-    for r in range(n_real):
-        ref = roi_sums(exact_imgs[r], ph.lesion_masks)
-        got = roi_sums(comb[r], ph.lesion_masks)
-        dev_roi.append([abs(a - b) / b for a, b in zip(got, ref)])
-    dev_roi = np.asarray(dev_roi)
+    # the combined form, with the network at every voxel and on the coarse
+    # grid (the first batched call of each tunes the launch shape)
+    out = {"workload": f"{n_real} realisations of {sc.name} with U[{lo}, {hi}] events "
+                       f"({int(sizes.sum())} events, resampled from one MC pool), "
+                       f"{sc.n_subsets} subsets x {iters} iterations each",
+           "surrogate_training": {"objects": n_objects, "samples": n_samples,
+                                  "sample_s": t_sample, "train_s": t_train},
+           "exact_fp32_one_at_a_time_s": t_exact}
+    for kind, key in (("surrogate", ""), ("surrogate_coarse", "coarse_")):
+        model.set_scatter_model(kind, sur)
+        imgs = lam0.repeat(n_real, 1).contiguous()
+        model.osem_batch(devs, imgs, sc.n_subsets, iters)
+        imgs = lam0.repeat(n_real, 1).contiguous()
+        t_comb = timed(lambda: model.osem_batch(devs, imgs, sc.n_subsets, iters))
+        model.set_scatter_model("exact")
+        comb = imgs.cpu().numpy().astype(np.float64)
+        dev_roi = []
+        for r in range(n_real):
+            ref = roi_sums(exact_imgs[r], ph.lesion_masks)
+            got = roi_sums(comb[r], ph.lesion_masks)
+            dev_roi.append([abs(a - b) / b for a, b in zip(got, ref)])
+        dev_roi = np.asarray(dev_roi)
+        out[key + "surrogate_bf16_batched_s"] = t_comb
+        out[key + "speedup_vs_exact_fp32"] = t_exact / t_comb
+        out[key + "roi_rel_dev_vs_exact"] = {"mean": float(dev_roi.mean()),
+                                             "max": float(dev_roi.max()),
+                                             "per_lesion_mean": dev_roi.mean(axis=0).tolist()}
     sur.close()
     model.close()
-    return {"workload": f"{n_real} realisations of {sc.name} with U[{lo}, {hi}] events "
-                        f"({int(sizes.sum())} events, resampled from one MC pool), "
-                        f"{sc.n_subsets} subsets x {iters} iterations each",
-            "surrogate_training": {"objects": n_objects, "samples": n_samples,
-                                   "sample_s": t_sample, "train_s": t_train},
-            "exact_fp32_one_at_a_time_s": t_exact,
-            "surrogate_bf16_batched_s": t_comb,
-            "speedup_vs_exact_fp32": t_exact / t_comb,
-            "roi_rel_dev_vs_exact": {"mean": float(dev_roi.mean()), "max": float(dev_roi.max()),
-                                     "per_lesion_mean": dev_roi.mean(axis=0).tolist()}}
+    return out
 
 
 def run_batch_forms():

@@ -231,7 +231,8 @@ class Model:
                                                               self.PRECISIONS[precision]))
 
     SCATTER_MODELS = {"exact": _native.SCATTER_EXACT, "surrogate": _native.SCATTER_SURROGATE,
-                      "none": _native.SCATTER_NONE}
+                      "none": _native.SCATTER_NONE,
+                      "surrogate_coarse": _native.SCATTER_SURROGATE_COARSE}
 
     def set_scatter_model(self, model="exact", surrogate: "Surrogate | None" = None):
         """Scatter part of the rows: 'exact' (the single-scatter sum),

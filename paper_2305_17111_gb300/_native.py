@@ -109,7 +109,7 @@ SYMBOLS = {
     "lm_selftest_wait_timeout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
 }
 
-SCATTER_EXACT, SCATTER_SURROGATE, SCATTER_NONE = 0, 1, 2
+SCATTER_EXACT, SCATTER_SURROGATE, SCATTER_NONE, SCATTER_SURROGATE_COARSE = 0, 1, 2, 3
 
 
 def load(path: str = LIB_PATH):

@@ -87,7 +87,8 @@ int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t 
         h->tune_key = key;
         return recut_tiles(h, &se, h->tile_ev, st);
     }
-    if (h->scatter_model == LMMEW_SCATTER_SURROGATE) {
+    if (h->scatter_model == LMMEW_SCATTER_SURROGATE ||
+        h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE) {
         // the network kernel dominates and has its own launch shape
         h->tile_ev = kET;
         h->unit_order = 0;
@@ -367,6 +368,10 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_cs);
     cudaFree(h->d_crange);
     cudaFree(h->d_g8);
+    cudaFree(h->d_node_q);
+    cudaFree(h->d_interp_node);
+    cudaFree(h->d_interp_w);
+    cudaFree(h->scratch_nodes.ptr);
     cudaFree(h->d_rho);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
@@ -428,13 +433,16 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     if (rc != LMMEW_OK) return rc;
     // the surrogate adds its scatter part to stored rows; the other models
     // need only the partial forward sums
-    const bool keep_rows = h->scatter_model == LMMEW_SCATTER_SURROGATE;
+    const bool keep_rows = h->scatter_model == LMMEW_SCATTER_SURROGATE ||
+                           h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE;
     const int rs = row_stride_of(h);
     const int64_t max_ev =
         std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / (keep_rows ? rs : m.nqt)));
     std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
     int64_t biggest = 0;
     for (const Chunk& c : chunks) biggest = std::max(biggest, c.e1 - c.e0);
+    rc = surrogate_prepare(h, biggest, st);
+    if (rc != LMMEW_OK) return rc;
     rc = ensure(h, h->scratch_work,
                 bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * m.nqt * biggest) +
                     (keep_rows ? bump_bytes(sizeof(float) * rs * biggest) : 0),
@@ -484,6 +492,8 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
         biggest = std::max(biggest, c.e1 - c.e0);
         parts += bp_parts(c.e1 - c.e0);
     }
+    rc = surrogate_prepare(h, biggest, st);
+    if (rc != LMMEW_OK) return rc;
     rc = ensure(h, h->scratch_work,
                 bump_bytes(sizeof(float) * rs * biggest) + bump_bytes(sizeof(float) * parts * m.nq) +
                     bump_bytes(sizeof(double) * m.nq),
@@ -557,6 +567,8 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
                         bump_bytes(sizeof(float) * std::max<int64_t>(parts_max, 1) * m.nq) +
                         bump_bytes(sizeof(double) * std::max<int64_t>(parts_max, 1)) +
                         bump_bytes(sizeof(double) * m.nq);
+    rc = surrogate_prepare(h, biggest, st);
+    if (rc != LMMEW_OK) return rc;
     rc = ensure(h, h->scratch_work, need, st);
     if (rc != LMMEW_OK) return rc;
     char* w = (char*)h->scratch_work.ptr;
@@ -670,6 +682,8 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
         return set_error(LMMEW_ERR_INVALID_ARG, "realisations x row blocks too large for one batch");
     int64_t biggest = 1;
     for (const RowBlock& b : blocks) biggest = std::max(biggest, b.e1 - b.e0);
+    rc = surrogate_prepare(h, biggest, st);   // before the graph capture
+    if (rc != LMMEW_OK) return rc;
     // back-projection chunks: up to 128 events of one realisation in one block;
     // a subset's slots run realisation-major, so each realisation's partial
     // sums are one contiguous run of slots.  Chunks of a subset: at most its

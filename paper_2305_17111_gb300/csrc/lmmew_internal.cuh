@@ -118,7 +118,13 @@ struct lm_handle {
     float* d_rho = nullptr;        // [n][n] relative density (surrogate inputs)
     double mu_line[LMMEW_MAX_LINES] = {};   // mu_water at each line energy
     const struct lm_surrogate* surrogate = nullptr;   // scatter model when set
-    int scatter_model = 0;         // 0 exact, 1 surrogate, 2 none
+    int scatter_model = 0;         // 0 exact, 1 surrogate, 2 none, 3 surrogate on the coarse grid
+    // coarse-grid surrogate: network nodes and each voxel's interpolation
+    int n_nodes = 0;
+    int* d_node_q = nullptr;       // [n_nodes] support voxel of each node
+    int4* d_interp_node = nullptr; // [nq] up to 4 nodes of each voxel (-1: none)
+    float4* d_interp_w = nullptr;  // [nq] their weights (sum 1)
+    lmmew::Scratch scratch_nodes;  // [block events][n_nodes] network outputs
     double* d_sens_a_prim = nullptr;   // [A][nq] unscattered part of the sensitivity
     int sens_prim_only = 0;
     float setup_ms = 0.f;
@@ -222,6 +228,11 @@ int set_precision(lm_handle* h, int prec);
 // mlp.cu: the surrogate's rows (adds the learned scatter part to rows k_row
 // wrote without scatter, then the partial forward sums)
 int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st);
+// mlp.cu: nodes of the coarse-grid surrogate and each voxel's interpolation
+// (built once per handle), and the node-output scratch for a row block of
+// up to max_events events (called by the planners before any capture)
+int build_coarse_nodes(lm_handle* h);
+int surrogate_prepare(lm_handle* h, int64_t max_events, cudaStream_t st);
 size_t row_smem_bytes(const lm_handle* h);
 int row_kernel_occupancy(lm_handle* h);
 

@@ -882,6 +882,12 @@ struct SurrogateRowParams {
     // backscatter energy and E_w, widened by 8 energy-resolution sigmas
     float reach_lo[LMMEW_MAX_LINES], reach_hi[LMMEW_MAX_LINES];
     const float* rho;
+    // coarse-grid form: the columns are network nodes (node_q: their voxels)
+    // and the outputs go to nodebuf [event][n_cols] instead of the rows
+    const int* node_q;     // null: the columns are the support voxels
+    int n_cols, n_col_tiles;
+    float* nodebuf;
+    int64_t nodebuf_stride;
 };
 
 // The surrogate inside the row pipeline: after k_row wrote the unscattered
@@ -909,23 +915,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
     const int gt = G.gt;
     uint32_t phase = 0;
     const int n_tiles = P.tile_end - P.tile_begin;
-    const int n_units = n_tiles * P.nqt;
+    const int n_units = n_tiles * P.n_col_tiles;
     const float half_det = 0.5f * P.B * P.bin_w;
     bool ok = true;
     for (int unit = blockIdx.x * kTcGroups + G.g; unit < n_units && ok;
          unit += gridDim.x * kTcGroups) {
-        const Tile T = P.tiles[P.tile_begin + unit / P.nqt];
-        const int qt = unit % P.nqt;
-        const int nq_here = min(32, P.nq - qt * 32);
+        const Tile T = P.tiles[P.tile_begin + unit / P.n_col_tiles];
+        const int qt = unit % P.n_col_tiles;   // column tile: 32 voxels or 32 nodes
+        const int nq_here = min(32, P.n_cols - qt * 32);
         group_sync(G.g);   // the group's previous unit is done with the unit data
         if (gt < 32 && gt < nq_here) {
-            const int pix = P.q_pix[qt * 32 + gt];
+            const int pix = P.q_pix[P.node_q ? P.node_q[qt * 32 + gt] : qt * 32 + gt];
             Vxy[2 * gt] = ((pix % P.n) + 0.5f - 0.5f * P.n) * P.h;
             Vxy[2 * gt + 1] = ((pix / P.n) + 0.5f - 0.5f * P.n) * P.h;
         }
         for (int i = gt; i < 32 * 8; i += kGrpThreads)
-            if ((i >> 3) < nq_here)
-                Vg8[i] = P.g8[((size_t)T.a * P.nq + qt * 32 + (i >> 3)) * 8 + (i & 7)];
+            if ((i >> 3) < nq_here) {
+                const int col = qt * 32 + (i >> 3);
+                const int q = P.node_q ? P.node_q[col] : col;
+                Vg8[i] = P.g8[((size_t)T.a * P.nq + q) * 8 + (i & 7)];
+            }
         if (gt < T.count) {
             Eeu[2 * gt] = P.ev_e[T.begin + gt];
             Eeu[2 * gt + 1] = -half_det + (P.ev_bin[T.begin + gt] + 0.5f) * P.bin_w;
@@ -994,15 +1003,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
                 const int slot = c * 4 + (gt >> 5), ql = gt & 31;
                 if (ok && slot < n_act && ql < nq_here) {
                     const float v = __expf(o) - kSurrogateEps;
-                    if (v > 0.f)
-                        P.rows[(size_t)(T.begin + act[slot] - P.row_base) * P.row_stride +
-                               qt * 32 + ql] += v;
+                    if (v > 0.f) {
+                        const size_t e = (size_t)(T.begin + act[slot] - P.row_base);
+                        if (P.node_q)
+                            P.nodebuf[e * P.nodebuf_stride + qt * 32 + ql] += v;
+                        else
+                            P.rows[e * P.row_stride + qt * 32 + ql] += v;
+                    }
                 }
             }
         }
         if (!ok) break;
         group_sync(G.g);   // the group's row updates are visible to the whole group
-        if (P.lam && gt < T.count) {
+        if (P.lam && !P.node_q && gt < T.count) {
             const int rr = P.ev_real ? (int)P.ev_real[T.begin + gt] : T.r;
             const float* lam = P.lam + (size_t)rr * P.lam_stride;
             const float* row = P.rows + (size_t)(T.begin + gt - P.row_base) * P.row_stride + qt * 32;
@@ -1012,6 +1025,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
         }
     }
     tc_teardown(S, G, tmem_base, phase);
+}
+
+// Coarse-grid surrogate: each voxel's scatter part is the weighted sum of
+// its nodes' network outputs (weights summing to 1); it is added to the
+// voxel's row, then the forward partial sum of every 32-voxel tile is
+// formed in a fixed order.  One warp per event, a lane per voxel of the tile.
+__global__ void __launch_bounds__(256) k_interp_rows(const int4* inode, const float4* iw,
+                                                     const float* nodebuf, int64_t nb_stride,
+                                                     float* rows, int row_stride, int64_t count,
+                                                     int nq, const float* lam, int lam_stride,
+                                                     const uint16_t* ev_real, int64_t row_base,
+                                                     float* ypart, int64_t ypart_stride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 8 + warp;
+    const int qt = blockIdx.y;
+    const int q = qt * 32 + lane;
+    if (e >= count) return;   // the whole warp leaves together
+    float v = 0.f;
+    if (q < nq) {
+        const int4 id = inode[q];
+        const float4 w = iw[q];
+        const float* nb = nodebuf + e * nb_stride;
+        float sct = w.x * nb[id.x];
+        if (id.y >= 0) sct = fmaf(w.y, nb[id.y], sct);
+        if (id.z >= 0) sct = fmaf(w.z, nb[id.z], sct);
+        if (id.w >= 0) sct = fmaf(w.w, nb[id.w], sct);
+        float* r = rows + e * row_stride + q;
+        v = *r + sct;
+        *r = v;
+    }
+    if (lam) {
+        const float* lm = lam + (ev_real ? (size_t)ev_real[row_base + e] * lam_stride : 0);
+        float p = q < nq ? lm[q] * v : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (lane == 0) ypart[(size_t)qt * ypart_stride + e] = p;
+    }
 }
 
 }  // namespace mlp
@@ -1071,11 +1121,109 @@ int surrogate_kernel_attrs() {
     return LMMEW_OK;
 }
 
+// Nodes of the coarse-grid surrogate: the support voxels at even pixel
+// coordinates that some voxel interpolates from, and the support voxels
+// without any such neighbour (their own node).  Voxel (ix, iy) takes the
+// bilinear weights of the even-coordinate corners around it, (ix & ~1,
+// iy & ~1) to (+2, +2), keeps the corners in the support and renormalises
+// the weights to sum 1.  Built on the host once per handle.
+int build_coarse_nodes(lm_handle* h) {
+    if (h->d_node_q) return LMMEW_OK;
+    const int n = h->mc.n, nq = h->mc.nq;
+    std::vector<int> q_pix(nq);
+    LMMEW_CUDA(cudaMemcpy(q_pix.data(), h->d_q_pix, sizeof(int) * nq, cudaMemcpyDeviceToHost));
+    std::vector<int> q_of_pix((size_t)n * n, -1);
+    for (int q = 0; q < nq; ++q) q_of_pix[q_pix[q]] = q;
+    std::vector<int> node_of_q(nq, -1), node_q;
+    auto node_for = [&](int q) {
+        if (node_of_q[q] < 0) {
+            node_of_q[q] = (int)node_q.size();
+            node_q.push_back(q);
+        }
+        return node_of_q[q];
+    };
+    std::vector<int4> idx(nq);
+    std::vector<float4> wt(nq);
+    for (int q = 0; q < nq; ++q) {
+        const int ix = q_pix[q] % n, iy = q_pix[q] / n;
+        const int x0 = ix & ~1, y0 = iy & ~1;
+        const double tx = 0.5 * (ix - x0), ty = 0.5 * (iy - y0);
+        const int cx[4] = {x0, x0 + 2, x0, x0 + 2}, cy[4] = {y0, y0, y0 + 2, y0 + 2};
+        const double w0[4] = {(1 - tx) * (1 - ty), tx * (1 - ty), (1 - tx) * ty, tx * ty};
+        int cq[4];
+        double sum = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            cq[k] = (w0[k] > 0.0 && cx[k] < n && cy[k] < n) ? q_of_pix[(size_t)cy[k] * n + cx[k]] : -1;
+            if (cq[k] >= 0) sum += w0[k];
+        }
+        int ni[4] = {-1, -1, -1, -1};
+        float nw[4] = {0.f, 0.f, 0.f, 0.f};
+        if (sum <= 0.0) {
+            ni[0] = node_for(q);
+            nw[0] = 1.f;
+        } else {
+            int j = 0;
+            for (int k = 0; k < 4; ++k)
+                if (cq[k] >= 0) {
+                    ni[j] = node_for(cq[k]);
+                    nw[j] = (float)(w0[k] / sum);
+                    ++j;
+                }
+        }
+        idx[q] = make_int4(ni[0], ni[1], ni[2], ni[3]);
+        wt[q] = make_float4(nw[0], nw[1], nw[2], nw[3]);
+    }
+    const int nn = (int)node_q.size();
+    if (cudaMalloc(&h->d_node_q, sizeof(int) * nn) != cudaSuccess ||
+        cudaMalloc(&h->d_interp_node, sizeof(int4) * nq) != cudaSuccess ||
+        cudaMalloc(&h->d_interp_w, sizeof(float4) * nq) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->d_node_q);
+        cudaFree(h->d_interp_node);
+        cudaFree(h->d_interp_w);
+        h->d_node_q = nullptr;
+        h->d_interp_node = nullptr;
+        h->d_interp_w = nullptr;
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the coarse-grid surrogate tables");
+    }
+    LMMEW_CUDA(cudaMemcpy(h->d_node_q, node_q.data(), sizeof(int) * nn, cudaMemcpyHostToDevice));
+    LMMEW_CUDA(cudaMemcpy(h->d_interp_node, idx.data(), sizeof(int4) * nq, cudaMemcpyHostToDevice));
+    LMMEW_CUDA(cudaMemcpy(h->d_interp_w, wt.data(), sizeof(float4) * nq, cudaMemcpyHostToDevice));
+    h->n_nodes = nn;
+    return LMMEW_OK;
+}
+
+int surrogate_prepare(lm_handle* h, int64_t max_events, cudaStream_t st) {
+    if (h->scatter_model != LMMEW_SCATTER_SURROGATE_COARSE) return LMMEW_OK;
+    const size_t need = sizeof(float) * (size_t)std::max<int64_t>(max_events, 1) * h->n_nodes;
+    if (h->scratch_nodes.bytes >= need) return LMMEW_OK;
+    if (h->scratch_nodes.ptr) {
+        LMMEW_CUDA(cudaStreamSynchronize(st));
+        cudaFree(h->scratch_nodes.ptr);
+        h->scratch_nodes.ptr = nullptr;
+        h->scratch_nodes.bytes = 0;
+    }
+    if (cudaMalloc(&h->scratch_nodes.ptr, need) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the coarse-grid surrogate outputs");
+    }
+    h->scratch_nodes.bytes = need;
+    return LMMEW_OK;
+}
+
 int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
-    const int n_units = (L.tile_end - L.tile_begin) * h->mc.nqt;
+    const bool coarse = h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE;
+    const int n_cols = coarse ? h->n_nodes : h->mc.nq;
+    const int n_col_tiles = (n_cols + 31) / 32;
+    const int n_units = (L.tile_end - L.tile_begin) * n_col_tiles;
     if (n_units <= 0) return LMMEW_OK;
     int rc = surrogate_kernel_attrs();
     if (rc != LMMEW_OK) return rc;
+    const int64_t count = L.n_events;   // events of the row block
+    const size_t node_bytes = sizeof(float) * (size_t)std::max<int64_t>(count, 0) * h->n_nodes;
+    if (coarse && h->scratch_nodes.bytes < node_bytes)
+        return set_error(LMMEW_ERR_INVALID_ARG,
+                         "coarse-grid surrogate outputs not prepared for this row block");
     mlp::SurrogateRowParams P;
     surrogate_weights(h->surrogate, &P.w);
     P.tiles = L.tiles;
@@ -1116,10 +1264,25 @@ int launch_surrogate_rows(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
         P.reach_hi[w] = (float)(ew + kSurrogateReachSigmas * sigma_e(ew));
     }
     P.rho = h->d_rho;
+    P.node_q = coarse ? h->d_node_q : nullptr;
+    P.n_cols = n_cols;
+    P.n_col_tiles = n_col_tiles;
+    P.nodebuf = coarse ? (float*)h->scratch_nodes.ptr : nullptr;
+    P.nodebuf_stride = h->n_nodes;
+    if (coarse) LMMEW_CUDA(cudaMemsetAsync(P.nodebuf, 0, node_bytes, st));
     const int grid = std::min((n_units + mlp::kTcGroups - 1) / mlp::kTcGroups, h->sm_count);
     mlp::k_surrogate_rows<<<grid, mlp::kTcThreads, mlp::kTcSmem, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
+    if (coarse && count > 0) {
+        dim3 g((unsigned)((count + 7) / 8), (unsigned)h->mc.nqt);
+        mlp::k_interp_rows<<<g, 256, 0, st>>>(h->d_interp_node, h->d_interp_w, P.nodebuf, h->n_nodes,
+                                              L.rows, L.row_stride, count, h->mc.nq, L.lam_v,
+                                              L.lam_stride, L.ev_real, L.row_base, L.ypart,
+                                              L.ypart_stride);
+        ++h->launches;
+        LMMEW_CUDA(cudaGetLastError());
+    }
     return LMMEW_OK;
 }
 

@@ -142,13 +142,18 @@ extern "C" int lm_surrogate_sample(lm_handle* h, const lm_events* ev, int64_t n,
 
 extern "C" int lm_set_scatter_model(lm_handle* h, int model, const lm_surrogate* s) {
     if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
-    if (model < 0 || model > 2) return set_error(LMMEW_ERR_INVALID_ARG, "unknown scatter model");
-    if (model == LMMEW_SCATTER_SURROGATE) {
+    if (model < 0 || model > 3) return set_error(LMMEW_ERR_INVALID_ARG, "unknown scatter model");
+    const bool learned = model == LMMEW_SCATTER_SURROGATE || model == LMMEW_SCATTER_SURROGATE_COARSE;
+    if (learned) {
         if (!s) return set_error(LMMEW_ERR_INVALID_ARG, "surrogate is NULL");
         if (h->mc.W > 3)
             return set_error(LMMEW_ERR_NOT_IMPLEMENTED, "the surrogate covers up to 3 lines");
     }
+    if (model == LMMEW_SCATTER_SURROGATE_COARSE) {
+        const int rc = build_coarse_nodes(h);
+        if (rc != LMMEW_OK) return rc;
+    }
     h->scatter_model = model;
-    h->surrogate = model == LMMEW_SCATTER_SURROGATE ? s : nullptr;
+    h->surrogate = learned ? s : nullptr;
     return LMMEW_OK;
 }

@@ -373,19 +373,46 @@ def test_surrogate_fit_on_held_out_samples():
     assert mass_err < 0.35, mass_err
 
 
-def test_surrogate_rows_match_primary_plus_oracle_network():
+def _coarse_interpolation(pix, n):
+    """[nq][nq] interpolation of the coarse-grid surrogate, restated from its
+    definition: voxel (ix, iy) takes the bilinear weights of the corners
+    (ix - ix % 2, iy - iy % 2) .. (+2, +2) that lie in the support,
+    renormalised to sum 1; with no such corner it is its own node."""
+    q_of = {int(p): q for q, p in enumerate(pix)}
+    M = np.zeros((len(pix), len(pix)))
+    for q, p in enumerate(pix):
+        ix, iy = int(p) % n, int(p) // n
+        x0, y0 = ix - ix % 2, iy - iy % 2
+        tx, ty = (ix - x0) / 2.0, (iy - y0) / 2.0
+        corners = [(x0, y0, (1 - tx) * (1 - ty)), (x0 + 2, y0, tx * (1 - ty)),
+                   (x0, y0 + 2, (1 - tx) * ty), (x0 + 2, y0 + 2, tx * ty)]
+        keep = [(q_of[cy * n + cx], w) for cx, cy, w in corners
+                if w > 0 and cx < n and cy < n and (cy * n + cx) in q_of]
+        if not keep:
+            M[q, q] = 1.0
+        else:
+            tot = sum(w for _, w in keep)
+            for qq, w in keep:
+                M[q, qq] += w / tot
+    return M
+
+
+@pytest.mark.parametrize("model", ["surrogate", "surrogate_coarse"])
+def test_surrogate_rows_match_primary_plus_oracle_network(model):
     sc, ph, orc, gpu, ev, dev = _fine_model()
     s, _ = _trained_surrogate()
     p = s.get_params()
     orc0 = oracle.Model.from_scenario(sc.with_(scatter_n=0), ph.rho)
     lam = (np.random.default_rng(2).uniform(0.2, 3, ph.rho.size) * (ph.rho.reshape(-1) > 0))
     lam = lam.astype(np.float32)
-    gpu.set_scatter_model("surrogate", s)
+    gpu.set_scatter_model(model, s)
     try:
         got = gpu.forward(dev, torch.from_numpy(lam).cuda()).cpu().numpy().astype(np.float64)
     finally:
         gpu.set_scatter_model("exact")
     lam_q = lam.astype(np.float64)[orc.voxel_pixels]
+    interp = (_coarse_interpolation(orc.voxel_pixels, sc.n) if model == "surrogate_coarse"
+              else None)
     W = len(sc.line_keV)
     checked = 0
     for j in range(0, len(ev), 97):
@@ -400,6 +427,8 @@ def test_surrogate_rows_match_primary_plus_oracle_network():
                                               sc.e_ref_keV, sc.fwhm_exponent)
                            for w in range(W))])
         scat = (np.maximum(np.exp(out) - omlp.EPS_TARGET, 0.0) * reach[:, None]).sum(axis=0)
+        if interp is not None:
+            scat = interp @ scat
         want = float(lam_q @ (prim + scat))
         # BF16 network: outputs within ~1e-2 in log space, i.e. ~1e-2 of the
         # scatter part (3e-2 allowed), plus the primary part's 1e-5
@@ -414,8 +443,8 @@ def test_surrogate_gain_over_the_scatter_free_model():
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
     res = {}
-    for model in ("exact", "surrogate", "none"):
-        gpu.set_scatter_model(model, s if model == "surrogate" else None)
+    for model in ("exact", "surrogate", "surrogate_coarse", "none"):
+        gpu.set_scatter_model(model, s if model.startswith("surrogate") else None)
         y = gpu.forward(dev, lam_true).cpu().numpy().astype(np.float64)
         img = lam0.clone()
         gpu.osem(dev, img, 4, 5)
@@ -427,18 +456,19 @@ def test_surrogate_gain_over_the_scatter_free_model():
     roi = {k: np.array([v[1][m].sum() for m in masks]) for k, v in res.items()}
     roi_err = {k: float(np.mean(np.abs(roi[k] - roi["exact"]) / roi["exact"])) for k in res}
     img_err = {k: np.linalg.norm(v[1] - img_ex) / np.linalg.norm(img_ex) for k, v in res.items()}
-    assert fwd_err["surrogate"] < 0.5 * fwd_err["none"], fwd_err
-    assert img_err["surrogate"] < img_err["none"], img_err
-    assert roi_err["surrogate"] < roi_err["none"], roi_err
+    for kind in ("surrogate", "surrogate_coarse"):
+        assert fwd_err[kind] < 0.5 * fwd_err["none"], fwd_err
+        assert img_err[kind] < img_err["none"], img_err
+        assert roi_err[kind] < roi_err["none"], roi_err
 
 
-@pytest.mark.parametrize("model", ["surrogate", "none"])
+@pytest.mark.parametrize("model", ["surrogate", "surrogate_coarse", "none"])
 def test_batched_reconstruction_with_scatter_models_equals_single(model):
     """lm_osem_batch under the surrogate and the scatter-free model gives every
     realisation the image lm_osem gives it alone, bit for bit (each row value
     is computed the same way whatever tile it lands in)."""
     sc, ph, orc, gpu, ev, dev = _fine_model()
-    s, _ = _trained_surrogate() if model == "surrogate" else (None, None)
+    s, _ = _trained_surrogate() if model.startswith("surrogate") else (None, None)
     sizes = [500, 0, 333, 800]
     rng = np.random.default_rng(9)
     evs = [ev.subset(rng.choice(len(ev), size=n, replace=False)) for n in sizes]

@@ -790,6 +790,16 @@ def run_gpu(args, rank, local_rank, world):
                    "comparison": run_comparison_form, "surrogate": run_surrogate_form,
                    "combined": run_combined_form}
         line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}
+        comb = line["forms"].get("combined")
+        if comb:
+            # the metric's third part: the chosen forms together against the
+            # plain FP32 path on the same GPU, at the stated ROI-activity error
+            line["chosen_form"] = {
+                "form": "BF16 tensor-core surrogate on the coarse grid + batched realisations "
+                        "in one CUDA graph",
+                "workload": comb["workload"],
+                "speedup_vs_plain_fp32": comb["coarse_speedup_vs_exact_fp32"],
+                "roi_rel_dev_vs_plain_fp32": comb["coarse_roi_rel_dev_vs_exact"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

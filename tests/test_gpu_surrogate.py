@@ -487,15 +487,16 @@ def test_batched_reconstruction_with_scatter_models_equals_single(model):
         gpu.set_scatter_model("exact")
 
 
-def test_surrogate_backprojection_uses_the_surrogate_rows():
-    """Back projection under the surrogate model is the adjoint of its forward
-    projection: <A x, w> = <x, A^T w> in FP64 to FP32 rounding."""
+@pytest.mark.parametrize("model", ["surrogate", "surrogate_coarse"])
+def test_surrogate_backprojection_uses_the_surrogate_rows(model):
+    """Back projection under the surrogate models is the adjoint of their
+    forward projection: <A x, w> = <x, A^T w> in FP64 to FP32 rounding."""
     sc, ph, orc, gpu, ev, dev = _fine_model()
     s, _ = _trained_surrogate()
     rng = np.random.default_rng(4)
     x = (rng.uniform(0.2, 3, ph.rho.size) * (ph.rho.reshape(-1) > 0)).astype(np.float32)
     wv = rng.uniform(0.1, 1.0, len(ev)).astype(np.float32)
-    gpu.set_scatter_model("surrogate", s)
+    gpu.set_scatter_model(model, s)
     try:
         y = gpu.forward(dev, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
         bp = gpu.backproject(dev, torch.from_numpy(wv).cuda()).cpu().numpy().astype(np.float64)

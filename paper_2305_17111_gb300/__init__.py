@@ -236,8 +236,10 @@ class Model:
 
     def set_scatter_model(self, model="exact", surrogate: "Surrogate | None" = None):
         """Scatter part of the rows: 'exact' (the single-scatter sum),
-        'surrogate' (the learned network, which must stay alive while used)
-        or 'none' (unscattered paths only)."""
+        'surrogate' (the learned network at every voxel, which must stay
+        alive while used), 'surrogate_coarse' (the network on a
+        half-resolution grid of emission positions, interpolated) or 'none'
+        (unscattered paths only)."""
         ptr = surrogate._s if surrogate is not None else None
         _native.check(_native.load().lm_set_scatter_model(self._h, self.SCATTER_MODELS[model], ptr))
         self._surrogate_ref = surrogate

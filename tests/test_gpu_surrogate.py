@@ -34,6 +34,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import paper_2305_17111_gb300 as lm  # noqa: E402
+from paper_2305_17111_gb300 import _native  # noqa: E402
 from oracle import mlp as omlp  # noqa: E402
 from synthetic import preset, simulate  # noqa: E402
 
@@ -504,3 +505,28 @@ def test_surrogate_backprojection_uses_the_surrogate_rows(model):
         gpu.set_scatter_model("exact")
     lhs, rhs = float(y @ wv), float(x.astype(np.float64) @ bp)
     assert lhs == pytest.approx(rhs, rel=2e-5)
+
+
+def test_scatter_model_arguments_are_checked():
+    """The learned models need a network and at most three lines; unknown
+    models are refused; a refused call leaves the handle's model unchanged."""
+    sc, ph, orc, gpu, ev, dev = _model()
+    s = lm.Surrogate(0)
+    lib = _native.load()
+    for model in (_native.SCATTER_SURROGATE, _native.SCATTER_SURROGATE_COARSE):
+        assert lib.lm_set_scatter_model(gpu._h, model, None) == -1
+    assert lib.lm_set_scatter_model(gpu._h, 7, s._s) == -1
+    four = preset("small_16").with_(line_keV=(82.0, 154.0, 270.0, 300.0),
+                                    yields=(0.4, 0.2, 0.2, 0.2))
+    g4 = lm.Model.from_scenario(four, four.make_phantom().rho)
+    for name in ("surrogate", "surrogate_coarse"):
+        with pytest.raises(lm.LmmewError):
+            g4.set_scatter_model(name, s)
+    g4.close()
+    # the handle still runs the exact model
+    x = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    y = gpu.forward(dev, x).cpu().numpy().astype(np.float64)
+    idx = np.arange(0, len(ev), 37)
+    ref = orc.forward(ev.subset(idx), (ph.rho.reshape(-1) > 0).astype(np.float64))
+    assert float(np.max(np.abs(y[idx] - ref) / ref)) < 1e-5
+    s.close()

@@ -670,6 +670,14 @@ def run_comparison_form(noise_realisations=16, events=10_000, seed=21):
                      "enrmse": [float(v) for v in r["enrmse"]],
                      "bias": [float(v) for v in r["bias"]],
                      "std": [float(v) for v in r["std"]]}
+    # the other signal-to-background ratios of the study (ENRMSE per lesion)
+    from synthetic.phantom import paper_study_phantom
+    out["sbr_sweep_enrmse"] = {}
+    for sbr in (2.0, 6.0):
+        rs = studies.run_study(sc.with_(phantom=paper_study_phantom(sbr)), noise_realisations,
+                               events, seed=seed)
+        out["sbr_sweep_enrmse"][f"{sbr:g}:1"] = {name: [float(v) for v in r["enrmse"]]
+                                                 for name, r in rs.items()}
     return out
 
 

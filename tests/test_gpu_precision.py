@@ -62,3 +62,37 @@ def test_reduced_precision_errors(name):
     if out:
         with open(os.path.join(out, f"precision_{name}.json"), "w") as f:
             json.dump(report, f)
+
+
+def test_reduced_precision_forward_full_size_128():
+    """The precision form's workload (128 x 128, 120 angles, 1 M events):
+    forward projections of FP32, FP16 and BF16 scatter sums on events sampled
+    from spread-out angles, against the FP64 oracle event by event."""
+    from synthetic import simulate_cached
+    sc = preset("lmmew_128")
+    ph = sc.make_phantom()
+    ev = simulate_cached(sc)
+    gpu = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    rng = np.random.default_rng(12)
+    lam = (rng.uniform(0.2, 3.0, ph.rho.size) * (ph.rho.reshape(-1) > 0)).astype(np.float32)
+    idx = []
+    for a in rng.choice(sc.n_angles, size=3, replace=False):
+        cand = np.nonzero(ev.angle == a)[0]
+        idx.extend(rng.choice(cand, size=3, replace=False).tolist())
+    idx = np.array(sorted(idx))
+    ref = oracle.Model.from_scenario(sc, ph.rho).forward(ev.subset(idx), lam.astype(np.float64))
+    bounds = {"fp32": 1e-5, "fp16": BOUNDS["fp16"]["fwd_max"], "bf16": BOUNDS["bf16"]["fwd_max"]}
+    report = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        gpu.set_scatter_precision(prec)
+        y = gpu.forward(dev, torch.from_numpy(lam).cuda()).cpu().numpy().astype(np.float64)
+        rel = np.abs(y[idx] - ref) / ref
+        report[prec] = float(rel.max())
+        assert rel.max() < bounds[prec], report
+    gpu.set_scatter_precision("fp32")
+    gpu.close()
+    out = os.environ.get("LMMEW_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "precision_lmmew_128_sampled.json"), "w") as f:
+            json.dump(report, f)

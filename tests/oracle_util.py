@@ -54,3 +54,27 @@ def events_of(angle, bin_, energy) -> synthetic.EventList:
                                np.asarray(energy, dtype=np.float32),
                                np.zeros(k, np.int32), np.zeros(k, np.uint8),
                                np.zeros(k, bool))
+
+
+def coarse_interpolation(pix, n):
+    """[nq][nq] interpolation of the coarse-grid surrogate, restated from its
+    definition: voxel (ix, iy) takes the bilinear weights of the corners
+    (ix - ix % 2, iy - iy % 2) .. (+2, +2) that lie in the support,
+    renormalised to sum 1; with no such corner it is its own node."""
+    q_of = {int(p): q for q, p in enumerate(pix)}
+    M = np.zeros((len(pix), len(pix)))
+    for q, p in enumerate(pix):
+        ix, iy = int(p) % n, int(p) // n
+        x0, y0 = ix - ix % 2, iy - iy % 2
+        tx, ty = (ix - x0) / 2.0, (iy - y0) / 2.0
+        corners = [(x0, y0, (1 - tx) * (1 - ty)), (x0 + 2, y0, tx * (1 - ty)),
+                   (x0, y0 + 2, (1 - tx) * ty), (x0 + 2, y0 + 2, tx * ty)]
+        keep = [(q_of[cy * n + cx], w) for cx, cy, w in corners
+                if w > 0 and cx < n and cy < n and (cy * n + cx) in q_of]
+        if not keep:
+            M[q, q] = 1.0
+        else:
+            tot = sum(w for _, w in keep)
+            for qq, w in keep:
+                M[q, qq] += w / tot
+    return M

@@ -35,6 +35,7 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 import paper_2305_17111_gb300 as lm  # noqa: E402
 from paper_2305_17111_gb300 import _native  # noqa: E402
+from oracle_util import coarse_interpolation  # noqa: E402
 from oracle import mlp as omlp  # noqa: E402
 from synthetic import preset, simulate  # noqa: E402
 
@@ -374,30 +375,6 @@ def test_surrogate_fit_on_held_out_samples():
     assert mass_err < 0.35, mass_err
 
 
-def _coarse_interpolation(pix, n):
-    """[nq][nq] interpolation of the coarse-grid surrogate, restated from its
-    definition: voxel (ix, iy) takes the bilinear weights of the corners
-    (ix - ix % 2, iy - iy % 2) .. (+2, +2) that lie in the support,
-    renormalised to sum 1; with no such corner it is its own node."""
-    q_of = {int(p): q for q, p in enumerate(pix)}
-    M = np.zeros((len(pix), len(pix)))
-    for q, p in enumerate(pix):
-        ix, iy = int(p) % n, int(p) // n
-        x0, y0 = ix - ix % 2, iy - iy % 2
-        tx, ty = (ix - x0) / 2.0, (iy - y0) / 2.0
-        corners = [(x0, y0, (1 - tx) * (1 - ty)), (x0 + 2, y0, tx * (1 - ty)),
-                   (x0, y0 + 2, (1 - tx) * ty), (x0 + 2, y0 + 2, tx * ty)]
-        keep = [(q_of[cy * n + cx], w) for cx, cy, w in corners
-                if w > 0 and cx < n and cy < n and (cy * n + cx) in q_of]
-        if not keep:
-            M[q, q] = 1.0
-        else:
-            tot = sum(w for _, w in keep)
-            for qq, w in keep:
-                M[q, qq] += w / tot
-    return M
-
-
 @pytest.mark.parametrize("model", ["surrogate", "surrogate_coarse"])
 def test_surrogate_rows_match_primary_plus_oracle_network(model):
     sc, ph, orc, gpu, ev, dev = _fine_model()
@@ -412,7 +389,7 @@ def test_surrogate_rows_match_primary_plus_oracle_network(model):
     finally:
         gpu.set_scatter_model("exact")
     lam_q = lam.astype(np.float64)[orc.voxel_pixels]
-    interp = (_coarse_interpolation(orc.voxel_pixels, sc.n) if model == "surrogate_coarse"
+    interp = (coarse_interpolation(orc.voxel_pixels, sc.n) if model == "surrogate_coarse"
               else None)
     W = len(sc.line_keV)
     checked = 0

@@ -1,10 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the LM-MEW OSEM hot path on GB300.
 
-One step = one full LM-OSEM iteration (every subset: event sort, system-matrix
-rows computed on the fly, forward projection, ratio, back projection, update)
-over the 64x64 study-scale workload (300k events, 60 angles, 64 bins, 64x64
-scatter grid, 3 emission lines, 8 subsets), through the C ABI.
+One step = one full LM-OSEM iteration (every subset: system-matrix rows
+computed on the fly, forward projection, ratio, back projection, update) over
+the 64x64 study-scale workload (300k events, 60 angles, 64 bins, 64x64
+scatter grid, 3 emission lines, 8 subsets), through the C ABI.  The K timed
+steps are K iterations of one lm_osem call (the events are sorted once per
+call); the end-to-end measure makes one call per step, with that step's host
+copies.
 
 Metric: system-matrix elements per second (events x support voxels per
 step / step time), plus seconds per OSEM iteration.  With --gpus N under

@@ -178,7 +178,10 @@ int lm_forward(lm_handle* h, const lm_events* events, const float* image, float*
  * before reading it): calls that overlap on the GPU -- two streams, two host
  * threads, or a call queued before an earlier one finished on another
  * stream -- race, so serialise them.  Arguments and errors as lm_forward;
- * the caller still provides events, image and output. */
+ * the caller still provides events, image and output.  It runs the exact and
+ * the scatter-free models; the surrogate models keep a row block of the
+ * whole event list, so with them it returns LMMEW_ERR_NOT_IMPLEMENTED (use
+ * lm_forward). */
 int lm_forward_noalloc(lm_handle* h, const lm_events* events, const float* image, float* out_y,
                        lm_stream stream);
 

@@ -56,6 +56,21 @@ __device__ __forceinline__ double window_mass(const ModelConst& m, double e) {
     return window_mass(m, e, sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e));
 }
 
+// The same window mass in FP32 (a per-term probability of the sensitivity;
+// the sensitivity itself is accumulated in FP64).
+__device__ __forceinline__ float gauss_mass_f(float lo, float hi, float mean, float sigma) {
+    const float inv = 1.0f / (1.41421356f * sigma);
+    const float a = (lo - mean) * inv, b = (hi - mean) * inv;
+    if (a >= 0.f) return 0.5f * (erfcf(a) - erfcf(b));
+    if (b <= 0.f) return 0.5f * (erfcf(-b) - erfcf(-a));
+    return 0.5f * (erff(b) - erff(a));
+}
+__device__ __forceinline__ float window_mass_f(const ModelConst& m, float e, float s) {
+    float t = 0.f;
+    for (int k = 0; k < m.n_win; ++k) t += gauss_mass_f((float)m.win_lo[k], (float)m.win_hi[k], e, s);
+    return t;
+}
+
 // Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E.
 __device__ __forceinline__ double kn_shape(double e, double c) {
     const double r = 1.0 / (1.0 + (e / kMeC2) * (1.0 - c));
@@ -407,7 +422,8 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-log2(wgt)) : kPosHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
             base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
-            if (path > 0.0) sens += m.alpha[w] * path * od * window_mass(m, e1, sg);
+            if (path > 0.0)
+                sens += m.alpha[w] * path * od * (double)window_mass_f(m, (float)e1, (float)sg);
         }
     }
     for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);

@@ -65,7 +65,8 @@ def test_sensitivity_full_size_128():
     s = 5
     got = gpu.sensitivity(s).cpu().numpy()
     ref = orc.sensitivity(s, sc.n_subsets)
-    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=0)
+    # FP64 accumulation of terms whose window masses are FP32 (R29)
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=0)
 
 
 def test_osem_full_size_invariants_64():

@@ -2,7 +2,8 @@
 
 Tolerances: forward projections within a relative 1e-5 per event, the image
 after the stated OSEM iterations within a relative L2 of 1e-4, sensitivities
-(FP64 on both sides) within 1e-9, back projections within 1e-5 per voxel.
+(accumulated in FP64; the scatter paths' window masses in FP32) within 2e-6,
+back projections within 1e-5 per voxel.
 Cases span several 32-voxel and 32-point tiles and 128-event tiles with
 ragged tails, one to three energy windows and the scatter-free model.
 """
@@ -20,7 +21,7 @@ from synthetic import preset, simulate  # noqa: E402
 
 FWD_RTOL = 1e-5
 IMG_RL2 = 1e-4
-SENS_RTOL = 1e-9
+SENS_RTOL = 2e-6   # FP64 accumulation of terms whose window masses are FP32 (R29)
 
 CASES = ["tiny_8", "small_16", "small_24", "small_32_4w", "noscatter_16", "lmmew_32"]
 

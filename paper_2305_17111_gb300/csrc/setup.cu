@@ -27,10 +27,13 @@ __device__ __forceinline__ double mu_water(const ModelConst& m, double e) {
     return m.knot_mu[s] + t * (m.knot_mu[s + 1] - m.knot_mu[s]);
 }
 
-// sigma of the energy response: FWHM = frac * E * (E / E_ref)^expo
+// sigma of the energy response: FWHM = frac * E * (E / E_ref)^expo.  For the
+// usual expo = -1/2 this is frac * sqrt(E * E_ref): a square root instead of
+// an FP64 power (the same value to rounding).
 __host__ __device__ __forceinline__ double sigma_energy(double frac, double e_ref, double expo,
                                                         double e) {
-    return frac * e * pow(e / e_ref, expo) / (2.0 * sqrt(2.0 * log(2.0)));
+    const double fwhm = expo == -0.5 ? frac * sqrt(e * e_ref) : frac * e * pow(e / e_ref, expo);
+    return fwhm / (2.0 * sqrt(2.0 * log(2.0)));
 }
 
 __device__ __forceinline__ double sigma_coll(const ModelConst& m, double depth) {

@@ -236,7 +236,10 @@ int lm_set_scatter_precision(lm_handle* h, int precision);
  * events: HOST array of n_real lm_events (device pointers inside); images:
  * DEVICE float[n_real][n*n], lambda^0 in, lambda out; loglik: NULL or DEVICE
  * double[n_real][n_iters*n_subsets].  Every realisation's result equals
- * lm_osem's on its own events bit for bit.  Errors: as lm_osem. */
+ * lm_osem's on its own events bit for bit while each subset's events (all
+ * realisations together) fit one row block; beyond that the back
+ * projection's event chunks break at row-block edges and results agree to
+ * FP32 rounding.  Errors: as lm_osem. */
 int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subsets, int n_iters,
                   float* images, double* loglik, lm_stream stream);
 

@@ -53,7 +53,7 @@ def parse_args():
                     help="skip the forms section (precision, batching, comparison, surrogate, combined)")
     ap.add_argument("--forms", default="precision,batching,comparison,surrogate,combined",
                     help="comma-separated forms to measure")
-    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train"],
+    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train", "surrogate_coarse_osem"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
     return ap.parse_args()
 
@@ -877,6 +877,47 @@ def run_surrogate_rows_case(n_events=20_000, repeats=3):
     return 0
 
 
+def run_surrogate_coarse_osem_case(n_events=200_000, repeats=2):
+    """Small case for the launch list of the coarse-grid surrogate form: the
+    128 x 128 object, 200 000 MC events, OSEM iterations of 8 subsets with
+    the surrogate evaluated on the half-resolution node grid (untrained
+    weights: the work does not depend on them).  One untimed iteration tunes
+    the row kernel; then `repeats` iterations are timed one by one.  Prints
+    one JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate
+    sc = preset("lmmew_128")
+    ph = sc.make_phantom()
+    ev = simulate(sc, n_events=n_events, seed=3)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    dev = lm.DeviceEvents.from_list(ev)
+    sur = lm.Surrogate(1)
+    model.set_scatter_model("surrogate_coarse", sur)
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+    img = lam0.clone()
+    model.osem(dev, img, sc.n_subsets, 1)
+    times = []
+    for _ in range(repeats):
+        img.copy_(lam0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        model.osem(dev, img, sc.n_subsets, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": "surrogate_coarse_osem", "events": len(ev), "voxels": model.nq,
+                      "subsets": sc.n_subsets, "ms_per_iter": times}), flush=True)
+    model.set_scatter_model("exact")
+    sur.close()
+    model.close()
+    return 0
+
+
 def run_surrogate_train_case(steps=10, batch=16_384, n=200_000):
     """Small case for profiling one surrogate training step: Adam on
     minibatches of 16 384 of 200 000 random inputs (2 warm-up steps, then
@@ -910,6 +951,8 @@ def main():
         return run_surrogate_rows_case()
     if args.case == "surrogate_train":
         return run_surrogate_train_case()
+    if args.case == "surrogate_coarse_osem":
+        return run_surrogate_coarse_osem_case()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_gpu(args, rank, local_rank, world)

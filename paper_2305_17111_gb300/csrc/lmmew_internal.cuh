@@ -294,6 +294,16 @@ constexpr float kElectronRestKeV = 510.99895f;
 // 8 rho line integrals of the voxel at this angle.  Four threads can build
 // one sample's inputs side by side; surrogate_features calls this for all j,
 // so every kernel computes the same values.
+// Division in the network's input features: the fast approximate form on the
+// device (about 2 ulp; the inputs are rounded to BF16 afterwards), IEEE on the
+// host.
+__host__ __device__ __forceinline__ float feature_div(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
 __host__ __device__ __forceinline__ void surrogate_features_chunk(
     int j, float xq, float yq, float ca, float sa, float ub, float e_hat, int w, float e_line,
     float mu_w, const float* g8, const float* rho, int n, float h, float* f8) {
@@ -315,11 +325,11 @@ __host__ __device__ __forceinline__ void surrogate_features_chunk(
     }
     const float uq = -xq * sa + yq * ca, tq = xq * ca + yq * sa;
     const float du = ub - uq;
-    const float kappa = kElectronRestKeV * (1.f / e_hat - 1.f / e_line);
+    const float kappa = kElectronRestKeV * (feature_div(1.f, e_hat) - feature_div(1.f, e_line));
     const float c = fminf(fmaxf(1.f - kappa, -1.f), 1.f);
     const float s = fmaxf(sqrtf(fmaxf(1.f - c * c, 0.f)), 0.05f);
     const float lim = n * h;
-    const float dt = fminf(fmaxf(fabsf(du) * c / s, -lim), lim);
+    const float dt = fminf(fmaxf(feature_div(fabsf(du) * c, s), -lim), lim);
     const float tp = tq + dt;
     const float xp = tp * ca - ub * sa, yp = tp * sa + ub * ca;
     if (j == 2) {
@@ -327,7 +337,7 @@ __host__ __device__ __forceinline__ void surrogate_features_chunk(
         f8[1] = du * 0.2f;
         f8[2] = tq * 0.05f;
         f8[3] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
-        f8[4] = e_hat / e_line;
+        f8[4] = feature_div(e_hat, e_line);
         f8[5] = fabsf(du) * 0.2f;
         f8[6] = xp * 0.05f;
         f8[7] = yp * 0.05f;
@@ -336,9 +346,9 @@ __host__ __device__ __forceinline__ void surrogate_features_chunk(
     const float r = sqrtf(dt * dt + du * du);
     f8[0] = r * 0.05f;
     f8[1] = c;
-    f8[2] = h / (r + h);
+    f8[2] = feature_div(h, r + h);
     f8[3] = kappa < 0.f ? 1.f : 0.f;
-    const float gx = floorf(xp / h + 0.5f * n), gy = floorf(yp / h + 0.5f * n);
+    const float gx = floorf(feature_div(xp, h) + 0.5f * n), gy = floorf(feature_div(yp, h) + 0.5f * n);
     f8[4] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n) ? rho[(int)gy * n + (int)gx]
                                                                        : 0.f;
     f8[5] = f8[6] = f8[7] = 0.f;

@@ -500,7 +500,7 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
     const int lq = G.gt >> 5;
     const int row = G.gt;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
-    float sacc = 0.f;
+    f32x2 sacc2 = pk(0.f, 0.f);   // output layer: even and odd columns
     for (int layer = 0; layer < 3; ++layer) {
         if (G.gt == 0) {
             tc_fence_after();
@@ -574,13 +574,8 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                         zp[0] = __floats2bfloat162_rn(a0, a1);
                         zp[1] = __floats2bfloat162_rn(a2, a3);
                     }
-                    float h0, h1, h2, h3;
-                    upk(gelu2_doubled(z0), h0, h1);
-                    upk(gelu2_doubled(z1), h2, h3);
-                    sacc = fmaf(h0, ww.x, sacc);
-                    sacc = fmaf(h1, ww.y, sacc);
-                    sacc = fmaf(h2, ww.z, sacc);
-                    sacc = fmaf(h3, ww.w, sacc);
+                    sacc2 = fma2(gelu2_doubled(z0), pk(ww.x, ww.y), sacc2);
+                    sacc2 = fma2(gelu2_doubled(z1), pk(ww.z, ww.w), sacc2);
                 }
             }
         }
@@ -588,7 +583,9 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
         tc_fence_before();
         group_sync(G.g);
     }
-    *out_row = sacc + b4;
+    float s_even, s_odd;
+    upk(sacc2, s_even, s_odd);
+    *out_row = (s_even + s_odd) + b4;
     return true;
 }
 

@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -179,14 +180,42 @@ class OracleSample:
         return len(sub) * self.orc.nq, dt
 
 
+def host_cpu_model():
+    """The host's core model as the kernel reports it (x86 'model name', or the
+    Arm implementer / part numbers), for the CPU baseline's record."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.processor() or "unknown"
+    for line in info:
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")]
+    part = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")]
+    if impl and part:
+        return f"{platform.machine()} implementer {impl[0]} part {part[0]}"
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(sc, n_sample=None):
+    import oracle
     o = OracleSample(sc)
     if n_sample is None:
         n_sample = 400 if sc.n <= 64 else 60
     elems, dt = o.run(n_sample)
+    # the same oracle on one core, on a tenth of the sample
+    n_one = max(n_sample // 10, 1)
+    oracle.set_threads(1)
+    try:
+        elems1, dt1 = o.run(n_one, seed=1)
+    finally:
+        oracle.set_threads(o.cores)
     return {"value": elems / dt, "unit": UNIT, "cores": o.cores, "kind": "oracle",
             "sample": f"{n_sample} random events of {sc.name}: FP64 oracle row + forward "
-                      f"projection ({elems:.3e} elements in {dt:.1f} s)"}
+                      f"projection ({elems:.3e} elements in {dt:.1f} s)",
+            "value_1core": elems1 / dt1,
+            "sample_1core": f"{n_one} other random events, one thread ({dt1:.1f} s)",
+            "cpu_model": host_cpu_model()}
 
 
 def run_reference(args, rank, world):

@@ -108,6 +108,7 @@ def _load():
             "orc_sensitivity": (None, [_P, _I, _I, _PD]),
             "orc_osem": (None, [_P, _I64, _PU16, _PU16, _PF, _I, _I, _I, _I, _PD, _PD]),
             "orc_max_threads": (_I, []),
+            "orc_set_threads": (None, [_I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -123,6 +124,11 @@ def _ptr(a, ct):
 
 def max_threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the oracle's later calls from this thread."""
+    _load().orc_set_threads(int(n))
 
 
 def kn_shape(e_kev: float, cos_t: float) -> float:

@@ -757,3 +757,13 @@ int orc_max_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads of the calling thread's later parallel regions (for timing the
+ * oracle on one core and on all of them); ignored without OpenMP or n < 1. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

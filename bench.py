@@ -181,8 +181,16 @@ class OracleSample:
 
 
 def host_cpu_model():
-    """The host's core model as the kernel reports it (x86 'model name', or the
-    Arm implementer / part numbers), for the CPU baseline's record."""
+    """The host's core model (lscpu's 'Model name'; else /proc/cpuinfo's x86
+    'model name' or Arm implementer / part numbers), for the CPU baseline's
+    record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         info = open("/proc/cpuinfo").read().splitlines()
     except OSError:

@@ -105,3 +105,20 @@ def test_resume_continues_the_same_iteration(small):
     lam = _explicit_subiteration(m, ev, lam0, n_sub, 0)
     rest = m.osem(ev, lam, n_sub, 1, 0, 1)
     np.testing.assert_allclose(m.osem(ev, lam0, n_sub, 1), rest, rtol=1e-12, atol=0)
+
+
+def test_thread_count_changes_no_result(small):
+    """The CPU baseline times the oracle on one thread and on all of them:
+    the thread count is a timing control only.  The forward projection is
+    the same on one thread as on all, and the count is restored."""
+    sc, m, ev, lam0 = small
+    n_all = oracle.max_threads()
+    y_all = m.forward(ev, lam0)
+    oracle.set_threads(1)
+    try:
+        assert oracle.max_threads() == 1
+        y_one = m.forward(ev, lam0)
+    finally:
+        oracle.set_threads(n_all)
+    assert oracle.max_threads() == n_all
+    np.testing.assert_array_equal(y_one, y_all)

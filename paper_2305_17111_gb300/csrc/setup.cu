@@ -2,8 +2,11 @@
 // the density map (Eq. radpath), path sensitivities s(P, E_0^w) of Eq. (s_p)
 // for the unscattered and single-scatter paths of every (angle, voxel,
 // scatter point, line), the collimator tables and the per-angle sensitivity
-// image (denominator of Eq. os-lm-mlem).  Arithmetic is FP64; the tables the
-// hot kernel streams are rounded to FP32 at the end.
+// image (denominator of Eq. os-lm-mlem).  Arithmetic is FP64, and every sum
+// is accumulated in FP64; inside each scatter-path term the window masses,
+// the attenuation factor's 2^-fraction and the mantissa's log2 are FP32
+// (about 2e-7 relative per term).  The tables the hot kernel streams are
+// rounded to FP32 at the end.
 #include <math.h>
 
 #include <algorithm>
@@ -34,6 +37,31 @@ __host__ __device__ __forceinline__ double sigma_energy(double frac, double e_re
                                                         double e) {
     const double fwhm = expo == -0.5 ? frac * sqrt(e * e_ref) : frac * e * pow(e / e_ref, expo);
     return fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+}
+
+// 1 / sigma of the energy response; for expo = -1/2 one reciprocal square root.
+__device__ __forceinline__ double inv_sigma_energy(double frac, double e_ref, double expo,
+                                                   double e) {
+    constexpr double kFwhmToSigma = 2.3548200450309493;   // 2 sqrt(2 ln 2)
+    if (expo == -0.5) return rsqrt(e * e_ref) * (kFwhmToSigma / frac);
+    return 1.0 / sigma_energy(frac, e_ref, expo, e);
+}
+
+// 2^-t: t = n + f with n = floor(t) taken exactly in FP64, 2^-f of the
+// fraction in FP32, then scaled by 2^-n exactly.  Relative error about 2e-7
+// whatever the size of t; 0 once t >= 1000 (and for NaN).
+__device__ __forceinline__ double pow2_neg(double t) {
+    if (!(t < 1000.0)) return 0.0;
+    const double n = floor(t);
+    return ldexp((double)exp2f(-(float)(t - n)), -(int)n);
+}
+
+// log2 z for z > 0: z = mant * 2^e exactly (frexp), log2 of the mantissa in
+// FP32.  Absolute error about 1.5e-7.
+__device__ __forceinline__ double log2_pos(double z) {
+    int e;
+    const double mant = frexp(z, &e);
+    return (double)e + (double)log2f((float)mant);
 }
 
 __device__ __forceinline__ double sigma_coll(const ModelConst& m, double depth) {
@@ -74,11 +102,6 @@ __device__ __forceinline__ float window_mass_f(const ModelConst& m, float e, flo
     return t;
 }
 
-// Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E.
-__device__ __forceinline__ double kn_shape(double e, double c) {
-    const double r = 1.0 / (1.0 + (e / kMeC2) * (1.0 - c));
-    return r * r * (r + 1.0 / r - (1.0 - c * c));
-}
 
 // Integral over [0, 2 pi) of the KN shape, in closed form: with a = 1 + k,
 // b = k, D = a^2 - b^2, int dth/(a - b cos) = 2 pi / sqrt(D),
@@ -383,6 +406,8 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
     const int own_cell = (qy / m.f) * m.S + (qx / m.f);
     const double xq = qx + 0.5, yq = qy + 0.5;
     const int qt = q / kQT, ql = q % kQT;
+    double inv_kn[LMMEW_MAX_LINES];
+    for (int w = 0; w < m.W; ++w) inv_kn[w] = 1.0 / m.kn_norm[w];
     double sens = 0.0;
     for (int pc = 0; pc < m.npc; ++pc) {
         const int r = pc * kPC + lane;   // slot in this angle's point order
@@ -408,25 +433,38 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
         const double xp = ((cell % m.S) + 0.5) * m.f, yp = ((cell / m.S) + 0.5) * m.f;
         const size_t k = (size_t)q * m.np + p;
         const double d = d_qp[k];
-        const double ux = (xp - xq) * m.h / d, uy = (yp - yq) * m.h / d;
+        const double inv_d = 1.0 / d;
+        const double ux = (xp - xq) * m.h * inv_d, uy = (yp - yq) * m.h * inv_d;
         const double cos_t = ux * c + uy * s;
         const double od = on_det[(size_t)a * m.np + p];
         const double gqp = g_qp[k], gp = g_p[(size_t)a * m.np + p];
-        const double inter = p_rho[p] * m.cell_area / (2.0 * kPi * d);
+        // rho_p A_p / (2 pi d) times the 2 pi of the in-plane KN density
+        const double inter = p_rho[p] * m.cell_area * inv_d;
         for (int w = 0; w < m.W; ++w) {
+            // s(P) = 2^-att * pre: att the attenuation of both legs in bits,
+            // pre the scatter density, the KN weight and the geometry
             const double e0 = m.line_e[w];
-            const double e1 = e0 / (1.0 + (e0 / kMeC2) * (1.0 - cos_t));
+            const double den = 1.0 + (e0 / kMeC2) * (1.0 - cos_t);   // E_w / E'
+            const double r = 1.0 / den;
+            const double e1 = e0 * r;
             const double mu0 = mu_line[w], mu1 = mu_water(m, e1);
-            const double path = exp(-mu0 * gqp - mu1 * gp) * inter * mu0 * 2.0 * kPi *
-                                kn_shape(e0, cos_t) / m.kn_norm[w];
-            const double sg = sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
-            const double wgt = m.alpha[w] * path / (sqrt(2.0 * kPi) * sg);
-            const double sr = sqrt(0.5 * kLog2e) / sg;
-            base[((0 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-log2(wgt)) : kPosHuge;
+            // Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E_w
+            const double kn = r * r * (r + den - (1.0 - cos_t * cos_t));
+            const double att = (mu0 * gqp + mu1 * gp) * kLog2e;
+            const double pre = inter * mu0 * kn * inv_kn[w];
+            const double path = pow2_neg(att) * pre;
+            const double inv_sg = inv_sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
+            const double pref = m.alpha[w] * inv_sg * (1.0 / sqrt(2.0 * kPi));
+            const double wgt = pref * path;
+            const double sr = sqrt(0.5 * kLog2e) * inv_sg;
+            // -log2(wgt) = att - log2(pref pre), without forming 2^-att
+            base[((0 * m.W + w) * kQT + ql) * kPC + lane] =
+                wgt > 0.0 ? (float)(att - log2_pos(pref * pre)) : kPosHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
             base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
             if (path > 0.0)
-                sens += m.alpha[w] * path * od * (double)window_mass_f(m, (float)e1, (float)sg);
+                sens += m.alpha[w] * path * od *
+                        (double)window_mass_f(m, (float)e1, 1.0f / (float)inv_sg);
         }
     }
     for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);

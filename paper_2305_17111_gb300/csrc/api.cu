@@ -323,6 +323,10 @@ int lm_create(const lm_geometry* g, const lm_attenuation* at, const lm_lines* ln
         m.knot_e[i] = at->knot_keV[i];
         m.knot_mu[i] = at->mu_water_cm[i];
     }
+    for (int i = 0; i < LMMEW_MAX_KNOTS; ++i)
+        m.knot_slope[i] = i + 1 < m.n_knots
+                              ? (m.knot_mu[i + 1] - m.knot_mu[i]) / (m.knot_e[i + 1] - m.knot_e[i])
+                              : 0.0;
     h->n_subsets_default = n_subsets;
     int rc = build_tables(h, at->rho, support);
     if (rc == LMMEW_OK &&

@@ -45,6 +45,7 @@ struct ModelConst {
     double line_e[LMMEW_MAX_LINES], alpha[LMMEW_MAX_LINES], kn_norm[LMMEW_MAX_LINES];
     double win_lo[LMMEW_MAX_WINDOWS], win_hi[LMMEW_MAX_WINDOWS];
     double knot_e[LMMEW_MAX_KNOTS], knot_mu[LMMEW_MAX_KNOTS];
+    double knot_slope[LMMEW_MAX_KNOTS];   // (mu[s+1] - mu[s]) / (e[s+1] - e[s])
 };
 
 // Per-line FP32 constants of the energy response used by the hot kernel.

@@ -26,8 +26,7 @@ __device__ __forceinline__ double mu_water(const ModelConst& m, double e) {
     if (m.n_knots == 1) return m.knot_mu[0];
     int s = 0;
     while (s < m.n_knots - 2 && e >= m.knot_e[s + 1]) ++s;
-    const double t = (e - m.knot_e[s]) / (m.knot_e[s + 1] - m.knot_e[s]);
-    return m.knot_mu[s] + t * (m.knot_mu[s + 1] - m.knot_mu[s]);
+    return m.knot_mu[s] + (e - m.knot_e[s]) * m.knot_slope[s];
 }
 
 // sigma of the energy response: FWHM = frac * E * (E / E_ref)^expo.  For the

@@ -54,7 +54,7 @@ def parse_args():
                     help="skip the forms section (precision, batching, comparison, surrogate, combined)")
     ap.add_argument("--forms", default="precision,batching,comparison,surrogate,combined",
                     help="comma-separated forms to measure")
-    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train", "surrogate_coarse_osem"],
+    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train", "surrogate_coarse_osem", "setup"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
     return ap.parse_args()
 
@@ -955,6 +955,22 @@ def run_surrogate_coarse_osem_case(n_events=200_000, repeats=2):
     return 0
 
 
+def run_setup_case(workload, repeats=2):
+    """Small case for profiling the set-up kernels: `lm_create` of the named
+    workload's model `repeats` times (no events).  Prints one JSON line."""
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    times = []
+    for _ in range(repeats):
+        model = lm.Model.from_scenario(sc, ph.rho)
+        times.append(model.setup_ms)
+        model.close()
+    print(json.dumps({"case": "setup", "workload": workload, "setup_ms": times}), flush=True)
+    return 0
+
+
 def run_surrogate_train_case(steps=10, batch=16_384, n=200_000):
     """Small case for profiling one surrogate training step: Adam on
     minibatches of 16 384 of 200 000 random inputs (2 warm-up steps, then
@@ -990,6 +1006,8 @@ def main():
         return run_surrogate_train_case()
     if args.case == "surrogate_coarse_osem":
         return run_surrogate_coarse_osem_case()
+    if args.case == "setup":
+        return run_setup_case(args.workload)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_gpu(args, rank, local_rank, world)

@@ -55,12 +55,12 @@ __device__ __forceinline__ double pow2_neg(double t) {
     return ldexp((double)exp2f(-(float)(t - n)), -(int)n);
 }
 
-// log2 z for z > 0: z = mant * 2^e exactly (frexp), log2 of the mantissa in
-// FP32.  Absolute error about 1.5e-7.
-__device__ __forceinline__ double log2_pos(double z) {
+// log2 z for a positive FP32 z: z = mant * 2^e exactly (frexpf), log2 of
+// the mantissa in [0.5, 1).  Absolute error about 1e-7 whatever the size of z.
+__device__ __forceinline__ double log2_pos_f(float z) {
     int e;
-    const double mant = frexp(z, &e);
-    return (double)e + (double)log2f((float)mant);
+    const float mant = frexpf(z, &e);
+    return (double)e + (double)log2f(mant);
 }
 
 __device__ __forceinline__ double sigma_coll(const ModelConst& m, double depth) {
@@ -405,8 +405,13 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
     const int own_cell = (qy / m.f) * m.S + (qx / m.f);
     const double xq = qx + 0.5, yq = qy + 0.5;
     const int qt = q / kQT, ql = q % kQT;
-    double inv_kn[LMMEW_MAX_LINES];
-    for (int w = 0; w < m.W; ++w) inv_kn[w] = 1.0 / m.kn_norm[w];
+    // per line: 1 / (in-plane KN normaliser) and E_w / (m_e c^2)
+    float inv_kn[LMMEW_MAX_LINES];
+    double k0[LMMEW_MAX_LINES];
+    for (int w = 0; w < m.W; ++w) {
+        inv_kn[w] = (float)(1.0 / m.kn_norm[w]);
+        k0[w] = m.line_e[w] / kMeC2;
+    }
     double sens = 0.0;
     for (int pc = 0; pc < m.npc; ++pc) {
         const int r = pc * kPC + lane;   // slot in this angle's point order
@@ -438,27 +443,30 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
         const double od = on_det[(size_t)a * m.np + p];
         const double gqp = g_qp[k], gp = g_p[(size_t)a * m.np + p];
         // rho_p A_p / (2 pi d) times the 2 pi of the in-plane KN density
-        const double inter = p_rho[p] * m.cell_area * inv_d;
+        const float inter = (float)(p_rho[p] * m.cell_area * inv_d);
+        const float sin2 = (float)(1.0 - cos_t * cos_t);
         for (int w = 0; w < m.W; ++w) {
-            // s(P) = 2^-att * pre: att the attenuation of both legs in bits,
-            // pre the scatter density, the KN weight and the geometry
+            // s(P) = 2^-att * pre: att the attenuation of both legs in bits
+            // (FP64: it is exponentiated), pre the scatter density, the KN
+            // weight and the geometry (FP32 factors, ~2e-7 relative)
             const double e0 = m.line_e[w];
-            const double den = 1.0 + (e0 / kMeC2) * (1.0 - cos_t);   // E_w / E'
+            const double den = 1.0 + k0[w] * (1.0 - cos_t);   // E_w / E'
             const double r = 1.0 / den;
             const double e1 = e0 * r;
             const double mu0 = mu_line[w], mu1 = mu_water(m, e1);
             // Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E_w
-            const double kn = r * r * (r + den - (1.0 - cos_t * cos_t));
+            const float rf = (float)r;
+            const float kn = rf * rf * (rf + (float)den - sin2);
             const double att = (mu0 * gqp + mu1 * gp) * kLog2e;
-            const double pre = inter * mu0 * kn * inv_kn[w];
-            const double path = pow2_neg(att) * pre;
+            const float pre = inter * (float)mu0 * kn * inv_kn[w];
+            const double path = pow2_neg(att) * (double)pre;
             const double inv_sg = inv_sigma_energy(m.fwhm_frac, m.e_ref, m.expo, e1);
-            const double pref = m.alpha[w] * inv_sg * (1.0 / sqrt(2.0 * kPi));
-            const double wgt = pref * path;
+            const float pref = (float)(m.alpha[w] * inv_sg) * 0.3989422804f;   // / sqrt(2 pi)
+            const double wgt = (double)pref * path;
             const double sr = sqrt(0.5 * kLog2e) * inv_sg;
             // -log2(wgt) = att - log2(pref pre), without forming 2^-att
             base[((0 * m.W + w) * kQT + ql) * kPC + lane] =
-                wgt > 0.0 ? (float)(att - log2_pos(pref * pre)) : kPosHuge;
+                wgt > 0.0 ? (float)(att - log2_pos_f(pref * pre)) : kPosHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
             base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
             if (path > 0.0)

@@ -38,11 +38,25 @@ __host__ __device__ __forceinline__ double sigma_energy(double frac, double e_re
     return fwhm / (2.0 * sqrt(2.0 * log(2.0)));
 }
 
+// 1/x and 1/sqrt(x) for positive normal x well inside the FP32 range: the
+// FP32 estimate y refined by one Newton-Raphson step in FP64, for 1/x
+// y (2 - x y) and for 1/sqrt(x) y (3/2 - x y^2 / 2).  A relative error e of y
+// becomes about e^2 (1.5 e^2 for the square root), here ~1e-13: far below
+// the FP32 rounding of every table entry they feed.
+__device__ __forceinline__ double recip_nr(double x) {
+    const double y = (double)(1.0f / (float)x);
+    return y * fma(-x, y, 2.0);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    const double y = (double)rsqrtf((float)x);
+    return y * fma(-0.5 * x * y, y, 1.5);
+}
+
 // 1 / sigma of the energy response; for expo = -1/2 one reciprocal square root.
 __device__ __forceinline__ double inv_sigma_energy(double frac, double e_ref, double expo,
                                                    double e) {
     constexpr double kFwhmToSigma = 2.3548200450309493;   // 2 sqrt(2 ln 2)
-    if (expo == -0.5) return rsqrt(e * e_ref) * (kFwhmToSigma / frac);
+    if (expo == -0.5) return rsqrt_nr(e * e_ref) * (kFwhmToSigma / frac);
     return 1.0 / sigma_energy(frac, e_ref, expo, e);
 }
 
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
             // weight and the geometry (FP32 factors, ~2e-7 relative)
             const double e0 = m.line_e[w];
             const double den = 1.0 + k0[w] * (1.0 - cos_t);   // E_w / E'
-            const double r = 1.0 / den;
+            const double r = recip_nr(den);
             const double e1 = e0 * r;
             const double mu0 = mu_line[w], mu1 = mu_water(m, e1);
             // Klein-Nishina angular shape r^2 (r + 1/r - sin^2), r = E'/E_w

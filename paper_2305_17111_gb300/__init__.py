@@ -40,6 +40,22 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _require_cuda(t, name, dtype, numel=None, min_numel=None):
+    """Refuse a tensor the library would read or write through a raw device
+    pointer unless it is a contiguous CUDA tensor of the right type and size
+    (the C ABI cannot tell a host pointer or a short buffer from a good one)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, not {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, not {t.numel()}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} must have at least {min_numel} elements, not {t.numel()}")
+    return t
+
+
 def _fptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
@@ -152,8 +168,10 @@ class Model:
     def forward(self, events: DeviceEvents, image, out=None, stream=None):
         torch = _torch()
         image = image.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
+        _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
         if out is None:
             out = torch.empty(len(events), dtype=torch.float32, device="cuda")
+        _require_cuda(out, "out", torch.float32, numel=len(events))
         ev = events.struct()
         _native.check(_native.load().lm_forward(self._h, ctypes.byref(ev),
                                                 ctypes.c_void_p(image.data_ptr()),
@@ -164,6 +182,9 @@ class Model:
     def forward_noalloc(self, events: DeviceEvents, image, out, stream=None):
         """lm_forward_noalloc: same result as forward(), no device allocation
         inside the call (``image`` and ``out`` are caller-owned CUDA tensors)."""
+        torch = _torch()
+        _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
+        _require_cuda(out, "out", torch.float32, numel=len(events))
         ev = events.struct()
         _native.check(_native.load().lm_forward_noalloc(self._h, ctypes.byref(ev),
                                                         ctypes.c_void_p(image.data_ptr()),
@@ -174,8 +195,10 @@ class Model:
     def backproject(self, events: DeviceEvents, weight, out=None, stream=None):
         torch = _torch()
         weight = weight.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
+        _require_cuda(weight, "weight", torch.float32, numel=len(events))
         if out is None:
             out = torch.empty(self.n * self.n, dtype=torch.float32, device="cuda")
+        _require_cuda(out, "out", torch.float32, numel=self.n * self.n)
         ev = events.struct()
         _native.check(_native.load().lm_backproject(self._h, ctypes.byref(ev),
                                                     ctypes.c_void_p(weight.data_ptr()),
@@ -187,9 +210,10 @@ class Model:
              loglik=None, stream=None):
         """Run LM-OSEM in place on ``image`` (a float32 CUDA tensor of n*n)."""
         torch = _torch()
-        if not (isinstance(image, torch.Tensor) and image.is_cuda and image.dtype == torch.float32
-                and image.is_contiguous()):
-            raise TypeError("image must be a contiguous float32 CUDA tensor")
+        _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
+        if loglik is not None:
+            _require_cuda(loglik, "loglik", torch.float64,
+                          min_numel=max(int(n_iters), 0) * max(int(n_subsets), 0))
         ev = events.struct()
         llp = ctypes.c_void_p(loglik.data_ptr()) if loglik is not None else None
         _native.check(_native.load().lm_osem(self._h, ctypes.byref(ev), int(n_subsets),
@@ -203,9 +227,10 @@ class Model:
         [R, n*n] updated in place; ``events_list`` holds R DeviceEvents."""
         torch = _torch()
         R = len(events_list)
-        if not (isinstance(images, torch.Tensor) and images.is_cuda and images.is_contiguous()
-                and images.dtype == torch.float32 and images.numel() == R * self.n * self.n):
-            raise TypeError("images must be a contiguous float32 CUDA tensor of R*n*n values")
+        _require_cuda(images, "images", torch.float32, numel=R * self.n * self.n)
+        if loglik is not None:
+            _require_cuda(loglik, "loglik", torch.float64,
+                          min_numel=R * max(int(n_iters), 0) * max(int(n_subsets), 0))
         arr = (_native.Events * R)(*[e.struct() for e in events_list])
         llp = ctypes.c_void_p(loglik.data_ptr()) if loglik is not None else None
         _native.check(_native.load().lm_osem_batch(self._h, R, arr, int(n_subsets), int(n_iters),
@@ -280,6 +305,15 @@ class Surrogate:
         self._s = s
         self.n_params = int(lib.lm_surrogate_param_count())
 
+    def _check_inputs(self, x, target=None):
+        """x: [rows, 32] float32 CUDA rows; target: one float32 per row."""
+        torch = _torch()
+        _require_cuda(x, "x", torch.float32)
+        if x.dim() != 2 or x.shape[1] != self.N_IN:
+            raise ValueError(f"x must have shape [rows, {self.N_IN}], not {tuple(x.shape)}")
+        if target is not None:
+            _require_cuda(target, "target", torch.float32, numel=x.shape[0])
+
     def close(self):
         if getattr(self, "_s", None) is not None and self._s.value:
             _native.load().lm_surrogate_destroy(self._s)
@@ -305,6 +339,7 @@ class Surrogate:
     def forward(self, x, stream=None):
         torch = _torch()
         x = x.to(device="cuda", dtype=torch.float32).contiguous()
+        self._check_inputs(x)
         out = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
         _native.check(_native.load().lm_surrogate_forward(self._s, ctypes.c_void_p(x.data_ptr()),
                                                           int(x.shape[0]),
@@ -317,8 +352,10 @@ class Surrogate:
         torch = _torch()
         x = x.to(device="cuda", dtype=torch.float32).contiguous()
         target = target.to(device="cuda", dtype=torch.float32).contiguous()
+        self._check_inputs(x, target)
         if weight is not None:
             weight = weight.to(device="cuda", dtype=torch.float32).contiguous()
+            _require_cuda(weight, "weight", torch.float32, numel=x.shape[0])
         g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
         loss = ctypes.c_double()
         _native.check(_native.load().lm_surrogate_gradient(
@@ -336,6 +373,7 @@ class Surrogate:
         torch = _torch()
         x = x.to(device="cuda", dtype=torch.float32).contiguous()
         target = target.to(device="cuda", dtype=torch.float32).contiguous()
+        self._check_inputs(x, target)
         hist = np.zeros(int(steps), dtype=np.float64) if record_loss else None
         _native.check(_native.load().lm_surrogate_train(
             self._s, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),

@@ -266,6 +266,22 @@ int lm_batch_tuning(const lm_handle* h, double* out5);
  * depend on it.  Not part of the paper's method.  Errors: INVALID_ARG. */
 int lm_set_tile_events(lm_handle* h, int tile_events);
 
+/* Energy-window pruning of the single-scatter terms (on by default).  A
+ * photon of line w scattered once leaves with E' between its backscatter
+ * energy E_w / (1 + 2 E_w / m_e c^2) and E_w (Compton's relation, paper
+ * Sec. "Likelihood of list-mode data using path-based formalism"), and the
+ * detector blurs E' by the energy-resolution Gaussian sigma_E(E').  With
+ * pruning on, the events of every call are sorted by (angle, energy class,
+ * bin); a class is a range of recorded energies in which each line's reach
+ * [min (E' - 8 sigma_E(E')), max (E' + 8 sigma_E(E'))] is either wholly in
+ * or out, and the row kernel evaluates the single-scatter terms of the lines
+ * in reach only.  A skipped term's energy factor is below exp(-32) of its
+ * path's peak, so forward projections move by far less than FP32 rounding.
+ * enable = 0 evaluates every line for every event (one class).  Applies to
+ * the handle's later calls.  Not part of the paper's method.  Errors:
+ * INVALID_ARG. */
+int lm_set_energy_pruning(lm_handle* h, int enable);
+
 /* ---------------------------------------------------------------------
  * Learned surrogate of the single-scatter term (not in the paper: the
  * paper evaluates Eq. s_p with n = 1 exactly; this replaces that sum by a

@@ -248,6 +248,11 @@ class Model:
         """Events per row-kernel tile (32, 64 or 128) until the next autotune."""
         _native.check(_native.load().lm_set_tile_events(self._h, int(tile_events)))
 
+    def set_energy_pruning(self, enable: bool = True):
+        """Evaluate each event's single-scatter terms only for the lines whose
+        scatter can reach its recorded energy (default), or for every line."""
+        _native.check(_native.load().lm_set_energy_pruning(self._h, 1 if enable else 0))
+
     PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 
     def set_scatter_precision(self, precision="fp32"):

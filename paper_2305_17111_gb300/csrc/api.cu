@@ -61,20 +61,22 @@ int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
 // it skips.
 constexpr int64_t kTuneEvents = 16384;
 
-int autotune_row(lm_handle* h, SortedEvents& se, int first_groups, cudaStream_t st) {
+int autotune_row(lm_handle* h, SortedEvents& se, int first_ranks, cudaStream_t st) {
+    // whole angle ranks (each n_classes groups) of the first subset
+    const int C = se.n_classes;
     int g1 = 0, ng = 0;
     int64_t ev = 0;
-    while (g1 < first_groups && ev < kTuneEvents) {
-        const int64_t c = se.h_angle_start[g1 + 1] - se.h_angle_start[g1];
+    for (int r = 0; r < first_ranks && ev < kTuneEvents; ++r) {
+        const int64_t c = se.h_group_start[(r + 1) * C] - se.h_group_start[r * C];
         ev += c;
         ng += c > 0;
-        ++g1;
+        g1 = (r + 1) * C;
     }
     if (ev == 0) return recut_tiles(h, &se, h->tile_ev, st);
     int bucket = 0;
     while (bucket < 40 && (int64_t(2) << bucket) <= ev / ng) ++bucket;
     const uint64_t key = 1ull | ((uint64_t)bucket << 8) | ((uint64_t)h->scatter_model << 4) |
-                         ((uint64_t)h->prec << 2);
+                         ((uint64_t)h->prec << 2) | ((uint64_t)(h->n_classes > 1) << 1);
     // the class in use keeps the current shape (it may have been set by
     // lm_set_tile_events); a class tuned before gets its stored shape back
     if (h->tune_key == key) return recut_tiles(h, &se, h->tile_ev, st);
@@ -182,14 +184,14 @@ struct Chunk {
     int64_t e0, e1;     // sorted event range
 };
 
-// Split the tiles of angle ranks [r0, r1) into chunks of at most max_events events.
-std::vector<Chunk> plan_chunks(const SortedEvents& se, int r0, int r1, int64_t max_events) {
+// Split the tiles of groups [g0, g1) into chunks of at most max_events events.
+std::vector<Chunk> plan_chunks(const SortedEvents& se, int g0, int g1, int64_t max_events) {
     std::vector<Chunk> out;
     Chunk cur{-1, -1, 0, 0};
-    for (int r = r0; r < r1; ++r) {
+    for (int r = g0; r < g1; ++r) {
         for (int t = se.h_tile_start[r]; t < se.h_tile_start[r + 1]; ++t) {
-            const int64_t b = se.h_angle_start[r] + (int64_t)(t - se.h_tile_start[r]) * se.tile_ev;
-            const int64_t e = std::min<int64_t>(b + se.tile_ev, se.h_angle_start[r + 1]);
+            const int64_t b = se.h_group_start[r] + (int64_t)(t - se.h_tile_start[r]) * se.tile_ev;
+            const int64_t e = std::min<int64_t>(b + se.tile_ev, se.h_group_start[r + 1]);
             if (cur.t0 >= 0 && (e - cur.e0) > max_events) {
                 out.push_back(cur);
                 cur.t0 = -1;
@@ -329,6 +331,7 @@ int lm_create(const lm_geometry* g, const lm_attenuation* at, const lm_lines* ln
                               : 0.0;
     h->n_subsets_default = n_subsets;
     int rc = build_tables(h, at->rho, support);
+    if (rc == LMMEW_OK) build_energy_classes(h);
     if (rc == LMMEW_OK &&
         (cudaMalloc(&h->d_term_counter, sizeof(unsigned long long)) != cudaSuccess ||
          cudaMemset(h->d_term_counter, 0, sizeof(unsigned long long)) != cudaSuccess ||
@@ -429,7 +432,7 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     if (ev->n == 0) return LMMEW_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const ModelConst& m = h->mc;
-    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, sort_groups(h, m.A)), st);
     if (rc != LMMEW_OK) return rc;
     char* arena = (char*)h->scratch_sort.ptr;
     SortedEvents se;
@@ -442,7 +445,7 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     const int rs = row_stride_of(h);
     const int64_t max_ev =
         std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / (keep_rows ? rs : m.nqt)));
-    std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
+    std::vector<Chunk> chunks = plan_chunks(se, 0, se.n_groups, max_ev);
     int64_t biggest = 0;
     for (const Chunk& c : chunks) biggest = std::max(biggest, c.e1 - c.e0);
     rc = surrogate_prepare(h, biggest, st);
@@ -482,7 +485,7 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
         LMMEW_CUDA(cudaMemsetAsync(out_image, 0, sizeof(float) * m.n * m.n, st));
         return LMMEW_OK;
     }
-    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, sort_groups(h, m.A)), st);
     if (rc != LMMEW_OK) return rc;
     char* arena = (char*)h->scratch_sort.ptr;
     SortedEvents se;
@@ -490,7 +493,7 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
     if (rc != LMMEW_OK) return rc;
     const int rs = row_stride_of(h);
     const int64_t max_ev = std::max<int64_t>(kET, (int64_t)(kRowBudgetFloats / rs));
-    std::vector<Chunk> chunks = plan_chunks(se, 0, m.A, max_ev);
+    std::vector<Chunk> chunks = plan_chunks(se, 0, se.n_groups, max_ev);
     int64_t biggest = 0, parts = 0;
     for (const Chunk& c : chunks) {
         biggest = std::max(biggest, c.e1 - c.e0);
@@ -538,7 +541,7 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
     cudaStream_t st = (cudaStream_t)stream;
     rc = subset_sensitivity(h, n_subsets, st);
     if (rc != LMMEW_OK) return rc;
-    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, m.A), st);
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(ev->n, sort_groups(h, m.A)), st);
     if (rc != LMMEW_OK) return rc;
     char* arena = (char*)h->scratch_sort.ptr;
     SortedEvents se;
@@ -556,7 +559,7 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
         int r = 0;
         for (int s = 0; s < n_subsets; ++s) {
             const int cnt = (m.A - s + n_subsets - 1) / n_subsets;
-            plan[s] = plan_chunks(se, r, r + cnt, max_ev);
+            plan[s] = plan_chunks(se, r * se.n_classes, (r + cnt) * se.n_classes, max_ev);
             int64_t parts = 0;
             for (const Chunk& c : plan[s]) {
                 biggest = std::max(biggest, c.e1 - c.e0);
@@ -643,7 +646,7 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     }
     int rc = subset_sensitivity(h, n_subsets, st);
     if (rc != LMMEW_OK) return rc;
-    rc = ensure(h, h->scratch_sort, sort_batch_scratch_bytes(n_total, V, R), st);
+    rc = ensure(h, h->scratch_sort, sort_batch_scratch_bytes(n_total, V * h->n_classes, R), st);
     if (rc != LMMEW_OK) return rc;
     char* arena = (char*)h->scratch_sort.ptr;
     SortedEvents se;
@@ -661,9 +664,10 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     for (int s = 0; s < n_subsets; ++s) {
         blk_off[s] = (int)blocks.size();
         RowBlock cur{-1, -1, 0, 0, 0, 0};
-        for (int64_t v = (int64_t)s * A_s; v < (int64_t)(s + 1) * A_s; ++v) {
-            int64_t e = se.h_angle_start[v];
-            const int64_t e_end = se.h_angle_start[v + 1];
+        const int64_t C = se.n_classes;
+        for (int64_t v = (int64_t)s * A_s * C; v < (int64_t)(s + 1) * A_s * C; ++v) {
+            int64_t e = se.h_group_start[v];
+            const int64_t e_end = se.h_group_start[v + 1];
             int t = se.h_tile_start[v];
             for (; e < e_end; ++t) {
                 const int64_t cnt = std::min<int64_t>(se.tile_ev, e_end - e);
@@ -694,7 +698,8 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     // events / 128 plus one per (block, realisation) run.
     size_t max_chunks = 1, parts_max = 1;
     for (int s = 0; s < n_subsets; ++s) {
-        const int64_t ev_s = se.h_angle_start[(size_t)(s + 1) * A_s] - se.h_angle_start[(size_t)s * A_s];
+        const int64_t ev_s = se.h_group_start[(size_t)(s + 1) * A_s * se.n_classes] -
+                             se.h_group_start[(size_t)s * A_s * se.n_classes];
         const size_t c = (size_t)(ev_s / kBpChunkEvents) + (size_t)(blk_off[s + 1] - blk_off[s]) * R;
         max_chunks += c;
         parts_max = std::max(parts_max, c);
@@ -827,6 +832,13 @@ int lm_set_tile_events(lm_handle* h, int tile_events) {
     if (tile_events != 32 && tile_events != 64 && tile_events != kET)
         return set_error(LMMEW_ERR_INVALID_ARG, "tile_events must be 32, 64 or 128");
     h->tile_ev = tile_events;
+    return LMMEW_OK;
+}
+
+int lm_set_energy_pruning(lm_handle* h, int enable) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    h->prune_lines = enable ? 1 : 0;
+    build_energy_classes(h);
     return LMMEW_OK;
 }
 

@@ -1,17 +1,95 @@
 // Event validation and grouping (once per call that takes events): every
-// event is checked against the model, keyed by (subset rank of its angle, bin)
-// and stably sorted with an LSD radix sort written here (8-bit digits,
-// per-block histograms, one global scan, stable per-block scatter by warp
-// match).  The sorted order groups each angle's events contiguously, subsets
-// in ascending order (subset(a) = a mod n_subsets, paper Sec. LM-OSEM), and
-// cuts every angle's run into tiles of up to tile_ev events for the row kernel.
+// event is checked against the model, keyed by (subset rank of its angle,
+// energy class of its recorded energy, bin) and stably sorted with an LSD
+// radix sort written here (8-bit digits, per-block histograms, one global
+// scan, stable per-block scatter by warp match).  The sorted order groups each
+// angle's events contiguously, subsets in ascending order (subset(a) = a mod
+// n_subsets, paper Sec. LM-OSEM), inside an angle by energy class, and cuts
+// every (angle, class) run into tiles of up to tile_ev events for the row
+// kernel.  The class of a tile tells the row kernel which lines' single
+// scatter can reach its recorded energies.
+#include <math.h>
+
 #include <algorithm>
 #include <vector>
 
 #include "lmmew_internal.cuh"
 
 namespace lmmew {
+
+// Reach of each line's single scatter in recorded energy, and the classes
+// its ends cut the energy axis into (see EnergyClasses).  E' runs from the
+// backscatter energy to E_w; E' -+ k sigma_E(E') is scanned in FP64 on a fine
+// grid, widened by the largest change between neighbouring samples (the
+// extremum between two samples lies within that of the nearer one), and
+// rounded outward to FP32, the precision the recorded energies are compared
+// in.  Classes are off (one class, every line) without scatter points, with
+// more than 4 lines, when pruning is switched off, or when (angle rank,
+// class, bin) keys would not fit 32 bits.
+void build_energy_classes(lm_handle* h) {
+    const ModelConst& m = h->mc;
+    const int all = (1 << m.W) - 1;
+    h->ecls.n_bnd = 0;
+    h->n_classes = 1;
+    for (int c = 0; c < 2 * LMMEW_MAX_LINES + 1; ++c) h->class_lines[c] = all;
+    // the row kernels instantiate a stage per staged-line count up to 4 lines
+    if (!h->prune_lines || m.np == 0 || m.W > 4) return;
+    const double f2s = 1.0 / (2.0 * sqrt(2.0 * log(2.0)));
+    auto sigma = [&](double e) { return m.fwhm_frac * e * pow(e / m.e_ref, m.expo) * f2s; };
+    float lo[LMMEW_MAX_LINES], hi[LMMEW_MAX_LINES];
+    std::vector<float> bnd;
+    for (int w = 0; w < m.W; ++w) {
+        const double ew = m.line_e[w];
+        const double eb = ew / (1.0 + 2.0 * ew / 510.99895);
+        constexpr int kSteps = 4096;
+        double mn = 1e300, mx = -1e300, dl = 0.0, du = 0.0, pl = 0.0, pu = 0.0;
+        for (int k = 0; k <= kSteps; ++k) {
+            const double e = eb + (ew - eb) * k / kSteps;
+            const double s = kScatterReachSigmas * sigma(e);
+            const double l = e - s, u = e + s;
+            if (k > 0) {
+                dl = std::max(dl, fabs(l - pl));
+                du = std::max(du, fabs(u - pu));
+            }
+            pl = l;
+            pu = u;
+            mn = std::min(mn, l);
+            mx = std::max(mx, u);
+        }
+        lo[w] = nextafterf((float)(mn - dl), -INFINITY);
+        hi[w] = nextafterf((float)(mx + du), INFINITY);
+        bnd.push_back(lo[w]);
+        bnd.push_back(hi[w]);
+    }
+    std::sort(bnd.begin(), bnd.end());
+    bnd.erase(std::unique(bnd.begin(), bnd.end()), bnd.end());
+    const int C = (int)bnd.size() + 1;
+    // keys of the batched sort reach (2 A classes + 1) bins
+    if ((2ull * (uint64_t)m.A * C + 1ull) * (uint64_t)m.B >= (1ull << 32)) return;
+    h->ecls.n_bnd = (int)bnd.size();
+    for (int k = 0; k < h->ecls.n_bnd; ++k) h->ecls.bnd[k] = bnd[k];
+    h->n_classes = C;
+    for (int c = 0; c < C; ++c) {
+        // class c: bnd[c - 1] <= E_hat < bnd[c]; line w covers it or misses it
+        int mask = 0;
+        for (int w = 0; w < m.W; ++w) {
+            const bool left_in = c > 0 && lo[w] <= bnd[c - 1];
+            const bool right_in = c < C - 1 && bnd[c] <= hi[w];
+            if (left_in && right_in) mask |= 1 << w;
+        }
+        h->class_lines[c] = mask;
+    }
+}
+
+int sort_groups(const lm_handle* h, int A) { return A * h->n_classes; }
+
 namespace {
+
+__device__ __forceinline__ uint32_t energy_class(const EnergyClasses& ec, float e) {
+    uint32_t c = 0;
+    for (int k = 0; k < ec.n_bnd; ++k) c += ec.bnd[k] <= e ? 1u : 0u;
+    return c;
+}
 
 constexpr int kSortThreads = 256;
 constexpr int kSortPerThread = 16;
@@ -19,8 +97,8 @@ constexpr int kSortChunk = kSortThreads * kSortPerThread;   // keys per block
 
 __global__ void k_keys(const uint16_t* angle, const uint16_t* bin, const float* energy, int64_t n,
                        int A, int B, const int* rank_of_angle, int n_win,
-                       float4 win01, float4 win23, float4 win45, float4 win67, uint32_t* keys,
-                       uint32_t* vals, int* status) {
+                       float4 win01, float4 win23, float4 win45, float4 win67,
+                       const EnergyClasses ec, uint32_t* keys, uint32_t* vals, int* status) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int a = angle[j], b = bin[j];
@@ -30,7 +108,9 @@ __global__ void k_keys(const uint16_t* angle, const uint16_t* bin, const float* 
     bool inwin = false;
     for (int k = 0; k < n_win; ++k) inwin |= (e >= lo[k] && e < hi[k]);
     const bool ok = a < A && b < B && isfinite(e) && inwin;
-    keys[j] = ok ? (uint32_t)rank_of_angle[a] * (uint32_t)B + (uint32_t)b : (uint32_t)A * (uint32_t)B;
+    const uint32_t C = (uint32_t)ec.n_bnd + 1u;
+    keys[j] = ok ? ((uint32_t)rank_of_angle[a] * C + energy_class(ec, e)) * (uint32_t)B + (uint32_t)b
+                 : (uint32_t)A * C * (uint32_t)B;
     vals[j] = (uint32_t)j;
     if (!ok) atomicOr(status, kStatusOutOfRange);
 }
@@ -165,7 +245,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int
 }
 
 __global__ void k_tiles(const int* start, const int* tile_start, const int* angle_of_rank, int A,
-                        int tile_ev, const uint16_t* bin_s, Tile* tiles,
+                        int tile_ev, const uint16_t* bin_s, const int* lines_of_group, Tile* tiles,
                         const int* real_of_rank = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A) return;
@@ -179,6 +259,7 @@ __global__ void k_tiles(const int* start, const int* tile_start, const int* angl
         T.count = cnt;
         T.b_lo_hi = ((int)bin_s[e] << 16) | (int)bin_s[e + cnt - 1];
         T.r = real_of_rank ? real_of_rank[r] : 0;
+        T.lines = lines_of_group[r];
         tiles[t] = T;
     }
 }
@@ -186,30 +267,121 @@ __global__ void k_tiles(const int* start, const int* tile_start, const int* angl
 
 }  // namespace
 
-size_t sort_scratch_bytes(int64_t n, int A) {
+size_t sort_scratch_bytes(int64_t n, int G) {
     const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
     size_t b = 0;
-    auto add = [&](size_t bytes) { b += ((bytes + 255) / 256) * 256 + 256; };
+    auto add = [&](size_t bytes) { b += bump_bytes(bytes); };
     add(4 * n); add(4 * n); add(4 * n); add(4 * n);    // keys/vals ping-pong
     add(4 * 256 * std::max<int64_t>(nblk, 1));         // histograms
     add(4 * n); add(2 * n); add(4 * n);                 // perm, bins, energies
-    add(4 * (A + 1)); add(4 * (A + 1)); add(4 * A);     // angle_start, tile_start, angle_of_rank
-    add(4 * A);                                         // rank_of_angle
-    add(sizeof(Tile) * (size_t)(n / kETMin + A + 1));   // tiles (smallest tile size)
+    add(4 * (G + 1)); add(4 * (G + 1));                 // group_start, tile_start
+    add(4 * G); add(4 * G); add(4 * G);                 // angle/lines of each group, rank of each angle
+    add(sizeof(Tile) * (size_t)(n / kETMin + G + 1));   // tiles (smallest tile size)
     return b;
 }
+
+namespace {
+
+int key_bits(uint64_t kmax) {
+    int bits = 1;
+    while (bits < 32 && (kmax >> bits) != 0) ++bits;
+    return bits;
+}
+
+struct Windows {
+    float4 w01, w23, w45, w67;
+};
+Windows windows_of(const ModelConst& m) {
+    float w[8][2] = {};
+    for (int k = 0; k < m.n_win; ++k) {
+        w[k][0] = (float)m.win_lo[k];
+        w[k][1] = (float)m.win_hi[k];
+    }
+    return Windows{make_float4(w[0][0], w[0][1], w[1][0], w[1][1]),
+                   make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
+                   make_float4(w[4][0], w[4][1], w[5][0], w[5][1]),
+                   make_float4(w[6][0], w[6][1], w[7][0], w[7][1])};
+}
+
+// The sort shared by sort_events and sort_events_fixed: keys, radix passes,
+// gather, group bounds and tiles of the G = A * n_classes groups, all on
+// the caller's stream.  rank_of_angle [A], angle_of_group and lines_of_group
+// [G] are device arrays already filled.
+int sort_and_tile(lm_handle* h, const lm_events* ev, int G, const int* rank_of_angle,
+                  const int* angle_of_group, const int* lines_of_group, uint32_t* keys0,
+                  uint32_t* keys1, uint32_t* vals0, uint32_t* vals1, uint32_t* hist,
+                  uint32_t* perm, uint16_t* bin_s, float* e_s, int* group_start, int* tile_start,
+                  int tile_ev, Tile* tiles, cudaStream_t st) {
+    const ModelConst& m = h->mc;
+    const int64_t n = ev->n;
+    const int B = m.B;
+    if (n > 0) {
+        const Windows wn = windows_of(m);
+        k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            ev->angle, ev->bin, ev->energy_keV, n, m.A, B, rank_of_angle, m.n_win, wn.w01, wn.w23,
+            wn.w45, wn.w67, h->ecls, keys0, vals0, h->d_status);
+        ++h->launches;
+        LMMEW_CUDA(cudaGetLastError());
+        const int bits = key_bits((uint64_t)G * (uint64_t)B);
+        const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+        uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
+            k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+            k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk,
+                                                              kout, vout);
+            h->launches += 3;
+            LMMEW_CUDA(cudaGetLastError());
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B, perm,
+                                                             bin_s, e_s);
+        k_bounds<<<(G + 1 + 127) / 128, 128, 0, st>>>(kin, n, G, B, group_start);
+        h->launches += 2;
+        LMMEW_CUDA(cudaGetLastError());
+    } else {
+        LMMEW_CUDA(cudaMemsetAsync(group_start, 0, sizeof(int) * (G + 1), st));
+    }
+    k_tile_scan<<<1, 1024, 0, st>>>(group_start, G, tile_ev, tile_start);
+    k_tiles<<<(G + 127) / 128, 128, 0, st>>>(group_start, tile_start, angle_of_group, G, tile_ev,
+                                             bin_s, lines_of_group, tiles);
+    h->launches += 2;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int status_error(int status) {
+    if (status & kStatusTimeout)
+        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
+    if (status & kStatusOutOfRange)
+        return set_error(LMMEW_ERR_OUT_OF_RANGE,
+                         "an event has an angle or bin outside the model or an energy outside "
+                         "every window");
+    return LMMEW_OK;
+}
+
+}  // namespace
 
 int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* out, char*& arena,
                 cudaStream_t st) {
     const ModelConst& m = h->mc;
     const int64_t n = ev->n;
-    const int A = m.A, B = m.B;
-    // angle order: subsets ascending, angles ascending inside a subset
-    std::vector<int> rank_of_angle(A), angle_of_rank(A);
+    const int A = m.A, C = h->n_classes, G = sort_groups(h, A);
+    // angle order: subsets ascending, angles ascending inside a subset; a
+    // rank's groups are its energy classes in ascending order
+    std::vector<int> rank_of_angle(A), angle_of_group(G), lines_of_group(G);
     {
         int r = 0;
         for (int s = 0; s < n_subsets; ++s)
-            for (int a = s; a < A; a += n_subsets) { rank_of_angle[a] = r; angle_of_rank[r] = a; ++r; }
+            for (int a = s; a < A; a += n_subsets) {
+                rank_of_angle[a] = r;
+                for (int c = 0; c < C; ++c) {
+                    angle_of_group[r * C + c] = a;
+                    lines_of_group[r * C + c] = h->class_lines[c];
+                }
+                ++r;
+            }
     }
     uint32_t* keys0 = bump<uint32_t>(arena, n);
     uint32_t* keys1 = bump<uint32_t>(arena, n);
@@ -220,81 +392,42 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
     out->perm = bump<uint32_t>(arena, n);
     out->bin = bump<uint16_t>(arena, n);
     out->energy = bump<float>(arena, n);
-    out->angle_start = bump<int>(arena, A + 1);
-    out->tile_start = bump<int>(arena, A + 1);
-    int* d_angle_of_rank = bump<int>(arena, A);
-    int* d_rank_of_angle = bump<int>(arena, A);
-    out->tiles = bump<Tile>(arena, n / kETMin + A + 1);
+    out->group_start = bump<int>(arena, G + 1);
+    out->tile_start = bump<int>(arena, G + 1);
+    int* d_angle_of_group = bump<int>(arena, G);
+    int* d_lines_of_group = bump<int>(arena, G);
+    int* d_rank_of_angle = bump<int>(arena, G);
+    out->tiles = bump<Tile>(arena, n / kETMin + G + 1);
     out->tile_ev = h->tile_ev;
-    out->n_groups = A;
-    out->angle_of_group = d_angle_of_rank;
+    out->n_groups = G;
+    out->n_classes = C;
+    out->angle_of_group = d_angle_of_group;
+    out->lines_of_group = d_lines_of_group;
 
     LMMEW_CUDA(cudaMemcpyAsync(d_rank_of_angle, rank_of_angle.data(), sizeof(int) * A,
                                cudaMemcpyHostToDevice, st));
-    LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_rank, angle_of_rank.data(), sizeof(int) * A,
+    LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_group, angle_of_group.data(), sizeof(int) * G,
                                cudaMemcpyHostToDevice, st));
-    if (n > 0) {
-        float w[8][2] = {};
-        for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
-        const float4 w01 = make_float4(w[0][0], w[0][1], w[1][0], w[1][1]);
-        const float4 w23 = make_float4(w[2][0], w[2][1], w[3][0], w[3][1]);
-        const float4 w45 = make_float4(w[4][0], w[4][1], w[5][0], w[5][1]);
-        const float4 w67 = make_float4(w[6][0], w[6][1], w[7][0], w[7][1]);
-        k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ev->angle, ev->bin, ev->energy_keV, n, A,
-                                                            B, d_rank_of_angle, m.n_win, w01,
-                                                            w23, w45, w67, keys0, vals0, h->d_status);
-        ++h->launches;
-        LMMEW_CUDA(cudaGetLastError());
-        const uint64_t kmax = (uint64_t)A * (uint64_t)B;
-        int bits = 1;
-        while (bits < 32 && (kmax >> bits) != 0) ++bits;
-        uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
-        for (int shift = 0; shift < bits; shift += 8) {
-            k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
-            ++h->launches;
-            k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
-            ++h->launches;
-            k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk,
-                                                              kout, vout);
-            ++h->launches;
-            LMMEW_CUDA(cudaGetLastError());
-            std::swap(kin, kout);
-            std::swap(vin, vout);
-        }
-        k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B,
-                                                             out->perm, out->bin, out->energy);
-        ++h->launches;
-        k_bounds<<<(A + 1 + 127) / 128, 128, 0, st>>>(kin, n, A, B, out->angle_start);
-        ++h->launches;
-        LMMEW_CUDA(cudaGetLastError());
-    } else {
-        LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (A + 1), st));
-    }
-    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, A, out->tile_ev, out->tile_start);
-    ++h->launches;
-    k_tiles<<<(A + 127) / 128, 128, 0, st>>>(out->angle_start, out->tile_start, d_angle_of_rank, A,
-                                             out->tile_ev, out->bin, out->tiles);
-    ++h->launches;
-    LMMEW_CUDA(cudaGetLastError());
+    LMMEW_CUDA(cudaMemcpyAsync(d_lines_of_group, lines_of_group.data(), sizeof(int) * G,
+                               cudaMemcpyHostToDevice, st));
+    int rc = sort_and_tile(h, ev, G, d_rank_of_angle, d_angle_of_group, d_lines_of_group, keys0,
+                           keys1, vals0, vals1, hist, out->perm, out->bin, out->energy,
+                           out->group_start, out->tile_start, out->tile_ev, out->tiles, st);
+    if (rc != LMMEW_OK) return rc;
     // one synchronisation: validation status and the work sizes
-    out->h_angle_start.resize(A + 1);
-    out->h_tile_start.resize(A + 1);
-    out->h_rank_angle = angle_of_rank;
+    out->h_group_start.resize(G + 1);
+    out->h_tile_start.resize(G + 1);
     int status = 0;
-    LMMEW_CUDA(cudaMemcpyAsync(&out->h_angle_start[0], out->angle_start, sizeof(int) * (A + 1),
+    LMMEW_CUDA(cudaMemcpyAsync(&out->h_group_start[0], out->group_start, sizeof(int) * (G + 1),
                                cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaMemcpyAsync(&out->h_tile_start[0], out->tile_start, sizeof(int) * (A + 1),
+    LMMEW_CUDA(cudaMemcpyAsync(&out->h_tile_start[0], out->tile_start, sizeof(int) * (G + 1),
                                cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaStreamSynchronize(st));
     if (status != 0) LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
-    if (status & kStatusTimeout)
-        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
-    if (status & kStatusOutOfRange)
-        return set_error(LMMEW_ERR_OUT_OF_RANGE,
-                         "an event has an angle or bin outside the model or an energy outside "
-                         "every window");
-    out->n_valid = out->h_angle_start[A];
+    rc = status_error(status);
+    if (rc != LMMEW_OK) return rc;
+    out->n_valid = out->h_group_start[G];
     return LMMEW_OK;
 }
 
@@ -303,19 +436,27 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
 // caller-provided region, no host container is built, and the host reads
 // back only three integers.  Angles keep their natural order (one subset).
 namespace {
-__global__ void k_identity(int* a, int* b, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) { a[i] = i; b[i] = i; }
+struct ClassLines {
+    int v[2 * LMMEW_MAX_LINES + 1];
+};
+__global__ void k_identity_groups(int* rank_of_angle, int* angle_of_group, int* lines_of_group,
+                                  int A, int C, const ClassLines cl) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < A) rank_of_angle[g] = g;
+    if (g < A * C) {
+        angle_of_group[g] = g / C;
+        lines_of_group[g] = cl.v[g % C];
+    }
 }
 }  // namespace
 
-size_t sort_fixed_bytes(int64_t n, int A) { return sort_scratch_bytes(n, A); }
+size_t sort_fixed_bytes(int64_t n, int G) { return sort_scratch_bytes(n, G); }
 
 int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
                       cudaStream_t st) {
     const ModelConst& m = h->mc;
     const int64_t n = ev->n;
-    const int A = m.A, B = m.B;
+    const int A = m.A, C = h->n_classes, G = sort_groups(h, A);
     uint32_t* keys0 = bump<uint32_t>(arena, n);
     uint32_t* keys1 = bump<uint32_t>(arena, n);
     uint32_t* vals0 = bump<uint32_t>(arena, n);
@@ -325,58 +466,35 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
     out->perm = bump<uint32_t>(arena, n);
     out->bin = bump<uint16_t>(arena, n);
     out->energy = bump<float>(arena, n);
-    int* angle_start = bump<int>(arena, A + 1);
-    int* tile_start = bump<int>(arena, A + 1);
-    int* d_angle_of_rank = bump<int>(arena, A);
-    int* d_rank_of_angle = bump<int>(arena, A);
-    out->tiles = bump<Tile>(arena, n / kETMin + A + 1);
+    int* group_start = bump<int>(arena, G + 1);
+    int* tile_start = bump<int>(arena, G + 1);
+    int* d_angle_of_group = bump<int>(arena, G);
+    int* d_lines_of_group = bump<int>(arena, G);
+    int* d_rank_of_angle = bump<int>(arena, G);
+    out->tiles = bump<Tile>(arena, n / kETMin + G + 1);
     out->tile_ev = h->tile_ev;
 
-    k_identity<<<(A + 255) / 256, 256, 0, st>>>(d_rank_of_angle, d_angle_of_rank, A);
-    float w[8][2] = {};
-    for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
-    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        ev->angle, ev->bin, ev->energy_keV, n, A, B, d_rank_of_angle, m.n_win,
-        make_float4(w[0][0], w[0][1], w[1][0], w[1][1]), make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
-        make_float4(w[4][0], w[4][1], w[5][0], w[5][1]), make_float4(w[6][0], w[6][1], w[7][0], w[7][1]),
-        keys0, vals0, h->d_status);
+    ClassLines cl;
+    for (int c = 0; c < 2 * LMMEW_MAX_LINES + 1; ++c) cl.v[c] = h->class_lines[c];
+    k_identity_groups<<<(G + 255) / 256, 256, 0, st>>>(d_rank_of_angle, d_angle_of_group,
+                                                       d_lines_of_group, A, C, cl);
+    ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
-    const uint64_t kmax = (uint64_t)A * (uint64_t)B;
-    int bits = 1;
-    while (bits < 32 && (kmax >> bits) != 0) ++bits;
-    uint32_t *kin = keys0, *kout = keys1, *vin = vals0, *vout = vals1;
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_hist<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, n, shift, hist, (int)nblk);
-        k_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
-        k_scatter<<<(unsigned)nblk, kSortThreads, 0, st>>>(kin, vin, n, shift, hist, (int)nblk, kout,
-                                                          vout);
-        LMMEW_CUDA(cudaGetLastError());
-        uint32_t* t = kin; kin = kout; kout = t;
-        t = vin; vin = vout; vout = t;
-    }
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, ev->energy_keV, n, B, out->perm,
-                                                         out->bin, out->energy);
-    k_bounds<<<(A + 1 + 127) / 128, 128, 0, st>>>(kin, n, A, B, angle_start);
-    k_tile_scan<<<1, 1024, 0, st>>>(angle_start, A, out->tile_ev, tile_start);
-    k_tiles<<<(A + 127) / 128, 128, 0, st>>>(angle_start, tile_start, d_angle_of_rank, A,
-                                             out->tile_ev, out->bin, out->tiles);
-    LMMEW_CUDA(cudaGetLastError());
-    h->launches += 6 + 3 * ((bits + 7) / 8);
+    int rc = sort_and_tile(h, ev, G, d_rank_of_angle, d_angle_of_group, d_lines_of_group, keys0,
+                           keys1, vals0, vals1, hist, out->perm, out->bin, out->energy,
+                           group_start, tile_start, out->tile_ev, out->tiles, st);
+    if (rc != LMMEW_OK) return rc;
     int host3[3] = {0, 0, 0};   // tiles, valid events, status
-    LMMEW_CUDA(cudaMemcpyAsync(&host3[0], tile_start + A, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaMemcpyAsync(&host3[1], angle_start + A, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&host3[0], tile_start + G, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&host3[1], group_start + G, sizeof(int), cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaMemcpyAsync(&host3[2], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaStreamSynchronize(st));
     if (host3[2] != 0) {
         LMMEW_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
         LMMEW_CUDA(cudaStreamSynchronize(st));
     }
-    if (host3[2] & kStatusTimeout)
-        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
-    if (host3[2] & kStatusOutOfRange)
-        return set_error(LMMEW_ERR_OUT_OF_RANGE,
-                         "an event has an angle or bin outside the model or an energy outside "
-                         "every window");
+    rc = status_error(host3[2]);
+    if (rc != LMMEW_OK) return rc;
     out->n_tiles = host3[0];
     out->n_valid = host3[1];
     return LMMEW_OK;
@@ -384,10 +502,10 @@ int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFix
 
 // ---------------------------------------------------------------------------
 // Batched sort: R realisations' events concatenated and keyed by (subset,
-// angle within the subset, bin) alone.  The radix sort is stable, so within
-// one (angle, bin) the events keep realisation order and, inside a
-// realisation, their input order: each realisation's events appear in the
-// order lm_osem would sort them on their own.  An angle's run, and so every
+// angle within the subset, energy class, bin) alone.  The radix sort is
+// stable, so within one (angle, class, bin) the events keep realisation order
+// and, inside a realisation, their input order: each realisation's events
+// appear in the order lm_osem would sort them on their own.  An angle's run, and so every
 // tile, holds the events of all realisations together, each with its
 // realisation beside it: a sub-iteration's tiles are full whatever the
 // realisations' event counts, and their bin ranges narrow as the
@@ -396,7 +514,8 @@ namespace {
 __global__ void k_keys_batch(const uint16_t* angle, const uint16_t* bin, const float* energy,
                              int64_t n, int A, int B, int n_subsets, int A_s, int n_win,
                              float4 win01, float4 win23, float4 win45, float4 win67,
-                             uint32_t* keys, uint32_t* vals, int* status) {
+                             const EnergyClasses ec, uint32_t* keys, uint32_t* vals,
+                             int* status) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int a = angle[j], b = bin[j];
@@ -406,9 +525,10 @@ __global__ void k_keys_batch(const uint16_t* angle, const uint16_t* bin, const f
     bool inwin = false;
     for (int k = 0; k < n_win; ++k) inwin |= (e >= wl[k] && e < wh[k]);
     const bool ok = a < A && b < B && isfinite(e) && inwin;
-    const uint32_t V = (uint32_t)n_subsets * A_s;
+    const uint32_t C = (uint32_t)ec.n_bnd + 1u;
+    const uint32_t G = (uint32_t)n_subsets * A_s * C;
     const uint32_t v = (uint32_t)(a % n_subsets) * A_s + a / n_subsets;
-    keys[j] = ok ? v * (uint32_t)B + (uint32_t)b : V * (uint32_t)B;
+    keys[j] = ok ? (v * C + energy_class(ec, e)) * (uint32_t)B + (uint32_t)b : G * (uint32_t)B;
     vals[j] = (uint32_t)j;
     if (!ok) atomicOr(status, kStatusOutOfRange);
 }
@@ -441,12 +561,6 @@ __global__ void k_bp_keys(const uint16_t* real, int64_t n, const int64_t* blk_st
     vals[i] = (uint32_t)i;
 }
 
-int key_bits(uint64_t kmax) {
-    int bits = 1;
-    while (bits < 32 && (kmax >> bits) != 0) ++bits;
-    return bits;
-}
-
 // Stable LSD radix sort of (keys, vals) over the ping-pong buffers; the
 // sorted pair ends in (kin, vin).
 int radix_sort_pairs(lm_handle* h, int64_t n, int bits, uint32_t*& kin, uint32_t*& kout,
@@ -466,7 +580,7 @@ int radix_sort_pairs(lm_handle* h, int64_t n, int bits, uint32_t*& kin, uint32_t
 }
 }  // namespace
 
-size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R) {
+size_t sort_batch_scratch_bytes(int64_t n, int64_t G, int R) {
     const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
     size_t b = 0;
     auto add = [&](size_t bytes) { b += bump_bytes(bytes); };
@@ -474,26 +588,32 @@ size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R) {
     add(4 * 256 * (nblk > 0 ? nblk : 1));
     add(4 * n); add(2 * n); add(4 * n); add(2 * n);     // perm, bins, energies, realisations
     add(2 * n); add(2 * n); add(4 * n);                 // concatenated events
-    add(4 * (V + 1)); add(4 * (V + 1)); add(4 * V);
+    add(4 * (G + 1)); add(4 * (G + 1)); add(4 * G); add(4 * G);
     add(8 * (R + 1));
-    add(sizeof(Tile) * (size_t)(n / kETMin + V + 1));
+    add(sizeof(Tile) * (size_t)(n / kETMin + G + 1));
     return b;
 }
 
+// Groups of the batched sort: (subset, angle within the subset, class), with
+// A_s = ceil(A / n_subsets) angle slots per subset (empty past the last angle).
 int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                       SortedEvents* out, char*& arena, cudaStream_t st) {
     const ModelConst& m = h->mc;
-    const int A = m.A, B = m.B;
+    const int A = m.A, B = m.B, C = h->n_classes;
     const int A_s = (A + n_subsets - 1) / n_subsets;
     const int64_t V = (int64_t)n_subsets * A_s;
+    const int64_t G = V * C;
     std::vector<int64_t> off(R + 1, 0);
     for (int r = 0; r < R; ++r) off[r + 1] = off[r] + evs[r].n;
     const int64_t n = off[R];
-    std::vector<int> angle_of_v(V);
+    std::vector<int> angle_of_group(G), lines_of_group(G);
     for (int64_t v = 0; v < V; ++v) {
         const int ai = (int)(v % A_s), s = (int)(v / A_s);
         const int a = ai * n_subsets + s;
-        angle_of_v[v] = a < A ? a : 0;
+        for (int c = 0; c < C; ++c) {
+            angle_of_group[v * C + c] = a < A ? a : 0;
+            lines_of_group[v * C + c] = h->class_lines[c];
+        }
     }
     out->tmp_keys0 = bump<uint32_t>(arena, n);
     out->tmp_keys1 = bump<uint32_t>(arena, n);
@@ -508,14 +628,17 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     uint16_t* c_angle = bump<uint16_t>(arena, n);
     uint16_t* c_bin = bump<uint16_t>(arena, n);
     float* c_energy = bump<float>(arena, n);
-    out->angle_start = bump<int>(arena, V + 1);
-    out->tile_start = bump<int>(arena, V + 1);
-    int* d_angle_of_v = bump<int>(arena, V);
+    out->group_start = bump<int>(arena, G + 1);
+    out->tile_start = bump<int>(arena, G + 1);
+    int* d_angle_of_group = bump<int>(arena, G);
+    int* d_lines_of_group = bump<int>(arena, G);
     int64_t* d_off = bump<int64_t>(arena, R + 1);
-    out->tiles = bump<Tile>(arena, n / kETMin + V + 1);
+    out->tiles = bump<Tile>(arena, n / kETMin + G + 1);
     out->tile_ev = h->tile_ev;
-    out->n_groups = (int)V;
-    out->angle_of_group = d_angle_of_v;
+    out->n_groups = (int)G;
+    out->n_classes = C;
+    out->angle_of_group = d_angle_of_group;
+    out->lines_of_group = d_lines_of_group;
 
     for (int r = 0; r < R; ++r) {
         if (evs[r].n == 0) continue;
@@ -527,53 +650,51 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                                    cudaMemcpyDeviceToDevice, st));
     }
     LMMEW_CUDA(cudaMemcpyAsync(d_off, off.data(), 8 * (R + 1), cudaMemcpyHostToDevice, st));
-    LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_v, angle_of_v.data(), 4 * V, cudaMemcpyHostToDevice, st));
+    LMMEW_CUDA(cudaMemcpyAsync(d_angle_of_group, angle_of_group.data(), 4 * G,
+                               cudaMemcpyHostToDevice, st));
+    LMMEW_CUDA(cudaMemcpyAsync(d_lines_of_group, lines_of_group.data(), 4 * G,
+                               cudaMemcpyHostToDevice, st));
     if (n > 0) {
-        float w[8][2] = {};
-        for (int k = 0; k < m.n_win; ++k) { w[k][0] = (float)m.win_lo[k]; w[k][1] = (float)m.win_hi[k]; }
+        const Windows wn = windows_of(m);
         uint32_t *kin = out->tmp_keys0, *kout = out->tmp_keys1;
         uint32_t *vin = out->tmp_vals0, *vout = out->tmp_vals1;
         k_keys_batch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            c_angle, c_bin, c_energy, n, A, B, n_subsets, A_s, m.n_win,
-            make_float4(w[0][0], w[0][1], w[1][0], w[1][1]), make_float4(w[2][0], w[2][1], w[3][0], w[3][1]),
-            make_float4(w[4][0], w[4][1], w[5][0], w[5][1]), make_float4(w[6][0], w[6][1], w[7][0], w[7][1]),
-            kin, vin, h->d_status);
+            c_angle, c_bin, c_energy, n, A, B, n_subsets, A_s, m.n_win, wn.w01, wn.w23, wn.w45,
+            wn.w67, h->ecls, kin, vin, h->d_status);
+        ++h->launches;
         LMMEW_CUDA(cudaGetLastError());
-        int rc = radix_sort_pairs(h, n, key_bits((uint64_t)V * (uint64_t)B), kin, kout, vin, vout,
+        int rc = radix_sort_pairs(h, n, key_bits((uint64_t)G * (uint64_t)B), kin, kout, vin, vout,
                                   out->tmp_hist, st);
         if (rc != LMMEW_OK) return rc;
         k_gather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(kin, vin, c_energy, n, B, out->perm,
                                                              out->bin, out->energy);
         k_real_of<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out->perm, n, d_off, R, out->real);
-        k_bounds<<<(unsigned)((V + 1 + 127) / 128), 128, 0, st>>>(kin, n, (int)V, B, out->angle_start);
-        h->launches += 4;
+        k_bounds<<<(unsigned)((G + 1 + 127) / 128), 128, 0, st>>>(kin, n, (int)G, B,
+                                                                 out->group_start);
+        h->launches += 3;
         LMMEW_CUDA(cudaGetLastError());
     } else {
-        LMMEW_CUDA(cudaMemsetAsync(out->angle_start, 0, sizeof(int) * (V + 1), st));
+        LMMEW_CUDA(cudaMemsetAsync(out->group_start, 0, sizeof(int) * (G + 1), st));
     }
-    k_tile_scan<<<1, 1024, 0, st>>>(out->angle_start, (int)V, out->tile_ev, out->tile_start);
-    k_tiles<<<(unsigned)((V + 127) / 128), 128, 0, st>>>(out->angle_start, out->tile_start,
-                                                         d_angle_of_v, (int)V, out->tile_ev,
-                                                         out->bin, out->tiles);
+    k_tile_scan<<<1, 1024, 0, st>>>(out->group_start, (int)G, out->tile_ev, out->tile_start);
+    k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(out->group_start, out->tile_start,
+                                                         d_angle_of_group, (int)G, out->tile_ev,
+                                                         out->bin, d_lines_of_group, out->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
-    out->h_angle_start.resize(V + 1);
-    out->h_tile_start.resize(V + 1);
+    out->h_group_start.resize(G + 1);
+    out->h_tile_start.resize(G + 1);
     int status = 0;
-    LMMEW_CUDA(cudaMemcpyAsync(out->h_angle_start.data(), out->angle_start, 4 * (V + 1),
+    LMMEW_CUDA(cudaMemcpyAsync(out->h_group_start.data(), out->group_start, 4 * (G + 1),
                                cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaMemcpyAsync(out->h_tile_start.data(), out->tile_start, 4 * (V + 1),
+    LMMEW_CUDA(cudaMemcpyAsync(out->h_tile_start.data(), out->tile_start, 4 * (G + 1),
                                cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LMMEW_CUDA(cudaStreamSynchronize(st));
     if (status != 0) LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
-    if (status & kStatusTimeout)
-        return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
-    if (status & kStatusOutOfRange)
-        return set_error(LMMEW_ERR_OUT_OF_RANGE,
-                         "an event has an angle or bin outside the model or an energy outside "
-                         "every window");
-    out->n_valid = out->h_angle_start[V];
+    const int rc = status_error(status);
+    if (rc != LMMEW_OK) return rc;
+    out->n_valid = out->h_group_start[G];
     out->n_total = n;
     return LMMEW_OK;
 }
@@ -617,10 +738,10 @@ int recut_tiles(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st) {
         return set_error(LMMEW_ERR_INVALID_ARG, "tile size must be 32, 64 or 128 events");
     if (se->tile_ev == tile_ev) return LMMEW_OK;
     const int G = se->n_groups;
-    k_tile_scan<<<1, 1024, 0, st>>>(se->angle_start, G, tile_ev, se->tile_start);
-    k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->angle_start, se->tile_start,
+    k_tile_scan<<<1, 1024, 0, st>>>(se->group_start, G, tile_ev, se->tile_start);
+    k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->group_start, se->tile_start,
                                                          se->angle_of_group, G, tile_ev, se->bin,
-                                                         se->tiles);
+                                                         se->lines_of_group, se->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     se->h_tile_start.resize(G + 1);

@@ -55,13 +55,30 @@ struct LineConst {
     float norm[LMMEW_MAX_LINES];   // 1 / (sqrt(2 pi) sigma_E(E))
 };
 
-// One tile of events: one angle, up to tile_ev (<= kET) consecutive sorted events.
+// One tile of events: one angle and one energy class, up to tile_ev (<= kET)
+// consecutive sorted events.
 struct Tile {
     int a;          // detector angle
     int begin;      // first sorted event (index into the sorted arrays)
     int count;      // 1..tile_ev
     int b_lo_hi;    // (b_lo << 16) | b_hi: bin range of the tile's events
     int r;          // realisation (0 outside batched reconstruction)
+    int lines;      // bit w set: line w's single scatter can reach the tile's energies
+};
+
+// Energy classes of the recorded energy.  A photon of line w that scatters
+// once leaves with E' between the backscatter energy E_w / (1 + 2 E_w / m_e c^2)
+// and E_w; the detector blurs E' by a Gaussian of sigma_E(E').  Line w's
+// reach is [lo_w, hi_w] = the union of E' -+ kScatterReachSigmas sigma_E(E')
+// over those E'.  The 2W reach ends, sorted, cut the energy axis into classes;
+// inside one class every line's reach either covers the class or misses it,
+// so the class fixes which lines' single-scatter terms the row kernel
+// evaluates.  A term of a line out of reach has an energy factor below
+// exp(-kScatterReachSigmas^2 / 2) = exp(-32) of its own path's peak.
+constexpr float kScatterReachSigmas = 8.0f;
+struct EnergyClasses {
+    int n_bnd;                          // class boundaries (0: one class, every line)
+    float bnd[2 * LMMEW_MAX_LINES];     // ascending; class = #{k : bnd[k] <= E_hat}
 };
 
 struct Scratch {
@@ -85,6 +102,11 @@ struct lm_handle {
     float* d_prim = nullptr;       // [A][W][nq] alpha_w exp(-mu_w gamma_det)
     double* d_sens_a = nullptr;    // [A][nq] per-angle sensitivity (FP64)
     int* d_status = nullptr;       // device status word
+    // energy classes of the sort and the lines each class evaluates
+    lmmew::EnergyClasses ecls{};
+    int n_classes = 1;
+    int class_lines[2 * LMMEW_MAX_LINES + 1] = {};
+    int prune_lines = 1;           // 0: every tile evaluates every line (lm_set_energy_pruning)
     size_t tab_bytes = 0;
     // cached subset sensitivities for the last partition asked for
     int sens_parts = 0;
@@ -156,20 +178,26 @@ int cuda_error(cudaError_t e, const char* what);
 
 // setup.cu
 int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_host);
+// events.cu: the energy classes of the handle's lines and energy model
+void build_energy_classes(lm_handle* h);
 int subset_sensitivity(lm_handle* h, int n_subsets, cudaStream_t st);
 
-// events.cu: validation + stable sort by (subset rank of angle, bin)
+// events.cu: validation + stable sort by (subset rank of angle, energy class,
+// bin).  A group is one (angle rank, energy class): n_classes consecutive
+// groups per angle rank.
 struct SortedEvents {
     uint16_t* bin = nullptr;     // [n] sorted bins
     float* energy = nullptr;     // [n] sorted energies
     uint32_t* perm = nullptr;    // [n] caller index of each sorted event
-    int* angle_start = nullptr;  // [A+1] device: first sorted event of each angle rank
+    int* group_start = nullptr;  // [G+1] device: first sorted event of each group
     Tile* tiles = nullptr;       // [max_tiles]
-    int* tile_start = nullptr;   // [A+1] first tile of each angle rank
+    int* tile_start = nullptr;   // [G+1] first tile of each group
     int64_t n_valid = 0;
     int tile_ev = kET;           // events per tile the tiles were cut with
-    int n_groups = 0;            // angle groups (ranks) the tiles are cut in
+    int n_groups = 0;            // groups G the tiles are cut in
+    int n_classes = 1;           // groups per angle rank
     const int* angle_of_group = nullptr;   // device [n_groups]: angle of each group
+    const int* lines_of_group = nullptr;   // device [n_groups]: line mask of each group
     // batched sort only
     uint16_t* real = nullptr;    // [n] realisation of each sorted event
     uint32_t* bp_idx = nullptr;  // [n] back-projection order (bp_order_batch)
@@ -177,11 +205,13 @@ struct SortedEvents {
              *tmp_vals1 = nullptr, *tmp_hist = nullptr;
     int64_t n_total = 0;
     // host copies
-    std::vector<int> h_angle_start;  // [A+1]
-    std::vector<int> h_tile_start;   // [A+1]
-    std::vector<int> h_rank_angle;   // [A] angle of each rank
+    std::vector<int> h_group_start;  // [G+1]
+    std::vector<int> h_tile_start;   // [G+1]
 };
-size_t sort_scratch_bytes(int64_t n, int A);
+// Groups of a sort over A angle ranks (A * n_classes) and the line mask of
+// each class.
+int sort_groups(const lm_handle* h, int A);
+size_t sort_scratch_bytes(int64_t n, int G);
 int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* out,
                 char*& arena, cudaStream_t st);
 
@@ -195,8 +225,8 @@ struct SortedFixed {
     int64_t n_valid = 0;
     int tile_ev = kET;
 };
-size_t sort_fixed_bytes(int64_t n, int A);
-size_t sort_batch_scratch_bytes(int64_t n, int64_t V, int R);
+size_t sort_fixed_bytes(int64_t n, int G);
+size_t sort_batch_scratch_bytes(int64_t n, int64_t G, int R);
 int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                       SortedEvents* out, char*& arena, cudaStream_t st);
 int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_start, int n_blk,
@@ -289,7 +319,7 @@ constexpr float kSurrogateEps = 1e-8f;   // target = ln(S + eps)
 // energy-resolution sigmas of the energies single scatter of the line can
 // have (backscatter energy to E_w): outside, the exact term is below
 // exp(-32) of its largest value and the surrogate's part is 0.
-constexpr float kSurrogateReachSigmas = 8.0f;
+constexpr float kSurrogateReachSigmas = kScatterReachSigmas;
 constexpr float kElectronRestKeV = 510.99895f;
 // Inputs 8 j .. 8 j + 7 (j = 0..3) of one (event, voxel, line); g8 holds the
 // 8 rho line integrals of the voxel at this angle.  Four threads can build

@@ -52,7 +52,7 @@ extern "C" int lm_forward_noalloc(lm_handle* h, const lm_events* ev, const float
     const int64_t n = ev->n;
     // every word of the region below is written before it is read within a
     // call, so nothing has to start at zero
-    const size_t need = sort_fixed_bytes(n, m.A) + bump_bytes(sizeof(float) * m.nq) +
+    const size_t need = sort_fixed_bytes(n, sort_groups(h, m.A)) + bump_bytes(sizeof(float) * m.nq) +
                         bump_bytes(sizeof(float) * (size_t)m.nqt * n);
     if (n >= (int64_t(1) << 31) || need > kNoAllocBytes)
         return set_error(LMMEW_ERR_INVALID_ARG,

@@ -413,3 +413,45 @@ def test_scatter_line_row_scales_with_the_line_yield():
                                0.5 * m1.scatter_line_row(2, 6, 100.0, 0), rtol=1e-13)
     np.testing.assert_allclose(m2.scatter_line_row(2, 6, 240.0, 2),
                                4.0 * m1.scatter_line_row(2, 6, 240.0, 2), rtol=1e-13)
+
+
+def _scatter_reach(e_line, fwhm_frac, e_ref, exponent, k=8.0):
+    """Recorded energies one Compton scatter of line e_line can produce,
+    widened by k energy-resolution sigmas: the union over E' in
+    [backscatter energy, e_line] of E' -+ k sigma_E(E'), on a fine grid."""
+    e_back = e_line / (1.0 + 2.0 * e_line / 510.99895)
+    es = np.linspace(e_back, e_line, 20001)
+    sig = fwhm_frac * es * (es / e_ref) ** exponent / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    return float((es - k * sig).min()), float((es + k * sig).max())
+
+
+@pytest.mark.parametrize("name", ["small_16", "lmmew_32"])
+def test_scatter_of_lines_out_of_reach_is_negligible_in_rows(name):
+    """The exact row's single-scatter part of a line whose scatter cannot
+    reach the recorded energy within 8 sigmas (the energy-window pruning of
+    the row kernel) is negligible: below 1e-12 of the event's whole row
+    (its forward projection of a uniform image) and below 1e-6 of every
+    row element that is not zero.  Energies span the window so that each
+    line is out of reach for some of them (Compton's relation, Eq. s_p with
+    n = 1)."""
+    from synthetic import preset
+    sc = preset(name)
+    orc = oracle.Model.from_scenario(sc, sc.make_phantom().rho)
+    rng = np.random.default_rng(5)
+    checked = set()
+    for e in (52.0, 60.0, 70.0, 125.0, 160.0, 210.0, 250.0, 290.0):
+        for _ in range(3):
+            a, b = int(rng.integers(sc.n_angles)), int(rng.integers(sc.n_bins))
+            row = orc.row(a, b, e)
+            assert row.sum() > 0
+            for w, el in enumerate(sc.line_keV):
+                lo, hi = _scatter_reach(el, sc.fwhm_frac, sc.e_ref_keV, sc.fwhm_exponent)
+                if lo <= e <= hi:
+                    continue
+                s = orc.scatter_line_row(a, b, e, w)
+                assert np.all(s >= 0) and np.all(s <= row)
+                assert s.sum() <= 1e-12 * row.sum(), (w, e, s.sum() / row.sum())
+                m = row > 0
+                assert np.all(s[m] <= 1e-6 * row[m]), (w, e, float((s[m] / row[m]).max()))
+                checked.add(w)
+    assert checked == set(range(len(sc.line_keV)))

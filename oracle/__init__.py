@@ -14,6 +14,9 @@ Parity status of each function and what pins it (tests/test_oracle_*.py):
                                                     attenuator, brute-force
                                                     bin/energy integration
   osem                                            - EM invariants, MLEM ascent
+  angle_paths, sampler.sample_events              - chi-square of sampled event
+                                                    histograms against the rows'
+                                                    expectation
 """
 from __future__ import annotations
 
@@ -103,6 +106,7 @@ def _load():
             "orc_detector_integral": (_D, [_P, _D, _D, _I]),
             "orc_row": (None, [_P, _I, _I, _D, _PD]),
             "orc_scatter_line_row": (None, [_P, _I, _I, _D, _I, _PD]),
+            "orc_angle_paths": (None, [_P, _I, _PD, _PD, _PD, _PD, _PD, _PD, _PD]),
             "orc_forward": (None, [_P, _I64, _PU16, _PU16, _PF, _PD, _PD]),
             "orc_backproject": (None, [_P, _I64, _PU16, _PU16, _PF, _PD, _PD]),
             "orc_sensitivity": (None, [_P, _I, _I, _PD]),
@@ -256,6 +260,25 @@ class Model:
         out = np.zeros(self.nq, dtype=np.float64)
         _load().orc_scatter_line_row(self._h, int(a), int(b), float(e_hat), int(w),
                                      _ptr(out, ctypes.c_double))
+        return out
+
+    def angle_paths(self, a) -> dict:
+        """Path sensitivities of angle a (Eq. s_p, n = 0 and n = 1): s_prim
+        [W, nq], s_scat and e_scat [W, nq, np], and the detector coordinate
+        and collimator blur of every voxel (u_q, sig_q) and scatter point
+        (u_p, sig_p)."""
+        W, nq, npt = self.params.n_lines, self.nq, self.np_scatter
+        out = {"s_prim": np.zeros((W, nq)), "s_scat": np.zeros((W, nq, max(npt, 1))),
+               "e_scat": np.zeros((W, nq, max(npt, 1))), "u_q": np.zeros(nq),
+               "sig_q": np.zeros(nq), "u_p": np.zeros(max(npt, 1)), "sig_p": np.zeros(max(npt, 1))}
+        _load().orc_angle_paths(self._h, int(a), *[_ptr(out[k], ctypes.c_double) for k in
+                                                    ("s_prim", "s_scat", "e_scat", "u_q", "sig_q",
+                                                     "u_p", "sig_p")])
+        if npt == 0:
+            for k in ("s_scat", "e_scat"):
+                out[k] = out[k][:, :, :0]
+            for k in ("u_p", "sig_p"):
+                out[k] = out[k][:0]
         return out
 
     def row_image(self, a, b, e_hat) -> np.ndarray:

@@ -552,6 +552,28 @@ void orc_scatter_line_row(const orc_model* m, int a, int b, double e_hat, int w,
     angle_paths_free(&ap);
 }
 
+/* Path sensitivities of one detector angle, as angle_paths holds them:
+ * s_prim [W][nq] and s_scat, e_scat [W][nq][np] (Eq. s_p with n = 0 and
+ * n = 1; s_scat is 0 for the emission voxel's own cell), the detector
+ * coordinate and collimator blur of every voxel (u_q, sig_q [nq]) and scatter
+ * point (u_p, sig_p [np]).  Used by the model-consistent event sampler. */
+void orc_angle_paths(const orc_model* m, int a, double* s_prim, double* s_scat, double* e_scat,
+                     double* u_q, double* sig_q, double* u_p, double* sig_p) {
+    const size_t W = (size_t)m->p.n_lines, nq = (size_t)m->nq, np = (size_t)m->np;
+    angle_paths ap;
+    angle_paths_build(m, a, &ap);
+    memcpy(s_prim, ap.s_prim, sizeof(double) * W * nq);
+    if (np > 0) {
+        memcpy(s_scat, ap.s_scat, sizeof(double) * W * nq * np);
+        memcpy(e_scat, ap.e_scat, sizeof(double) * W * nq * np);
+        memcpy(u_p, ap.u_p, sizeof(double) * np);
+        memcpy(sig_p, ap.sig_p, sizeof(double) * np);
+    }
+    memcpy(u_q, ap.u_q, sizeof(double) * nq);
+    memcpy(sig_q, ap.sig_q, sizeof(double) * nq);
+    angle_paths_free(&ap);
+}
+
 /* Visit events angle by angle: build s(P) for that angle once, then hand
  * each event's row to a callback together with the index of the thread that
  * computed it (callbacks keep per-thread partial sums). */

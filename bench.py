@@ -51,8 +51,8 @@ def parse_args():
                     help="override the workload's event count (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the forms section (precision, batching, comparison, surrogate, combined)")
-    ap.add_argument("--forms", default="precision,batching,comparison,surrogate,combined",
+                    help="skip the forms section (precision, batching with the combined form, comparison, surrogate)")
+    ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
                     help="comma-separated forms to measure")
     ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train", "surrogate_coarse_osem", "setup"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
@@ -436,7 +436,7 @@ def train_surrogate_on_random_objects(sc, n_objects, n_samples, object_events, s
 
 
 def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_000,
-                       object_events=20_000, iters=2, seed=5):
+                       object_events=20_000, iters=10, seed=5):
     """The learned single-scatter surrogate against the exact FP32 path on the
     same GPU, on the 128 x 128, 2 M-event workload.  The network is trained
     on 10^7 exact single-scatter sums drawn (lm_surrogate_sample) from eight
@@ -527,30 +527,56 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     return out
 
 
-def run_combined_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, iters=2,
-                      n_objects=8, n_samples=4_000_000, seed=6):
-    """The forms together: many noise realisations of uneven size in one
-    batched call (persistent row launch per sub-iteration, one CUDA graph,
-    autotuned launch shape) with the scatter part from the BF16 tensor-core
-    surrogate (trained on random objects of the workload's grid, not its own
-    object), against the plain FP32 exact path one realisation at a time on
-    the same GPU.  Reported: the speed-up and every realisation's
-    lesion-activity deviation from its exact reconstruction."""
+def run_batch_forms():
+    """The batching form on two workloads: the scope's 256 realisations of
+    U[50k, 500k] events at 64^2 through 8 subsets x 10 iterations each
+    (run_c3_forms, with the combined form on the same realisations), and
+    256 realisations of the paper's own study (64^2 of 4.6 mm, 120 angles,
+    three windows, U[8k, 12k] events around its ~10^4 per realisation,
+    4 subsets x 16 iterations), where every single reconstruction is too
+    small to fill the GPU."""
+    return {"lmmew_64_256": run_c3_forms(),
+            "paper_study_256": run_batch_form(workload="paper_study", lo=8_000, hi=12_000,
+                                              iters=None, repeats=2, seed=31)}
+
+
+def run_c3_forms(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, seed=3,
+                 n_objects=8, n_samples=4_000_000, sur_seed=6):
+    """256 independent noise realisations of the 64 x 64 object with event
+    counts drawn uniformly from [50k, 500k] (seed 3), each through 8 subsets x
+    10 iterations.  The realisations are disjoint consecutive slices of one
+    pool of iid Monte-Carlo events (the torch port of the MC on the GPU,
+    seed 3): independent noise realisations.  Timed on the same GPU:
+      exact FP32 one realisation at a time (each reconstruction's own time:
+        p50 / p99 over the 256);
+      exact FP32 batched: all realisations in one lm_osem_batch call (one
+        persistent row launch per row block and sub-iteration over every
+        realisation, the reconstruction replayed as one CUDA graph, autotuned
+        launch shape); every reconstruction completes when the call does;
+      the combined form: the same batched call with the scatter part from
+        the BF16 tensor-core surrogate on the coarse grid, trained on random
+        water/bone objects (not this object), with every realisation's
+        lesion activities against its exact reconstruction.
+    Each batched call is preceded by an untimed one-iteration call that
+    tunes the launch shape and warms up."""
     import numpy as np
     import torch
 
     import paper_2305_17111_gb300 as lm
-    from synthetic import preset, simulate_cached
+    from synthetic import mc_torch, preset
     sc = preset(workload)
     ph = sc.make_phantom()
-    pool = simulate_cached(sc)
     rng = np.random.default_rng(seed)
     sizes = rng.integers(lo, hi + 1, size=n_real)
-    evs = [pool.subset(rng.integers(0, len(pool), size=int(k))) for k in sizes]
-    devs = [lm.DeviceEvents.from_list(e) for e in evs]
-    sur, t_sample, t_train, _, _ = train_surrogate_on_random_objects(
-        sc, n_objects, n_samples, 20_000, seed)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    t0 = time.time()
+    pool = mc_torch.simulate(sc, int(off[-1]), seed=seed, device="cuda")
+    t_pool = time.time() - t0
+    devs = [lm.DeviceEvents(pool.angle[off[r]:off[r + 1]], pool.bin[off[r]:off[r + 1]],
+                            pool.energy[off[r]:off[r + 1]]) for r in range(n_real)]
+    del pool
     model = lm.Model.from_scenario(sc, ph.rho)
+    n_it = sc.n_iters
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -563,58 +589,66 @@ def run_combined_form(workload="lmmew_64", n_real=16, lo=50_000, hi=500_000, ite
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
-    # plain FP32 exact path, one realisation at a time (after a warm-up call;
-    # the untimed calls with no iteration run the autotune of each class)
-    model.osem(devs[0], lam0.clone(), sc.n_subsets, 1)
+    # exact FP32, one realisation at a time (the untimed calls with no
+    # iteration sort and run the row-kernel autotune of each class: set-up)
     for d in devs:
         model.osem(d, lam0.clone(), sc.n_subsets, 0)
-    exact_imgs, t_exact = [], 0.0
+    seq, exact_roi = [], []
     for d in devs:
         img = lam0.clone()
-        t_exact += timed(lambda: model.osem(d, img, sc.n_subsets, iters))
-        exact_imgs.append(img.cpu().numpy().astype(np.float64))
-    # the combined form, with the network at every voxel and on the coarse
-    # grid (the first batched call of each tunes the launch shape)
-    out = {"workload": f"{n_real} realisations of {sc.name} with U[{lo}, {hi}] events "
-                       f"({int(sizes.sum())} events, resampled from one MC pool), "
-                       f"{sc.n_subsets} subsets x {iters} iterations each",
-           "surrogate_training": {"objects": n_objects, "samples": n_samples,
-                                  "sample_s": t_sample, "train_s": t_train},
-           "exact_fp32_one_at_a_time_s": t_exact}
-    for kind, key in (("surrogate", ""), ("surrogate_coarse", "coarse_")):
-        model.set_scatter_model(kind, sur)
+        seq.append(timed(lambda: model.osem(d, img, sc.n_subsets, n_it)))
+        exact_roi.append(roi_sums(img.cpu().numpy().astype(np.float64), ph.lesion_masks))
+    seq = np.asarray(seq)
+
+    def batched():
         imgs = lam0.repeat(n_real, 1).contiguous()
-        model.osem_batch(devs, imgs, sc.n_subsets, iters)
+        model.osem_batch(devs, imgs, sc.n_subsets, 1)          # tunes, warms up
         imgs = lam0.repeat(n_real, 1).contiguous()
-        t_comb = timed(lambda: model.osem_batch(devs, imgs, sc.n_subsets, iters))
-        model.set_scatter_model("exact")
-        comb = imgs.cpu().numpy().astype(np.float64)
-        dev_roi = []
-        for r in range(n_real):
-            ref = roi_sums(exact_imgs[r], ph.lesion_masks)
-            got = roi_sums(comb[r], ph.lesion_masks)
-            dev_roi.append([abs(a - b) / b for a, b in zip(got, ref)])
-        dev_roi = np.asarray(dev_roi)
-        out[key + "surrogate_bf16_batched_s"] = t_comb
-        out[key + "speedup_vs_exact_fp32"] = t_exact / t_comb
-        out[key + "roi_rel_dev_vs_exact"] = {"mean": float(dev_roi.mean()),
-                                             "max": float(dev_roi.max()),
-                                             "per_lesion_mean": dev_roi.mean(axis=0).tolist()}
+        sec = timed(lambda: model.osem_batch(devs, imgs, sc.n_subsets, n_it))
+        return sec, imgs.cpu().numpy().astype(np.float64)
+
+    t_batch, imgs_b = batched()
+    tune = model.batch_tuning()
+    dev_b = max(abs(a - b) / b for r in range(n_real)
+                for a, b in zip(roi_sums(imgs_b[r], ph.lesion_masks), exact_roi[r]))
+    elems = float(off[-1]) * model.nq * n_it
+    out = {"workload": f"{n_real} realisations of {sc.name} with U[{lo}, {hi}] events (seed "
+                       f"{seed}, {int(off[-1])} events: disjoint slices of one iid MC pool), "
+                       f"{sc.n_subsets} subsets x {n_it} iterations each",
+           "pool": {"generator": "synthetic.mc_torch on the GPU", "events": int(off[-1]),
+                    "generation_s": t_pool},
+           "one_at_a_time": {"realisations_per_s": n_real / float(seq.sum()),
+                             "elements_per_s": elems / float(seq.sum()),
+                             "recon_s_p50": float(np.percentile(seq, 50)),
+                             "recon_s_p99": float(np.percentile(seq, 99)),
+                             "total_s": float(seq.sum())},
+           "batched": {"realisations_per_s": n_real / t_batch,
+                       "elements_per_s": elems / t_batch,
+                       "batch_s": t_batch,
+                       "recon_latency_s": t_batch,
+                       "roi_max_rel_dev_vs_one_at_a_time": float(dev_b),
+                       "tuning": tune},
+           "speedup_batched_vs_one_at_a_time": float(seq.sum()) / t_batch}
+    # the combined form on the same realisations
+    sur, t_sample, t_train, _, _ = train_surrogate_on_random_objects(
+        sc, n_objects, n_samples, 20_000, sur_seed)
+    model.set_scatter_model("surrogate_coarse", sur)
+    t_comb, imgs_c = batched()
+    model.set_scatter_model("exact")
+    dev = np.asarray([[abs(a - b) / b for a, b in zip(roi_sums(imgs_c[r], ph.lesion_masks),
+                                                       exact_roi[r])] for r in range(n_real)])
+    out["combined"] = {"form": "BF16 tensor-core surrogate on the coarse grid + batched "
+                               "realisations in one CUDA graph",
+                       "surrogate_training": {"objects": n_objects, "samples": n_samples,
+                                              "sample_s": t_sample, "train_s": t_train},
+                       "batch_s": t_comb,
+                       "speedup_vs_exact_fp32_one_at_a_time": float(seq.sum()) / t_comb,
+                       "speedup_vs_exact_fp32_batched": t_batch / t_comb,
+                       "roi_rel_dev_vs_exact": {"mean": float(dev.mean()), "max": float(dev.max()),
+                                                "per_lesion_mean": dev.mean(axis=0).tolist()}}
     sur.close()
     model.close()
     return out
-
-
-def run_batch_forms():
-    """The batching form on two workloads: the scope's 256 realisations of
-    U[50k, 500k] events at 64^2 (one iteration each), and 256 realisations of
-    the paper's own study (64^2 of 4.6 mm, 120 angles, three windows,
-    U[8k, 12k] events around its ~10^4 per realisation, 4 subsets x 16
-    iterations), where every single reconstruction is too small to fill the
-    GPU."""
-    return {"lmmew_64_256": run_batch_form(),
-            "paper_study_256": run_batch_form(workload="paper_study", lo=8_000, hi=12_000,
-                                              iters=None, repeats=2, seed=31)}
 
 
 def run_batch_form(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, iters=1, repeats=2,
@@ -835,19 +869,28 @@ def run_gpu(args, rank, local_rank, world):
     if world == 1 and not args.no_forms and not args.events:
         model.close()
         runners = {"precision": run_precision_form, "batching": run_batch_forms,
-                   "comparison": run_comparison_form, "surrogate": run_surrogate_form,
-                   "combined": run_combined_form}
+                   "comparison": run_comparison_form, "surrogate": run_surrogate_form}
         line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}
-        comb = line["forms"].get("combined")
-        if comb:
-            # the metric's third part: the chosen forms together against the
-            # plain FP32 path on the same GPU, at the stated ROI-activity error
-            line["chosen_form"] = {
-                "form": "BF16 tensor-core surrogate on the coarse grid + batched realisations "
-                        "in one CUDA graph",
-                "workload": comb["workload"],
-                "speedup_vs_plain_fp32": comb["coarse_speedup_vs_exact_fp32"],
-                "roi_rel_dev_vs_plain_fp32": comb["coarse_roi_rel_dev_vs_exact"]}
+        # the metric's third part: the chosen forms against the plain FP32
+        # path on the same GPU, at the stated ROI-activity error, at the
+        # forms' own workloads
+        chosen = {"form": "BF16 tensor-core surrogate on the coarse grid (+ batched "
+                          "realisations in one CUDA graph where there are several)"}
+        c3 = line["forms"].get("batching", {}).get("lmmew_64_256", {}).get("combined")
+        if c3:
+            chosen["realisations_256"] = {
+                "workload": line["forms"]["batching"]["lmmew_64_256"]["workload"],
+                "speedup_vs_plain_fp32_one_at_a_time": c3["speedup_vs_exact_fp32_one_at_a_time"],
+                "speedup_vs_plain_fp32_batched": c3["speedup_vs_exact_fp32_batched"],
+                "roi_rel_dev_vs_plain_fp32": c3["roi_rel_dev_vs_exact"]}
+        c4 = line["forms"].get("surrogate")
+        if c4:
+            chosen["single_128_2m"] = {
+                "workload": c4["workload"],
+                "speedup_vs_plain_fp32": c4["surrogate_coarse"]["speedup_vs_exact"],
+                "roi_rel_dev_vs_plain_fp32": c4["surrogate_coarse"]["roi_rel_dev_vs_exact"]}
+        if len(chosen) > 1:
+            line["chosen_form"] = chosen
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

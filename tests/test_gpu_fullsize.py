@@ -24,14 +24,15 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def sample_indices(ev, n_angles, per_angle_groups, seed):
-    """A few events from spread-out angles (the oracle builds one table per angle)."""
+def sample_indices(ev, n_angles, per_angle_groups, seed, per_angle=3):
+    """A few events from spread-out angles (the oracle builds one table per
+    angle); per_angle_groups = n_angles takes every angle."""
     rng = np.random.default_rng(seed)
     angles = rng.choice(n_angles, size=per_angle_groups, replace=False)
     out = []
     for a in angles:
         idx = np.nonzero(ev.angle == a)[0]
-        out.extend(rng.choice(idx, size=min(3, idx.size), replace=False).tolist())
+        out.extend(rng.choice(idx, size=min(per_angle, idx.size), replace=False).tolist())
     return np.array(sorted(out))
 
 
@@ -40,8 +41,11 @@ def rand_image(ph, seed):
     return (rng.uniform(0.2, 3.0, ph.rho.size) * (ph.rho.reshape(-1) > 0)).astype(np.float32)
 
 
-@pytest.mark.parametrize("name,groups", [("lmmew_64", 8), ("lmmew_128", 3), ("lmmew_128_2m", 2)])
-def test_forward_sampled_parity_full_size(name, groups):
+@pytest.mark.parametrize("name,groups,per_angle", [("lmmew_64", 60, 1), ("lmmew_128", 120, 1),
+                                                   ("lmmew_128_2m", 4, 3)])
+def test_forward_sampled_parity_full_size(name, groups, per_angle):
+    """Every angle's point-run table is touched at 64^2 and 128^2 / 1 M
+    events (one sampled event per angle)."""
     sc = preset(name)
     ph = sc.make_phantom()
     ev = simulate_cached(sc)
@@ -50,7 +54,7 @@ def test_forward_sampled_parity_full_size(name, groups):
     lam = rand_image(ph, 11)
     y = gpu.forward(lm.DeviceEvents.from_list(ev), torch.from_numpy(lam).cuda()).cpu().numpy()
     assert np.all(np.isfinite(y)) and np.all(y > 0)
-    idx = sample_indices(ev, sc.n_angles, groups, seed=3)
+    idx = sample_indices(ev, sc.n_angles, groups, seed=3, per_angle=per_angle)
     orc = oracle.Model.from_scenario(sc, ph.rho)
     ref = orc.forward(ev.subset(idx), lam.astype(np.float64))
     rel = np.abs(y[idx].astype(np.float64) - ref) / ref
@@ -103,17 +107,20 @@ def test_osem_full_size_invariants_64():
 def test_batching_workload_full_size():
     """The batching workload in the launch configuration bench.py times:
     256 realisations of the 64 x 64 object with U[50k, 500k] events each,
-    resampled from one MC pool, one OSEM iteration of 8 subsets in one
-    lm_osem_batch call (71 M events, several row blocks per subset).  Sampled
-    realisations equal their own lm_osem runs to FP32 rounding (only the
-    back-projection chunk boundaries at row-block edges differ), and the
-    first one's forward projections match the FP64 oracle."""
+    disjoint slices of one iid pool from the GPU Monte-Carlo, one OSEM
+    iteration of 8 subsets in one lm_osem_batch call (71 M events, several
+    row blocks per subset).  Sampled realisations equal their own lm_osem
+    runs to FP32 rounding (only the back-projection chunk boundaries at
+    row-block edges differ), and the first one's forward projections match
+    the FP64 oracle."""
+    from synthetic import mc_torch
     sc = preset("lmmew_64")
     ph = sc.make_phantom()
-    pool = simulate_cached(sc)
     rng = np.random.default_rng(3)
     sizes = rng.integers(50_000, 500_001, size=256)
-    evs = [pool.subset(rng.integers(0, len(pool), size=int(k))) for k in sizes]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    pool = mc_torch.simulate(sc, int(off[-1]), seed=3, device="cuda")
+    evs = [pool.subset(slice(off[r], off[r + 1])) for r in range(256)]
     devs = [lm.DeviceEvents.from_list(e) for e in evs]
     gpu = lm.Model.from_scenario(sc, ph.rho)
     lam0 = (ph.rho.reshape(-1) > 0).astype(np.float32)

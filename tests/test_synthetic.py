@@ -4,6 +4,7 @@ the paper's structure (photopeaks plus a Compton continuum inside the window).""
 from __future__ import annotations
 
 import numpy as np
+import pytest
 
 from synthetic import preset, simulate
 
@@ -52,3 +53,28 @@ def test_pooled_generation_from_an_unguarded_script(tmp_path):
     out = subprocess.run([sys.executable, str(script)], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert "events 130000" in out.stdout
+
+
+def test_torch_monte_carlo_matches_numpy_monte_carlo():
+    """The torch port of the Monte-Carlo (used for large event pools on the
+    GPU) draws from the same distribution as synthetic.mc: two-sample
+    chi-square tests on angle, bin and energy-band histograms of 20 000
+    events each, and the same scattered fraction within 2 percentage
+    points; the same seed gives the same events."""
+    pytest.importorskip("torch")
+    from scipy import stats
+    from synthetic import mc_torch
+    sc = preset("small_24")
+    ev_t = mc_torch.simulate(sc, 20000, seed=5, device="cpu", batch=200000)
+    ev_n = simulate(sc, 20000, seed=5)
+    assert len(ev_t) == 20000
+    for f, k in ((lambda e: e.angle, sc.n_angles), (lambda e: e.bin, sc.n_bins)):
+        a, b = np.bincount(f(ev_t), minlength=k), np.bincount(f(ev_n), minlength=k)
+        m = (a + b) > 0
+        assert stats.chi2_contingency(np.vstack([a[m], b[m]]))[1] > 1e-3
+    bands = np.array([50.0, 75.0, 110.0, 200.0, 300.0])
+    a, b = np.histogram(ev_t.energy, bands)[0], np.histogram(ev_n.energy, bands)[0]
+    assert stats.chi2_contingency(np.vstack([a, b]))[1] > 1e-3
+    assert abs(ev_t.scattered.mean() - ev_n.scattered.mean()) < 0.02
+    again = mc_torch.simulate(sc, 5000, seed=5, device="cpu", batch=200000)
+    assert np.array_equal(again.energy, ev_t.energy[:5000])

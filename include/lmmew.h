@@ -34,11 +34,18 @@
  *   - events, images and outputs are DEVICE pointers owned by the caller; the
  *     library never frees or permutes them (it sorts a private copy);
  *   - work is queued on the caller's CUDA stream (a cudaStream_t; 0 = the
- *     legacy default stream).  Entry points that take events synchronise that
- *     stream once after validating them (to report out-of-range events and to
- *     size the work); the rest of the call runs asynchronously.  A device-side
- *     fault flag (a pipeline wait that ran out of time) is reported by the
- *     next call that synchronises;
+ *     legacy default stream).  lm_forward, lm_backproject and lm_osem with
+ *     the exact or the scatter-free model, and lm_forward_noalloc, queue
+ *     their kernels and return without waiting for the stream: events are
+ *     validated on the device and the work is sized from the event count
+ *     alone.  Errors found on the device (an event out of range, a pipeline
+ *     wait that ran out of time) set the handle's status word, which
+ *     lm_check reports (it synchronises the stream).  Set-up steps
+ *     synchronise: the first call of a subset partition (sensitivities,
+ *     group tables), scratch that has to grow, and lm_osem's first call of a
+ *     workload class (the launch-shape tuner, see lm_batch_tuning).
+ *     lm_osem_batch and the surrogate scatter models read the event counts
+ *     back once per call;
  *   - a handle serves one stream at a time;
  *   - there is no CPU fallback: every step runs in this library's kernels.
  *
@@ -153,8 +160,10 @@ int lm_sensitivity(lm_handle* h, int subset, double* out, lm_stream stream);
 /* Forward projection y_j = sum_q a_j[q] image[q] (the denominator of
  * Eq. z_bar_update_os), FP32 with hierarchical sums.  image: DEVICE
  * float[n*n] (pixels outside the support are ignored); out_y: DEVICE
- * float[events->n], in the caller's event order.
- * Errors: INVALID_ARG, OUT_OF_RANGE, OOM, CUDA, TIMEOUT. */
+ * float[events->n], in the caller's event order; an event out of range gets
+ * NaN and sets the status word (reported by lm_check).
+ * Errors (returned): INVALID_ARG, OOM, CUDA; (by lm_check) OUT_OF_RANGE,
+ * TIMEOUT. */
 int lm_forward(lm_handle* h, const lm_events* events, const float* image, float* out_y,
                lm_stream stream);
 
@@ -168,26 +177,31 @@ int lm_forward(lm_handle* h, const lm_events* events, const float* image, float*
  * all of its scratch in one 16 MiB array in the library's static device
  * memory, which every GPU that loads the library holds until the process
  * exits.  The call rejects, with LMMEW_ERR_INVALID_ARG and a message, event
- * counts whose scratch would exceed 16 MiB (about 27 + 4*ceil(nq/32) bytes
- * per event, nq = support voxels: some 180 000 events for a 32x32 model of
- * 484 voxels, 36 000 for a 128x128 model of 3 464); use lm_forward for
+ * counts whose scratch would exceed 16 MiB (about 31 + 4*ceil(nq/32) bytes
+ * per event, nq = support voxels: some 160 000 events for a 32x32 model of
+ * 484 voxels, 34 000 for a 128x128 model of 3 464); use lm_forward for
  * those.  Its first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture.  Every call shares the one array and
+ * first call before any stream capture.  The address is kept for the rest of
+ * the process, so the library must not be used across a cudaDeviceReset.
+ * Every call shares the one array and
  * it keeps the last call's contents (each call writes every word it reads
  * before reading it): calls that overlap on the GPU -- two streams, two host
  * threads, or a call queued before an earlier one finished on another
- * stream -- race, so serialise them.  Arguments and errors as lm_forward;
- * the caller still provides events, image and output.  It runs the exact and
- * the scatter-free models; the surrogate models keep a row block of the
- * whole event list, so with them it returns LMMEW_ERR_NOT_IMPLEMENTED (use
+ * stream -- race, so serialise them.  Like lm_forward it queues its work
+ * without waiting for the stream; events out of range get NaN and are
+ * reported by lm_check.  Arguments as lm_forward; the caller still provides
+ * events, image and output.  It runs the exact and the scatter-free models;
+ * the surrogate models keep a row block of the whole event list, so with
+ * them it returns LMMEW_ERR_NOT_IMPLEMENTED before queueing anything (use
  * lm_forward). */
 int lm_forward_noalloc(lm_handle* h, const lm_events* events, const float* image, float* out_y,
                        lm_stream stream);
 
 /* Back projection out[q] = sum_j weight_j a_j[q].  weight: DEVICE
  * float[events->n] in the caller's order; out_image: DEVICE float[n*n],
- * zero outside the support.  Errors: as lm_forward. */
+ * zero outside the support; events out of range contribute nothing.
+ * Errors: as lm_forward. */
 int lm_backproject(lm_handle* h, const lm_events* events, const float* weight,
                    float* out_image, lm_stream stream);
 
@@ -209,6 +223,14 @@ int lm_backproject(lm_handle* h, const lm_events* events, const float* weight,
 int lm_osem(lm_handle* h, const lm_events* events, int n_subsets, int n_iters,
             int start_iter, int start_subset, float* image, double* loglik,
             lm_stream stream);
+
+/* Waits for the stream, then reports (and clears) what the handle's earlier
+ * calls found on the device: LMMEW_ERR_OUT_OF_RANGE (an event's angle or bin
+ * outside the model, or its energy outside every window: the paper's events
+ * lie on the detector and in the windows, Sec. "Problem formulation"),
+ * LMMEW_ERR_TIMEOUT (a kernel's bounded pipeline wait ran out), or LMMEW_OK.
+ * Errors: INVALID_ARG, CUDA. */
+int lm_check(lm_handle* h, lm_stream stream);
 
 /* Arithmetic of the single-scatter sum (the reduced-precision form).
  * LMMEW_PREC_FP32 (default): every term in FP32.  LMMEW_PREC_FP16 /

@@ -165,7 +165,16 @@ class Model:
                                                     _stream(stream)))
         return out
 
-    def forward(self, events: DeviceEvents, image, out=None, stream=None):
+    def check(self, stream=None):
+        """lm_check: wait for the stream and raise LmmewError for what the
+        handle's earlier calls found on the device (an event out of range, a
+        pipeline wait that ran out of time)."""
+        _native.check(_native.load().lm_check(self._h, _stream(stream)))
+
+    def forward(self, events: DeviceEvents, image, out=None, stream=None, check=True):
+        """lm_forward.  The library queues its kernels without waiting; with
+        check (default) the call then waits and raises for errors found on
+        the device, with check=False it returns at once (call check() later)."""
         torch = _torch()
         image = image.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
         _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
@@ -177,11 +186,14 @@ class Model:
                                                 ctypes.c_void_p(image.data_ptr()),
                                                 ctypes.c_void_p(out.data_ptr()),
                                                 _stream(stream)))
+        if check:
+            self.check(stream)
         return out
 
-    def forward_noalloc(self, events: DeviceEvents, image, out, stream=None):
+    def forward_noalloc(self, events: DeviceEvents, image, out, stream=None, check=True):
         """lm_forward_noalloc: same result as forward(), no device allocation
-        inside the call (``image`` and ``out`` are caller-owned CUDA tensors)."""
+        inside the call (``image`` and ``out`` are caller-owned CUDA tensors);
+        ``check`` as in forward()."""
         torch = _torch()
         _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
         _require_cuda(out, "out", torch.float32, numel=len(events))
@@ -190,9 +202,12 @@ class Model:
                                                         ctypes.c_void_p(image.data_ptr()),
                                                         ctypes.c_void_p(out.data_ptr()),
                                                         _stream(stream)))
+        if check:
+            self.check(stream)
         return out
 
-    def backproject(self, events: DeviceEvents, weight, out=None, stream=None):
+    def backproject(self, events: DeviceEvents, weight, out=None, stream=None, check=True):
+        """lm_backproject; ``check`` as in forward()."""
         torch = _torch()
         weight = weight.to(device="cuda", dtype=torch.float32).contiguous().reshape(-1)
         _require_cuda(weight, "weight", torch.float32, numel=len(events))
@@ -204,11 +219,14 @@ class Model:
                                                     ctypes.c_void_p(weight.data_ptr()),
                                                     ctypes.c_void_p(out.data_ptr()),
                                                     _stream(stream)))
+        if check:
+            self.check(stream)
         return out
 
     def osem(self, events: DeviceEvents, image, n_subsets, n_iters, start_iter=0, start_subset=0,
-             loglik=None, stream=None):
-        """Run LM-OSEM in place on ``image`` (a float32 CUDA tensor of n*n)."""
+             loglik=None, stream=None, check=True):
+        """Run LM-OSEM in place on ``image`` (a float32 CUDA tensor of n*n);
+        ``check`` as in forward()."""
         torch = _torch()
         _require_cuda(image, "image", torch.float32, numel=self.n * self.n)
         if loglik is not None:
@@ -220,6 +238,8 @@ class Model:
                                              int(n_iters), int(start_iter), int(start_subset),
                                              ctypes.c_void_p(image.data_ptr()), llp,
                                              _stream(stream)))
+        if check:
+            self.check(stream)
         return image
 
     def osem_batch(self, events_list, images, n_subsets, n_iters, loglik=None, stream=None):

@@ -83,6 +83,7 @@ SYMBOLS = {
     "lm_batch_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "lm_set_tile_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_set_energy_pruning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lm_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lm_last_error": (ctypes.c_char_p, []),
     "lm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

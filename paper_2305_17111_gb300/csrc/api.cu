@@ -54,32 +54,26 @@ int ensure(lm_handle* h, Scratch& s, size_t bytes, cudaStream_t st) {
 // the FP32 form has the small-tile kernels) x work-unit order at the
 // occupancy limit of CTAs per SM, then the best of those with one CTA per SM
 // fewer.  The sample runs without forward sums or stored rows.  The choice
-// is kept per handle for each workload class: log2 of the sample's mean
-// events per angle, the scatter model and the precision.  The sorted events
-// leave re-cut into tiles of the chosen size.  Every choice gives
-// bit-identical results: a tile's size changes only which exact-zero terms
-// it skips.
+// is kept per handle for each workload class: log2 of the call's mean
+// events per angle, the scatter model, the precision and whether energy
+// classes are on, so a call of a class tuned before needs no event counts on
+// the host.  Every choice gives bit-identical results: a tile's size changes
+// only which exact-zero terms it skips.
 constexpr int64_t kTuneEvents = 16384;
 
-int autotune_row(lm_handle* h, SortedEvents& se, int first_ranks, cudaStream_t st) {
-    // whole angle ranks (each n_classes groups) of the first subset
-    const int C = se.n_classes;
-    int g1 = 0, ng = 0;
-    int64_t ev = 0;
-    for (int r = 0; r < first_ranks && ev < kTuneEvents; ++r) {
-        const int64_t c = se.h_group_start[(r + 1) * C] - se.h_group_start[r * C];
-        ev += c;
-        ng += c > 0;
-        g1 = (r + 1) * C;
-    }
-    if (ev == 0) return recut_tiles(h, &se, h->tile_ev, st);
+uint64_t tune_key_for(const lm_handle* h, double mean_events_per_angle) {
     int bucket = 0;
-    while (bucket < 40 && (int64_t(2) << bucket) <= ev / ng) ++bucket;
-    const uint64_t key = 1ull | ((uint64_t)bucket << 8) | ((uint64_t)h->scatter_model << 4) |
-                         ((uint64_t)h->prec << 2) | ((uint64_t)(h->n_classes > 1) << 1);
-    // the class in use keeps the current shape (it may have been set by
-    // lm_set_tile_events); a class tuned before gets its stored shape back
-    if (h->tune_key == key) return recut_tiles(h, &se, h->tile_ev, st);
+    while (bucket < 40 && (double)(int64_t(2) << bucket) <= mean_events_per_angle) ++bucket;
+    return 1ull | ((uint64_t)bucket << 8) | ((uint64_t)h->scatter_model << 4) |
+           ((uint64_t)h->prec << 2) | ((uint64_t)(h->n_classes > 1) << 1);
+}
+
+// True if the class has a shape: the class in use keeps the current one (it
+// may have been set by lm_set_tile_events), a class tuned before gets its
+// stored shape back, the surrogate models take 128-event tiles (the network
+// kernel dominates and has its own launch shape).
+bool tune_known(lm_handle* h, uint64_t key) {
+    if (h->tune_key == key) return true;
     const auto hit = h->tune_cache.find(key);
     if (hit != h->tune_cache.end()) {
         h->tile_ev = hit->second.tile_ev;
@@ -87,18 +81,33 @@ int autotune_row(lm_handle* h, SortedEvents& se, int first_ranks, cudaStream_t s
         h->grid_per_sm = hit->second.grid_per_sm;
         h->tune_ms = hit->second.ms;
         h->tune_key = key;
-        return recut_tiles(h, &se, h->tile_ev, st);
+        return true;
     }
     if (h->scatter_model == LMMEW_SCATTER_SURROGATE ||
         h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE) {
-        // the network kernel dominates and has its own launch shape
         h->tile_ev = kET;
         h->unit_order = 0;
         h->grid_per_sm = 0;
         h->tune_key = key;
         h->tune_ms = 0.f;
-        return recut_tiles(h, &se, kET, st);
+        return true;
     }
+    return false;
+}
+
+// Times the candidates on the sorted events (host counts required) and
+// stores the choice for the class; the events leave re-cut into tiles of the
+// chosen size.
+int autotune_run(lm_handle* h, SortedEvents& se, int first_ranks, uint64_t key, cudaStream_t st) {
+    // whole angle ranks (each n_classes groups) of the first subset
+    const int C = se.n_classes;
+    int g1 = 0;
+    int64_t ev = 0;
+    for (int r = 0; r < first_ranks && ev < kTuneEvents; ++r) {
+        ev += se.h_group_start[(r + 1) * C] - se.h_group_start[r * C];
+        g1 = (r + 1) * C;
+    }
+    if (ev == 0) return recut_tiles(h, &se, h->tile_ev, st);
     const bool small_tiles = h->prec == 0 && h->mc.W <= 4;
     const int sizes[3] = {kET, 64, 32};
     const int n_sizes = small_tiles ? 3 : 1;
@@ -179,6 +188,14 @@ int autotune_row(lm_handle* h, SortedEvents& se, int first_ranks, cudaStream_t s
     return recut_tiles(h, &se, best_size, st);
 }
 
+// The tuner for callers whose sort read the counts back (the batch and the
+// planned paths): the class from the call's mean events per angle.
+int autotune_row(lm_handle* h, SortedEvents& se, int first_ranks, cudaStream_t st) {
+    const uint64_t key = tune_key_for(h, (double)se.n_total / h->mc.A);
+    if (tune_known(h, key)) return recut_tiles(h, &se, h->tile_ev, st);
+    return autotune_run(h, se, first_ranks, key, st);
+}
+
 struct Chunk {
     int t0, t1;         // tile range
     int64_t e0, e1;     // sorted event range
@@ -239,6 +256,46 @@ int launch_row_profiled(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     h->prof_terms_dense += (double)L.n_events * (double)h->terms_per_event;
     h->prof_elems += (double)L.n_events * (double)h->mc.nq;
     return LMMEW_OK;
+}
+
+ForwardPlan forward_plan(const lm_handle* h, int64_t n, int64_t cap_max) {
+    ForwardPlan p;
+    p.G = sort_groups(h, h->mc.A);
+    const int te = h->tile_ev;
+    p.n = n;
+    p.cap = std::max<int64_t>(te, std::min<int64_t>(n + (int64_t)p.G * te, cap_max));
+    p.tpc = (int)(p.cap / te);
+    p.blocks = (int)((((n + te - 1) / te) + p.G + p.tpc - 1) / p.tpc);
+    return p;
+}
+
+size_t forward_region_bytes(const lm_handle* h, const ForwardPlan& p) {
+    return sort_scratch_bytes(p.n, p.G) + bump_bytes(sizeof(float) * h->mc.nq) +
+           bump_bytes(sizeof(float) * (size_t)h->mc.nqt * p.cap) +
+           bump_bytes(sizeof(ChunkRange) * (size_t)p.blocks);
+}
+
+int forward_async(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
+                  const GroupArrays& ga, const ForwardPlan& p, char* arena, cudaStream_t st) {
+    SortedEvents se;
+    int rc = sort_events_async(h, ev, ga, p.G, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    float* lam_v = bump<float>(arena, h->mc.nq);
+    float* ypart = bump<float>(arena, (size_t)h->mc.nqt * p.cap);
+    ChunkRange* ranges = bump<ChunkRange>(arena, p.blocks);
+    rc = launch_gather_image(h, image, lam_v, st);
+    if (rc == LMMEW_OK) rc = launch_plan(h, se, 1, p.blocks, p.tpc, ranges, st);
+    for (int k = 0; k < p.blocks && rc == LMMEW_OK; ++k) {
+        RowLaunch L{se.tiles, 0, p.tpc, se.bin, se.energy, lam_v, nullptr, 0, 0, ypart, p.cap,
+                    k == 0 ? p.n : 0};
+        L.tile_ev = se.tile_ev;
+        L.range = ranges + k;
+        rc = launch_row_profiled(h, L, st);
+        if (rc == LMMEW_OK)
+            rc = launch_forward_out_range(h, ypart, p.cap, p.cap, ranges + k, se.perm, out_y, st);
+    }
+    if (rc == LMMEW_OK) rc = launch_invalid_out(h, se.group_start + p.G, p.n, se.perm, out_y, st);
+    return rc;
 }
 
 }  // namespace lmmew
@@ -393,6 +450,7 @@ int lm_destroy(lm_handle* h) {
     cudaFree(h->d_sens_a_prim);
     cudaFree(h->d_status);
     cudaFree(h->d_sens_sub);
+    for (auto& kv : h->grp_cache) cudaFree(kv.second);
     cudaFree(h->scratch_sort.ptr);
     cudaFree(h->scratch_work.ptr);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
@@ -424,8 +482,12 @@ int lm_sensitivity(lm_handle* h, int subset, double* out, lm_stream stream) {
     return launch_scatter_image_d(h, src, out, st);
 }
 
-int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
-               lm_stream stream) {
+// The planned forms of lm_forward / lm_backproject / lm_osem: the sort's
+// counts are read back and the row blocks planned on the host.  The
+// surrogate scatter models use them (their network kernel takes host tile
+// ranges).
+static int forward_planned(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
+                           lm_stream stream) {
     int rc = check_events(h, ev);
     if (rc != LMMEW_OK) return rc;
     if (ev->n > 0 && (!image || !out_y)) return set_error(LMMEW_ERR_INVALID_ARG, "NULL image/output");
@@ -473,8 +535,8 @@ int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out
     return LMMEW_OK;
 }
 
-int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float* out_image,
-                   lm_stream stream) {
+static int backproject_planned(lm_handle* h, const lm_events* ev, const float* weight,
+                               float* out_image, lm_stream stream) {
     int rc = check_events(h, ev);
     if (rc != LMMEW_OK) return rc;
     if (!out_image || (ev->n > 0 && !weight))
@@ -527,8 +589,9 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
     return launch_num_to_image(h, num, out_image, st);
 }
 
-int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int start_iter,
-            int start_subset, float* image, double* loglik, lm_stream stream) {
+static int osem_planned(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters,
+                        int start_iter, int start_subset, float* image, double* loglik,
+                        lm_stream stream) {
     int rc = check_events(h, ev);
     if (rc != LMMEW_OK) return rc;
     const ModelConst& m = h->mc;
@@ -615,6 +678,180 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
         }
     }
     return launch_scatter_image(h, lam_v, image, st);
+}
+
+static bool surrogate_model(const lm_handle* h) {
+    return h->scatter_model == LMMEW_SCATTER_SURROGATE ||
+           h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE;
+}
+
+int lm_forward(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
+               lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    if (ev->n > 0 && (!image || !out_y)) return set_error(LMMEW_ERR_INVALID_ARG, "NULL image/output");
+    if (ev->n == 0) return LMMEW_OK;
+    if (surrogate_model(h)) return forward_planned(h, ev, image, out_y, stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    GroupArrays ga;
+    rc = group_arrays(h, 1, &ga);
+    if (rc != LMMEW_OK) return rc;
+    const ForwardPlan fp = forward_plan(h, ev->n, (int64_t)(kRowBudgetFloats / h->mc.nqt));
+    rc = ensure(h, h->scratch_sort, forward_region_bytes(h, fp), st);
+    if (rc != LMMEW_OK) return rc;
+    return forward_async(h, ev, image, out_y, ga, fp, (char*)h->scratch_sort.ptr, st);
+}
+
+int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float* out_image,
+                   lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    if (!out_image || (ev->n > 0 && !weight))
+        return set_error(LMMEW_ERR_INVALID_ARG, "NULL weight/output");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ModelConst& m = h->mc;
+    if (ev->n == 0) {
+        LMMEW_CUDA(cudaMemsetAsync(out_image, 0, sizeof(float) * m.n * m.n, st));
+        return LMMEW_OK;
+    }
+    if (surrogate_model(h)) return backproject_planned(h, ev, weight, out_image, stream);
+    GroupArrays ga;
+    rc = group_arrays(h, 1, &ga);
+    if (rc != LMMEW_OK) return rc;
+    const int64_t n = ev->n;
+    const int G = sort_groups(h, m.A), rs = row_stride_of(h);
+    const ForwardPlan fp = forward_plan(h, n, (int64_t)(kRowBudgetFloats / rs));
+    const int64_t ppc = bp_parts(fp.cap);
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(n, G), st);
+    if (rc == LMMEW_OK)
+        rc = ensure(h, h->scratch_work,
+                    bump_bytes(sizeof(float) * (size_t)rs * fp.cap) +
+                        bump_bytes(sizeof(float) * (size_t)fp.blocks * ppc * m.nq) +
+                        bump_bytes(sizeof(double) * m.nq) +
+                        bump_bytes(sizeof(ChunkRange) * (size_t)fp.blocks),
+                    st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events_async(h, ev, ga, G, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* rows = bump<float>(w, (size_t)rs * fp.cap);
+    float* bpart = bump<float>(w, (size_t)fp.blocks * ppc * m.nq);
+    double* num = bump<double>(w, m.nq);
+    ChunkRange* ranges = bump<ChunkRange>(w, fp.blocks);
+    rc = launch_plan(h, se, 1, fp.blocks, fp.tpc, ranges, st);
+    for (int k = 0; k < fp.blocks && rc == LMMEW_OK; ++k) {
+        RowLaunch L{se.tiles, 0, fp.tpc, se.bin, se.energy, nullptr, rows, 0, rs, nullptr, 0,
+                    k == 0 ? n : 0};
+        L.tile_ev = se.tile_ev;
+        L.range = ranges + k;
+        rc = launch_row_profiled(h, L, st);
+        if (rc == LMMEW_OK)
+            rc = launch_bp_partial_range(h, rows, rs, nullptr, 0, fp.cap, ranges + k, se.perm,
+                                         weight, bpart, (int64_t)k * ppc, nullptr, st);
+    }
+    if (rc == LMMEW_OK) rc = launch_voxel_reduce_ranges(h, bpart, ranges, fp.blocks, ppc, num, st);
+    if (rc != LMMEW_OK) return rc;
+    return launch_num_to_image(h, num, out_image, st);
+}
+
+int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int start_iter,
+            int start_subset, float* image, double* loglik, lm_stream stream) {
+    int rc = check_events(h, ev);
+    if (rc != LMMEW_OK) return rc;
+    const ModelConst& m = h->mc;
+    if (!image) return set_error(LMMEW_ERR_INVALID_ARG, "image is NULL");
+    if (n_subsets < 1 || n_subsets > m.A)
+        return set_error(LMMEW_ERR_INVALID_ARG, "n_subsets must be in 1..n_angles");
+    if (n_iters < 0 || start_iter < 0 || start_iter > n_iters || start_subset < 0 ||
+        start_subset >= n_subsets)
+        return set_error(LMMEW_ERR_INVALID_ARG, "iteration range out of bounds");
+    if (surrogate_model(h))
+        return osem_planned(h, ev, n_subsets, n_iters, start_iter, start_subset, image, loglik,
+                            stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = subset_sensitivity(h, n_subsets, st);
+    if (rc != LMMEW_OK) return rc;
+    GroupArrays ga;
+    rc = group_arrays(h, n_subsets, &ga);
+    if (rc != LMMEW_OK) return rc;
+    const int64_t n = ev->n;
+    const int G = sort_groups(h, m.A);
+    rc = ensure(h, h->scratch_sort, sort_scratch_bytes(n, G), st);
+    if (rc != LMMEW_OK) return rc;
+    char* arena = (char*)h->scratch_sort.ptr;
+    SortedEvents se;
+    rc = sort_events_async(h, ev, ga, G, &se, arena, st);
+    if (rc != LMMEW_OK) return rc;
+    // launch shape: a class tuned before needs no counts; a new class is
+    // tuned once (set-up: the counts are read back and trial launches timed)
+    const int first_ranks = (m.A + n_subsets - 1) / n_subsets;
+    const uint64_t key = tune_key_for(h, (double)n / m.A);
+    if (!tune_known(h, key)) {
+        rc = read_back_counts(h, &se, st);
+        if (rc == LMMEW_OK) rc = autotune_run(h, se, first_ranks, key, st);
+        if (rc != LMMEW_OK) return rc;
+    }
+    rc = recut_tiles_async(h, &se, h->tile_ev, st);
+    if (rc != LMMEW_OK) return rc;
+
+    // row blocks of whole tiles, sized from the event count alone: a subset
+    // has at most ceil(n / tile_ev) + (its groups) tiles
+    const int te = se.tile_ev, C = se.n_classes, rs = row_stride_of(h);
+    const int64_t g_sub = (int64_t)first_ranks * C;
+    const int64_t cap = std::max<int64_t>(
+        te, std::min<int64_t>(n + g_sub * te, (int64_t)(kRowBudgetFloats / rs)));
+    const int tpc = (int)(cap / te);
+    const int blocks = (int)((((n + te - 1) / te) + g_sub + tpc - 1) / tpc);
+    const int64_t ppc = bp_parts(cap);
+    rc = ensure(h, h->scratch_work,
+                bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * (size_t)rs * cap) +
+                    bump_bytes(sizeof(float) * (size_t)m.nqt * cap) +
+                    bump_bytes(sizeof(float) * (size_t)blocks * ppc * m.nq) +
+                    bump_bytes(sizeof(double) * (size_t)blocks * ppc) +
+                    bump_bytes(sizeof(double) * m.nq) +
+                    bump_bytes(sizeof(ChunkRange) * (size_t)n_subsets * blocks),
+                st);
+    if (rc != LMMEW_OK) return rc;
+    char* w = (char*)h->scratch_work.ptr;
+    float* lam_v = bump<float>(w, m.nq);
+    float* rows = bump<float>(w, (size_t)rs * cap);
+    float* ypart = bump<float>(w, (size_t)m.nqt * cap);
+    float* bpart = bump<float>(w, (size_t)blocks * ppc * m.nq);
+    double* llpart = bump<double>(w, (size_t)blocks * ppc);
+    double* num = bump<double>(w, m.nq);
+    ChunkRange* ranges = bump<ChunkRange>(w, (size_t)n_subsets * blocks);
+    rc = launch_gather_image(h, image, lam_v, st);
+    if (rc == LMMEW_OK) rc = launch_plan(h, se, n_subsets, blocks, tpc, ranges, st);
+    for (int it = start_iter; it < n_iters && rc == LMMEW_OK; ++it) {
+        for (int s = (it == start_iter ? start_subset : 0); s < n_subsets && rc == LMMEW_OK; ++s) {
+            const ChunkRange* rg = ranges + (size_t)s * blocks;
+            for (int k = 0; k < blocks && rc == LMMEW_OK; ++k) {
+                RowLaunch L{se.tiles, 0, tpc, se.bin, se.energy, lam_v, rows, 0, rs, ypart, cap,
+                            (s == 0 && k == 0) ? n : 0};
+                L.tile_ev = te;
+                L.range = rg + k;
+                rc = launch_row_profiled(h, L, st);
+                if (rc == LMMEW_OK)
+                    rc = launch_bp_partial_range(h, rows, rs, ypart, cap, cap, rg + k, nullptr,
+                                                 nullptr, bpart, (int64_t)k * ppc, llpart, st);
+            }
+            if (rc == LMMEW_OK) rc = launch_voxel_reduce_ranges(h, bpart, rg, blocks, ppc, num, st);
+            if (rc == LMMEW_OK)
+                rc = launch_update_ranges(h, lam_v, num, h->d_sens_sub + (size_t)s * m.nq, llpart,
+                                          rg, blocks, ppc,
+                                          loglik ? loglik + (size_t)it * n_subsets + s : nullptr,
+                                          st);
+        }
+    }
+    if (rc != LMMEW_OK) return rc;
+    return launch_scatter_image(h, lam_v, image, st);
+}
+
+int lm_check(lm_handle* h, lm_stream stream) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    return take_status(h, (cudaStream_t)stream);
 }
 
 int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subsets, int n_iters,

@@ -69,6 +69,92 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_partial(
     bpart[(size_t)(row0 + blockIdx.x) * nq + q] = acc;
 }
 
+// The same with the chunk's size on the device (range: sorted events
+// [z, w)); rows, ypart and weights are indexed from z, blocks past the
+// chunk's events return at once.
+__global__ void __launch_bounds__(kBpVoxels) k_bp_partial_range(
+    const float* rows, int row_stride, const float* ypart, int64_t ypart_stride, int nqt,
+    const ChunkRange* range, const uint32_t* perm, const float* weight, int nq, float* bpart,
+    int64_t slot0, double* llpart) {
+    __shared__ float r[kBpEvents];
+    __shared__ double ll[kBpEvents];
+    const ChunkRange R = *range;
+    const int64_t count = (int64_t)R.w - R.z;
+    const int t = threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.x * kBpEvents;
+    if (j0 >= count) return;
+    if (t < kBpEvents) {
+        const int64_t j = j0 + t;
+        float rv = 0.f;
+        double lv = 0.0;
+        if (j < count) {
+            if (weight) {
+                rv = weight[perm[R.z + j]];
+            } else {
+                float y = 0.f;
+                for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
+                if (y > 0.f) {
+                    rv = 1.0f / y;
+                    lv = log((double)y);
+                }
+            }
+        }
+        r[t] = rv;
+        ll[t] = lv;
+    }
+    __syncthreads();
+    if (llpart && blockIdx.y == 0) {
+        for (int off = kBpEvents / 2; off > 0; off >>= 1) {
+            if (t < off) ll[t] += ll[t + off];
+            __syncthreads();
+        }
+        if (t == 0) llpart[slot0 + blockIdx.x] = ll[0];
+    }
+    const int q = blockIdx.y * kBpVoxels + t;
+    if (q >= nq) return;
+    const int64_t rem = count - j0;
+    const int n_here = rem < kBpEvents ? (int)rem : kBpEvents;
+    const float* rp = rows + (size_t)j0 * row_stride + q;
+    float acc = 0.f;
+    for (int e = 0; e < n_here; ++e) acc = fmaf(r[e], rp[(size_t)e * row_stride], acc);
+    bpart[(size_t)(slot0 + blockIdx.x) * nq + q] = acc;
+}
+
+__device__ __forceinline__ int64_t parts_of(const ChunkRange& R) {
+    return ((int64_t)R.w - R.z + kBpEvents - 1) / kBpEvents;
+}
+
+// Voxel sums over the partials of n_blocks row blocks, block k's at slots
+// [k ppc, k ppc + its parts), in slot order.
+__global__ void k_voxel_reduce_ranges(const float* bpart, const ChunkRange* ranges, int n_blocks,
+                                      int64_t ppc, int nq, double* num) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double acc = 0.0;
+    for (int k = 0; k < n_blocks; ++k) {
+        const int64_t parts = parts_of(ranges[k]);
+        for (int64_t i = 0; i < parts; ++i) acc += (double)bpart[(size_t)(k * ppc + i) * nq + q];
+    }
+    num[q] = acc;
+}
+
+__global__ void k_forward_out_range(const float* ypart, int64_t stride, int nqt,
+                                    const ChunkRange* range, const uint32_t* perm, float* out_y) {
+    const ChunkRange R = *range;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (int64_t)R.w - R.z) return;
+    float y = 0.f;
+    for (int t = 0; t < nqt; ++t) y += ypart[(size_t)t * stride + j];
+    out_y[perm[R.z + j]] = y;
+}
+
+// Events that failed validation sort after the valid ones: their outputs
+// are NaN (the status word tells the next synchronising call).
+__global__ void k_invalid_out(const int* n_valid, int64_t n, const uint32_t* perm, float* out_y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && i >= *n_valid) out_y[perm[i]] = __int_as_float(0x7fc00000);
+}
+
 __global__ void k_voxel_reduce(const float* bpart, int64_t n_parts, int nq, double* num) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
@@ -77,15 +163,25 @@ __global__ void k_voxel_reduce(const float* bpart, int64_t n_parts, int nq, doub
     num[q] = acc;
 }
 
-// Single block: log-likelihood at the incoming image, then the update.
+// Single block: log-likelihood at the incoming image, then the update.  The
+// log terms are the n_ll partials at llpart, or (ranges set) the partials of
+// n_ll row blocks, block k's at slots [k ppc, k ppc + its parts).
 __global__ void __launch_bounds__(1024) k_update(float* lam, const double* num, const double* sens,
                                                  int nq, const double* llpart, int64_t n_ll,
-                                                 double* loglik) {
+                                                 double* loglik, const ChunkRange* ranges = nullptr,
+                                                 int64_t ppc = 0) {
     __shared__ double red[1024];
     const int t = threadIdx.x;
     if (loglik) {
         double s = 0.0;
-        for (int64_t i = t; i < n_ll; i += 1024) s += llpart[i];
+        if (ranges) {
+            for (int64_t k = 0; k < n_ll; ++k) {
+                const int64_t parts = parts_of(ranges[k]);
+                for (int64_t i = t; i < parts; i += 1024) s += llpart[k * ppc + i];
+            }
+        } else {
+            for (int64_t i = t; i < n_ll; i += 1024) s += llpart[i];
+        }
         for (int q = t; q < nq; q += 1024) s -= (double)lam[q] * sens[q];
         red[t] = s;
         __syncthreads();
@@ -159,6 +255,59 @@ int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, doubl
 int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
                   const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st) {
     k_update<<<1, 1024, 0, st>>>(lam_v, num, sens, h->mc.nq, llpart, n_ll, loglik_out);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_forward_out_range(lm_handle* h, const float* ypart, int64_t ypart_stride,
+                             int64_t capacity, const ChunkRange* range, const uint32_t* perm,
+                             float* out_y, cudaStream_t st) {
+    if (capacity <= 0) return LMMEW_OK;
+    k_forward_out_range<<<(unsigned)((capacity + 255) / 256), 256, 0, st>>>(
+        ypart, ypart_stride, h->mc.nqt, range, perm, out_y);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_invalid_out(lm_handle* h, const int* n_valid, int64_t n, const uint32_t* perm,
+                       float* out_y, cudaStream_t st) {
+    if (n <= 0) return LMMEW_OK;
+    k_invalid_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n_valid, n, perm, out_y);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_bp_partial_range(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                            int64_t ypart_stride, int64_t capacity, const ChunkRange* range,
+                            const uint32_t* perm, const float* weight, float* bpart,
+                            int64_t slot0, double* llpart, cudaStream_t st) {
+    if (capacity <= 0) return LMMEW_OK;
+    const int nq = h->mc.nq;
+    dim3 g((unsigned)((capacity + kBpEvents - 1) / kBpEvents), (nq + kBpVoxels - 1) / kBpVoxels);
+    k_bp_partial_range<<<g, kBpVoxels, 0, st>>>(rows, row_stride, ypart, ypart_stride, h->mc.nqt,
+                                                range, perm, weight, nq, bpart, slot0, llpart);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_voxel_reduce_ranges(lm_handle* h, const float* bpart, const ChunkRange* ranges,
+                               int n_blocks, int64_t ppc, double* num, cudaStream_t st) {
+    k_voxel_reduce_ranges<<<(h->mc.nq + 255) / 256, 256, 0, st>>>(bpart, ranges, n_blocks, ppc,
+                                                                  h->mc.nq, num);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+int launch_update_ranges(lm_handle* h, float* lam_v, const double* num, const double* sens,
+                         const double* llpart, const ChunkRange* ranges, int n_blocks,
+                         int64_t ppc, double* loglik_out, cudaStream_t st) {
+    k_update<<<1, 1024, 0, st>>>(lam_v, num, sens, h->mc.nq, llpart, n_blocks, loglik_out, ranges,
+                                 ppc);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

@@ -303,7 +303,7 @@ Windows windows_of(const ModelConst& m) {
                    make_float4(w[6][0], w[6][1], w[7][0], w[7][1])};
 }
 
-// The sort shared by sort_events and sort_events_fixed: keys, radix passes,
+// The sort shared by sort_events and sort_events_async: keys, radix passes,
 // gather, group bounds and tiles of the G = A * n_classes groups, all on
 // the caller's stream.  rank_of_angle [A], angle_of_group and lines_of_group
 // [G] are device arrays already filled.
@@ -428,13 +428,164 @@ int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* 
     rc = status_error(status);
     if (rc != LMMEW_OK) return rc;
     out->n_valid = out->h_group_start[G];
+    out->n_total = n;
     return LMMEW_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Variant for callers that cannot allocate: every buffer comes from a
-// caller-provided region, no host container is built, and the host reads
-// back only three integers.  Angles keep their natural order (one subset).
+// The sort without host read-back (lm_forward, lm_backproject, lm_osem).
+
+// Rank of each angle, angle and line mask of each group, for a partition into
+// n_subsets: built on the host and copied once per partition and class set
+// (set-up, like the subset sensitivities), then reused by every call.
+int group_arrays(lm_handle* h, int n_subsets, GroupArrays* out) {
+    const int A = h->mc.A, C = h->n_classes, G = A * C;
+    if (h->grp_classes != C) {
+        for (auto& kv : h->grp_cache) cudaFree(kv.second);
+        h->grp_cache.clear();
+        h->grp_classes = C;
+    }
+    auto it = h->grp_cache.find(n_subsets);
+    if (it == h->grp_cache.end()) {
+        std::vector<int> buf((size_t)A + 2 * (size_t)G);
+        int* rank_of_angle = buf.data();
+        int* angle_of_group = rank_of_angle + A;
+        int* lines_of_group = angle_of_group + G;
+        int r = 0;
+        for (int s = 0; s < n_subsets; ++s)
+            for (int a = s; a < A; a += n_subsets) {
+                rank_of_angle[a] = r;
+                for (int c = 0; c < C; ++c) {
+                    angle_of_group[r * C + c] = a;
+                    lines_of_group[r * C + c] = h->class_lines[c];
+                }
+                ++r;
+            }
+        int* d = nullptr;
+        if (cudaMalloc(&d, sizeof(int) * buf.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(LMMEW_ERR_OOM, "cannot allocate the sort's group arrays");
+        }
+        const cudaError_t e = cudaMemcpy(d, buf.data(), sizeof(int) * buf.size(),
+                                         cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_error(e, "cudaMemcpy(group arrays)");
+        }
+        it = h->grp_cache.emplace(n_subsets, d).first;
+    }
+    out->rank_of_angle = it->second;
+    out->angle_of_group = it->second + A;
+    out->lines_of_group = it->second + A + G;
+    return LMMEW_OK;
+}
+
+int sort_events_async(lm_handle* h, const lm_events* ev, const GroupArrays& ga, int G,
+                      SortedEvents* out, char*& arena, cudaStream_t st) {
+    const int64_t n = ev->n;
+    uint32_t* keys0 = bump<uint32_t>(arena, n);
+    uint32_t* keys1 = bump<uint32_t>(arena, n);
+    uint32_t* vals0 = bump<uint32_t>(arena, n);
+    uint32_t* vals1 = bump<uint32_t>(arena, n);
+    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
+    uint32_t* hist = bump<uint32_t>(arena, 256 * std::max<int64_t>(nblk, 1));
+    out->perm = bump<uint32_t>(arena, n);
+    out->bin = bump<uint16_t>(arena, n);
+    out->energy = bump<float>(arena, n);
+    out->group_start = bump<int>(arena, G + 1);
+    out->tile_start = bump<int>(arena, G + 1);
+    out->tiles = bump<Tile>(arena, n / kETMin + G + 1);
+    out->tile_ev = h->tile_ev;
+    out->n_groups = G;
+    out->n_classes = h->n_classes;
+    out->angle_of_group = ga.angle_of_group;
+    out->lines_of_group = ga.lines_of_group;
+    out->n_total = n;
+    return sort_and_tile(h, ev, G, ga.rank_of_angle, ga.angle_of_group, ga.lines_of_group, keys0,
+                         keys1, vals0, vals1, hist, out->perm, out->bin, out->energy,
+                         out->group_start, out->tile_start, out->tile_ev, out->tiles, st);
+}
+
+int read_back_counts(lm_handle* h, SortedEvents* se, cudaStream_t st) {
+    const int G = se->n_groups;
+    se->h_group_start.resize(G + 1);
+    se->h_tile_start.resize(G + 1);
+    int status = 0;
+    LMMEW_CUDA(cudaMemcpyAsync(se->h_group_start.data(), se->group_start, sizeof(int) * (G + 1),
+                               cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(se->h_tile_start.data(), se->tile_start, sizeof(int) * (G + 1),
+                               cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    const int rc = status_error(status);
+    if (rc != LMMEW_OK) return rc;
+    se->n_valid = se->h_group_start[G];
+    return LMMEW_OK;
+}
+
+int take_status(lm_handle* h, cudaStream_t st) {
+    int status = 0;
+    LMMEW_CUDA(cudaStreamSynchronize(st));
+    LMMEW_CUDA(cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
+    return status_error(status);
+}
+
+int recut_tiles_async(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st) {
+    if (tile_ev != 32 && tile_ev != 64 && tile_ev != kET)
+        return set_error(LMMEW_ERR_INVALID_ARG, "tile size must be 32, 64 or 128 events");
+    if (se->tile_ev == tile_ev) return LMMEW_OK;
+    const int G = se->n_groups;
+    k_tile_scan<<<1, 1024, 0, st>>>(se->group_start, G, tile_ev, se->tile_start);
+    k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->group_start, se->tile_start,
+                                                         se->angle_of_group, G, tile_ev, se->bin,
+                                                         se->lines_of_group, se->tiles);
+    h->launches += 2;
+    LMMEW_CUDA(cudaGetLastError());
+    se->tile_ev = tile_ev;
+    return LMMEW_OK;
+}
+
+namespace {
+// One thread per (set, block): set s holds the ranks of subset s (ascending
+// rank order: subset s has ceil((A - s) / n_subsets) of them), i.e. groups
+// [r0 C, r1 C) and tiles [T0, T1) = [tile_start[r0 C], tile_start[r1 C]).
+__global__ void k_plan(const int* group_start, const int* tile_start, const Tile* tiles, int A,
+                       int C, int n_subsets, int blocks_per_set, int tpc, ChunkRange* ranges) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_subsets * blocks_per_set) return;
+    const int s = i / blocks_per_set, k = i % blocks_per_set;
+    int r0 = 0;
+    for (int u = 0; u < s; ++u) r0 += (A - u + n_subsets - 1) / n_subsets;
+    const int r1 = r0 + (A - s + n_subsets - 1) / n_subsets;
+    const int T0 = tile_start[r0 * C], T1 = tile_start[r1 * C];
+    const int t0 = min(T0 + k * tpc, T1), t1 = min(t0 + tpc, T1);
+    ChunkRange R;
+    R.x = t0;
+    R.y = t1;
+    if (t0 < t1) {
+        R.z = tiles[t0].begin;
+        R.w = tiles[t1 - 1].begin + tiles[t1 - 1].count;
+    } else {
+        R.z = R.w = group_start[r1 * C];
+    }
+    ranges[i] = R;
+}
+}  // namespace
+
+int launch_plan(lm_handle* h, const SortedEvents& se, int n_subsets, int blocks_per_set,
+                int tiles_per_block, ChunkRange* ranges, cudaStream_t st) {
+    const int total = n_subsets * blocks_per_set;
+    k_plan<<<(total + 127) / 128, 128, 0, st>>>(se.group_start, se.tile_start, se.tiles, h->mc.A,
+                                                se.n_classes, n_subsets, blocks_per_set,
+                                                tiles_per_block, ranges);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+// Group arrays of one subset built on the device into a caller's region.
 namespace {
 struct ClassLines {
     int v[2 * LMMEW_MAX_LINES + 1];
@@ -450,54 +601,17 @@ __global__ void k_identity_groups(int* rank_of_angle, int* angle_of_group, int* 
 }
 }  // namespace
 
-size_t sort_fixed_bytes(int64_t n, int G) { return sort_scratch_bytes(n, G); }
-
-int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
-                      cudaStream_t st) {
-    const ModelConst& m = h->mc;
-    const int64_t n = ev->n;
-    const int A = m.A, C = h->n_classes, G = sort_groups(h, A);
-    uint32_t* keys0 = bump<uint32_t>(arena, n);
-    uint32_t* keys1 = bump<uint32_t>(arena, n);
-    uint32_t* vals0 = bump<uint32_t>(arena, n);
-    uint32_t* vals1 = bump<uint32_t>(arena, n);
-    const int64_t nblk = (n + kSortChunk - 1) / kSortChunk;
-    uint32_t* hist = bump<uint32_t>(arena, 256 * (nblk > 0 ? nblk : 1));
-    out->perm = bump<uint32_t>(arena, n);
-    out->bin = bump<uint16_t>(arena, n);
-    out->energy = bump<float>(arena, n);
-    int* group_start = bump<int>(arena, G + 1);
-    int* tile_start = bump<int>(arena, G + 1);
-    int* d_angle_of_group = bump<int>(arena, G);
-    int* d_lines_of_group = bump<int>(arena, G);
-    int* d_rank_of_angle = bump<int>(arena, G);
-    out->tiles = bump<Tile>(arena, n / kETMin + G + 1);
-    out->tile_ev = h->tile_ev;
-
+GroupArrays group_arrays_into(lm_handle* h, char*& arena, cudaStream_t st) {
+    const int A = h->mc.A, C = h->n_classes, G = A * C;
+    int* rank_of_angle = bump<int>(arena, A);
+    int* angle_of_group = bump<int>(arena, G);
+    int* lines_of_group = bump<int>(arena, G);
     ClassLines cl;
     for (int c = 0; c < 2 * LMMEW_MAX_LINES + 1; ++c) cl.v[c] = h->class_lines[c];
-    k_identity_groups<<<(G + 255) / 256, 256, 0, st>>>(d_rank_of_angle, d_angle_of_group,
-                                                       d_lines_of_group, A, C, cl);
+    k_identity_groups<<<(G + 255) / 256, 256, 0, st>>>(rank_of_angle, angle_of_group,
+                                                       lines_of_group, A, C, cl);
     ++h->launches;
-    LMMEW_CUDA(cudaGetLastError());
-    int rc = sort_and_tile(h, ev, G, d_rank_of_angle, d_angle_of_group, d_lines_of_group, keys0,
-                           keys1, vals0, vals1, hist, out->perm, out->bin, out->energy,
-                           group_start, tile_start, out->tile_ev, out->tiles, st);
-    if (rc != LMMEW_OK) return rc;
-    int host3[3] = {0, 0, 0};   // tiles, valid events, status
-    LMMEW_CUDA(cudaMemcpyAsync(&host3[0], tile_start + G, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaMemcpyAsync(&host3[1], group_start + G, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaMemcpyAsync(&host3[2], h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LMMEW_CUDA(cudaStreamSynchronize(st));
-    if (host3[2] != 0) {
-        LMMEW_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
-        LMMEW_CUDA(cudaStreamSynchronize(st));
-    }
-    rc = status_error(host3[2]);
-    if (rc != LMMEW_OK) return rc;
-    out->n_tiles = host3[0];
-    out->n_valid = host3[1];
-    return LMMEW_OK;
+    return GroupArrays{rank_of_angle, angle_of_group, lines_of_group};
 }
 
 // ---------------------------------------------------------------------------

@@ -86,6 +86,11 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// Work of one row block (a chunk of whole tiles), written on the device by
+// the planning kernel so that the host needs no event counts: tiles
+// [x, y) and sorted events [z, w) (x = y: nothing to do).
+typedef int4 ChunkRange;
+
 }  // namespace lmmew
 
 struct lm_handle {
@@ -107,6 +112,11 @@ struct lm_handle {
     int n_classes = 1;
     int class_lines[2 * LMMEW_MAX_LINES + 1] = {};
     int prune_lines = 1;           // 0: every tile evaluates every line (lm_set_energy_pruning)
+    // device copies of the sort's group arrays, one set per subset partition
+    // (rank of each angle [A], angle and line mask of each group [G]) for the
+    // energy classes grp_classes; emptied when the classes change
+    int grp_classes = 0;
+    std::map<int, int*> grp_cache;
     size_t tab_bytes = 0;
     // cached subset sensitivities for the last partition asked for
     int sens_parts = 0;
@@ -215,17 +225,46 @@ size_t sort_scratch_bytes(int64_t n, int G);
 int sort_events(lm_handle* h, const lm_events* ev, int n_subsets, SortedEvents* out,
                 char*& arena, cudaStream_t st);
 
-// events.cu: the same sort on a caller-provided region, no host containers
-struct SortedFixed {
-    uint16_t* bin = nullptr;
-    float* energy = nullptr;
-    uint32_t* perm = nullptr;
-    Tile* tiles = nullptr;
-    int n_tiles = 0;
-    int64_t n_valid = 0;
-    int tile_ev = kET;
+// events.cu: the sort without any host read-back: every size the later
+// kernels need stays on the device (group_start[G] = valid events,
+// tile_start[G] = tiles).  The group arrays come from the handle's cache
+// (group_arrays) or, for callers that may not allocate, from ga.
+struct GroupArrays {
+    const int* rank_of_angle;    // [A]
+    const int* angle_of_group;   // [G]
+    const int* lines_of_group;   // [G]
 };
-size_t sort_fixed_bytes(int64_t n, int G);
+int group_arrays(lm_handle* h, int n_subsets, GroupArrays* out);   // cached per partition
+int sort_events_async(lm_handle* h, const lm_events* ev, const GroupArrays& ga, int G,
+                      SortedEvents* out, char*& arena, cudaStream_t st);
+// Group arrays of one subset (angles in natural order) built on the device
+// into a caller-provided region (no allocation, no copy from the host).
+GroupArrays group_arrays_into(lm_handle* h, char*& arena, cudaStream_t st);
+// Tiles re-cut on the device only (no read-back).
+int recut_tiles_async(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st);
+// Read back the group and tile starts of an async sort (synchronises).
+int read_back_counts(lm_handle* h, SortedEvents* se, cudaStream_t st);
+// Synchronises the stream, then returns (and clears) the error the device
+// status word holds: LMMEW_ERR_OUT_OF_RANGE, LMMEW_ERR_TIMEOUT or LMMEW_OK.
+int take_status(lm_handle* h, cudaStream_t st);
+// api.cu: the forward projection without host read-back, shared by
+// lm_forward and lm_forward_noalloc.  One set of all groups, row blocks of
+// tpc tiles (cap events), `blocks` of them: enough for any n events.
+struct ForwardPlan {
+    int G;
+    int64_t n, cap;
+    int tpc, blocks;
+};
+ForwardPlan forward_plan(const lm_handle* h, int64_t n, int64_t cap_max);
+size_t forward_region_bytes(const lm_handle* h, const ForwardPlan& p);
+int forward_async(lm_handle* h, const lm_events* ev, const float* image, float* out_y,
+                  const GroupArrays& ga, const ForwardPlan& p, char* arena, cudaStream_t st);
+// Row blocks of n_sets consecutive rank ranges (the subsets of a partition
+// into n_subsets, or all ranks for n_subsets = 1): set s, block k covers
+// tiles [T0 + k tpc, T0 + (k + 1) tpc) of the set's tiles [T0, T1).
+int launch_plan(lm_handle* h, const SortedEvents& se, int n_subsets, int blocks_per_set,
+                int tiles_per_block, ChunkRange* ranges, cudaStream_t st);
+
 size_t sort_batch_scratch_bytes(int64_t n, int64_t G, int R);
 int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
                       SortedEvents* out, char*& arena, cudaStream_t st);
@@ -233,8 +272,6 @@ int bp_order_batch(lm_handle* h, SortedEvents* se, int R, const int64_t* blk_sta
                    int* grp_start, std::vector<int>& h_grp_start, cudaStream_t st);
 // Re-cut the sorted groups into tiles of tile_ev events (h_tile_start updated).
 int recut_tiles(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st);
-int sort_events_fixed(lm_handle* h, const lm_events* ev, char*& arena, SortedFixed* out,
-                      cudaStream_t st);
 
 // row.cu: fused system-matrix row kernel
 struct RowLaunch {
@@ -253,6 +290,7 @@ struct RowLaunch {
     int tile_ev = kET;      // events per tile the tiles were cut with (32, 64 or 128)
     const uint16_t* ev_real = nullptr;   // batched: realisation of each sorted event
     int skip_scatter = 0;   // unscattered terms only (the surrogate adds the rest)
+    const ChunkRange* range = nullptr;   // if set: tiles and row_base read on the device
 };
 int launch_row(lm_handle* h, const RowLaunch& L, cudaStream_t st);
 int set_precision(lm_handle* h, int prec);
@@ -279,6 +317,23 @@ int launch_voxel_reduce(lm_handle* h, const float* bpart, int64_t n_parts, doubl
                         cudaStream_t st);
 int launch_update(lm_handle* h, float* lam_v, const double* num, const double* sens,
                   const double* llpart, int64_t n_ll, double* loglik_out, cudaStream_t st);
+// The same steps with the sizes on the device: row block k of a set holds
+// ranges[k].w - ranges[k].z events, its ypart / rows indexed from
+// ranges[k].z, its back-projection partials at slots [k * ppc, ...).
+int launch_forward_out_range(lm_handle* h, const float* ypart, int64_t ypart_stride,
+                             int64_t capacity, const ChunkRange* range, const uint32_t* perm,
+                             float* out_y, cudaStream_t st);
+int launch_invalid_out(lm_handle* h, const int* n_valid, int64_t n, const uint32_t* perm,
+                       float* out_y, cudaStream_t st);
+int launch_bp_partial_range(lm_handle* h, const float* rows, int row_stride, const float* ypart,
+                            int64_t ypart_stride, int64_t capacity, const ChunkRange* range,
+                            const uint32_t* perm, const float* weight, float* bpart,
+                            int64_t slot0, double* llpart, cudaStream_t st);
+int launch_voxel_reduce_ranges(lm_handle* h, const float* bpart, const ChunkRange* ranges,
+                               int n_blocks, int64_t ppc, double* num, cudaStream_t st);
+int launch_update_ranges(lm_handle* h, float* lam_v, const double* num, const double* sens,
+                         const double* llpart, const ChunkRange* ranges, int n_blocks,
+                         int64_t ppc, double* loglik_out, cudaStream_t st);
 constexpr int kBpChunkEvents = 128;   // events per back-projection partial sum
 struct BpChunk {
     int64_t begin;   // first entry of the back-projection order

@@ -1,8 +1,10 @@
 // lm_forward_noalloc: the forward projection of lm_forward for callers that
-// cannot allocate device memory while they run.  Its scratch (sorted events,
-// tiles, the image on the voxel list and the per-tile partial sums) lives in
-// one statically sized device array of this file instead of memory the
-// library would otherwise cudaMalloc.
+// cannot allocate device memory while they run.  Its scratch (the sort's
+// group arrays, sorted events, tiles, the image on the voxel list, the
+// per-tile partial sums and the row-block ranges) lives in one statically
+// sized device array of this file instead of memory the library would
+// otherwise cudaMalloc; it runs the same kernels, in the same order, as
+// lm_forward.
 #include <mutex>
 
 #include "lmmew_internal.cuh"
@@ -19,7 +21,10 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the static array on the current device, looked up once
-// per device (host code must not use the symbol itself as an address).
+// per device (host code must not use the symbol itself as an address).  The
+// address stays cached for the life of the process: after a device reset
+// (cudaDeviceReset) it would be stale, so the library must not be used
+// across one.
 int scratch_address(void** out) {
     int dev = 0;
     LMMEW_CUDA(cudaGetDevice(&dev));
@@ -45,16 +50,27 @@ extern "C" int lm_forward_noalloc(lm_handle* h, const lm_events* ev, const float
                                   float* out_y, lm_stream stream) {
     if (!h || !ev) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
     if (ev->n < 0) return set_error(LMMEW_ERR_INVALID_ARG, "negative event count");
+    // the surrogate models keep a row block of the whole event list: refused
+    // before anything is queued
+    if (h->scatter_model == LMMEW_SCATTER_SURROGATE ||
+        h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "lm_forward_noalloc runs the exact and the scatter-free models; use "
+                         "lm_forward with a surrogate scatter model");
     if (ev->n == 0) return LMMEW_OK;
     if (!ev->angle || !ev->bin || !ev->energy_keV || !image || !out_y)
         return set_error(LMMEW_ERR_INVALID_ARG, "NULL event, image or output pointer");
     const ModelConst& m = h->mc;
     const int64_t n = ev->n;
-    // every word of the region below is written before it is read within a
-    // call, so nothing has to start at zero
-    const size_t need = sort_fixed_bytes(n, sort_groups(h, m.A)) + bump_bytes(sizeof(float) * m.nq) +
-                        bump_bytes(sizeof(float) * (size_t)m.nqt * n);
-    if (n >= (int64_t(1) << 31) || need > kNoAllocBytes)
+    if (n >= (int64_t(1) << 31))
+        return set_error(LMMEW_ERR_INVALID_ARG, "at most 2^31 - 1 events per call");
+    // one row block of every event; every word of the region is written
+    // before it is read within a call, so nothing has to start at zero
+    const ForwardPlan fp = forward_plan(h, n, int64_t(1) << 40);
+    const int G = sort_groups(h, m.A);
+    const size_t need = bump_bytes(sizeof(int) * m.A) + 2 * bump_bytes(sizeof(int) * G) +
+                        forward_region_bytes(h, fp);
+    if (need > kNoAllocBytes)
         return set_error(LMMEW_ERR_INVALID_ARG,
                          "lm_forward_noalloc: " + std::to_string(n) + " events need " +
                              std::to_string(need) + " bytes of scratch, more than its fixed " +
@@ -64,17 +80,7 @@ extern "C" int lm_forward_noalloc(lm_handle* h, const lm_events* ev, const float
     if (rc != LMMEW_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     char* arena = (char*)base;
-    SortedFixed se;
-    rc = sort_events_fixed(h, ev, arena, &se, st);
-    if (rc != LMMEW_OK) return rc;
-    float* lam_v = bump<float>(arena, m.nq);
-    float* ypart = bump<float>(arena, (size_t)m.nqt * n);
-    rc = launch_gather_image(h, image, lam_v, st);
-    if (rc != LMMEW_OK) return rc;
-    RowLaunch L{se.tiles, 0, se.n_tiles, se.bin, se.energy, lam_v, nullptr, 0, 0, ypart, n,
-                se.n_valid};
-    L.tile_ev = se.tile_ev;
-    rc = launch_row(h, L, st);
-    if (rc != LMMEW_OK) return rc;
-    return launch_forward_out(h, ypart, n, 0, se.n_valid, se.perm, out_y, st);
+    const GroupArrays ga = group_arrays_into(h, arena, st);
+    LMMEW_CUDA(cudaGetLastError());
+    return forward_async(h, ev, image, out_y, ga, fp, arena, st);
 }

@@ -38,6 +38,7 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     P.tiles = L.tiles;
     P.tile_begin = L.tile_begin;
     P.tile_end = L.tile_end;
+    P.range = L.range;
     P.ev_bin = L.ev_bin;
     P.ev_e = L.ev_e;
     P.lam = L.lam_v;

@@ -56,6 +56,7 @@ struct RowParams {
     const float* prim;    // [A][W][nq]
     const Tile* tiles;
     int tile_begin, tile_end;
+    const ChunkRange* range;   // if set: tiles [x, y) and row_base z read from the device
     const uint16_t* ev_bin;
     const float* ev_e;
     const float* lam;     // [nq] (per realisation, lam_stride apart) or null
@@ -330,7 +331,15 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     }
     __syncthreads();
 
-    const int n_tiles = P.tile_end - P.tile_begin;
+    int tile_begin = P.tile_begin, tile_end = P.tile_end;
+    int64_t row_base = P.row_base;
+    if (P.range) {
+        const ChunkRange R = *P.range;
+        tile_begin = R.x;
+        tile_end = R.y;
+        row_base = R.z;
+    }
+    const int n_tiles = tile_end - tile_begin;
     const int n_units = n_tiles * P.nqt;
     constexpr int kComp = PREC == 0 ? 3 : 2;                         // table components
     constexpr int kTabBlock = kComp * W * kQT * kPC;   // 4-byte words per (a, qt, pc)
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
     // each CTA starts on unit blockIdx.x and then takes the next unhanded
     // unit from the counter, so CTAs that drew lighter units take more
     for (int unit = blockIdx.x; unit < n_units;) {
-        const Tile T = P.tiles[P.tile_begin + (P.unit_order ? unit % n_tiles : unit / P.nqt)];
+        const Tile T = P.tiles[tile_begin + (P.unit_order ? unit % n_tiles : unit / P.nqt)];
         const int qt = P.unit_order ? unit / n_tiles : unit % P.nqt;
         const float* lam = P.lam ? P.lam + (size_t)T.r * P.lam_stride : nullptr;
         const int b_lo = T.b_lo_hi >> 16, b_hi = T.b_lo_hi & 0xffff;
@@ -520,7 +529,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 const int e = i >> 5, ql = i & 31;
                 const int q = qt * kQT + ql;
                 if (e < T.count && q < P.nq)
-                    P.rows[(size_t)(T.begin + e - P.row_base) * P.row_stride + q] = tt[e * 33 + ql];
+                    P.rows[(size_t)(T.begin + e - row_base) * P.row_stride + q] = tt[e * 33 + ql];
             }
         }
         if (lam && tid < T.count) {
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
             float s = 0.f;
             const int qmax = min(kQT, P.nq - qt * kQT);
             for (int ql = 0; ql < qmax; ++ql) s = fmaf(le[qt * kQT + ql], tt[e * 33 + ql], s);
-            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - P.row_base)] = s;
+            P.ypart[(size_t)qt * P.ypart_stride + (T.begin + e - row_base)] = s;
         }
         if (tid == 0) s_unit = (int)gridDim.x + atomicAdd(P.work, 1);
         __syncthreads();

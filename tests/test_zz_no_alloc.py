@@ -3,9 +3,11 @@ allocate device memory while they run (their device memory belongs to
 another allocator, or their steady-state loop forbids the allocation and
 synchronisation cudaMalloc brings).  It keeps its scratch in a fixed 16 MiB
 static device array of the library.  These tests call it through the C ABI
-and compare it with lm_forward, the entry point that allocates, on two calls
-in a row (the second call reuses the array the first one left behind), and
-check that an oversized request is refused before any work is queued.
+and compare it bit for bit with lm_forward, the entry point that allocates,
+on two calls in a row (the second call reuses the array the first one left
+behind), with the exact and the scatter-free models; check that an
+oversized request and the surrogate models are refused before any work is
+queued; and check the Python wrapper's argument checks.
 
 The file sorts last so that a failure here stops a -x run only after every
 other test has run.
@@ -23,9 +25,6 @@ pytestmark = pytest.mark.gpu
 import paper_2305_17111_gb300 as lm  # noqa: E402
 from paper_2305_17111_gb300 import _native  # noqa: E402
 from synthetic import preset, simulate  # noqa: E402
-
-FWD_RTOL = 1e-5   # the forward-projection tolerance of the parity tests
-
 
 @pytest.fixture(scope="module")
 def case():
@@ -49,19 +48,53 @@ def call_noalloc(model, events, image, out):
                                              ctypes.c_void_p(out.data_ptr()), stream)
 
 
-def test_noalloc_matches_lm_forward_on_two_calls(case):
+def check(model):
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _native.load().lm_check(model._h, stream)
+
+
+@pytest.mark.parametrize("scatter", ["exact", "none"])
+def test_noalloc_matches_lm_forward_on_two_calls(case, scatter):
     sc, model, image = case
+    model.set_scatter_model(scatter)
     first = lm.DeviceEvents.from_list(simulate(sc, n_events=3000, seed=21))
     second = lm.DeviceEvents.from_list(simulate(sc, n_events=1700, seed=22))
     for events in (first, second):
         ref = model.forward(events, image)
         out = torch.full((len(events),), float("nan"), dtype=torch.float32, device="cuda")
         assert call_noalloc(model, events, image, out) == 0, _native.load().lm_last_error()
-        torch.cuda.synchronize()
-        got = out.cpu().numpy().astype(np.float64)
-        want = ref.cpu().numpy().astype(np.float64)
+        assert check(model) == 0
+        got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
-        np.testing.assert_allclose(got, want, rtol=FWD_RTOL, atol=0)
+        # same kernels in the same order: bit-identical
+        np.testing.assert_array_equal(got, ref.cpu().numpy())
+    model.set_scatter_model("exact")
+
+
+def test_noalloc_refuses_the_surrogate_models_before_queueing(case):
+    sc, model, image = case
+    sur = lm.Surrogate(3)
+    events = lm.DeviceEvents.from_list(simulate(sc, n_events=200, seed=24))
+    out = torch.zeros(len(events), dtype=torch.float32, device="cuda")
+    for kind in ("surrogate", "surrogate_coarse"):
+        model.set_scatter_model(kind, sur)
+        assert call_noalloc(model, events, image, out) == -6   # LMMEW_ERR_NOT_IMPLEMENTED
+        torch.cuda.synchronize()
+        assert float(out.abs().sum()) == 0.0
+    model.set_scatter_model("exact")
+    sur.close()
+
+
+def test_noalloc_wrapper_checks_its_arguments(case):
+    sc, model, image = case
+    events = lm.DeviceEvents.from_list(simulate(sc, n_events=300, seed=25))
+    with pytest.raises(ValueError):
+        model.forward_noalloc(events, image, torch.zeros(len(events) + 1, device="cuda"))
+    with pytest.raises(TypeError):
+        model.forward_noalloc(events, image, torch.zeros(len(events)))   # host tensor
+    out = torch.empty(len(events), dtype=torch.float32, device="cuda")
+    model.forward_noalloc(events, image, out)
+    assert torch.equal(out, model.forward(events, image))
 
 
 def test_noalloc_refuses_requests_beyond_its_array(case):
@@ -79,5 +112,5 @@ def test_noalloc_refuses_requests_beyond_its_array(case):
     small = lm.DeviceEvents.from_list(simulate(sc, n_events=500, seed=23))
     out2 = torch.empty(len(small), dtype=torch.float32, device="cuda")
     assert call_noalloc(model, small, image, out2) == 0
-    np.testing.assert_allclose(out2.cpu().numpy(), model.forward(small, image).cpu().numpy(),
-                               rtol=FWD_RTOL)
+    assert check(model) == 0
+    np.testing.assert_array_equal(out2.cpu().numpy(), model.forward(small, image).cpu().numpy())

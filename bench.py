@@ -54,7 +54,7 @@ def parse_args():
                     help="skip the forms section (precision, batching with the combined form, comparison, surrogate)")
     ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
                     help="comma-separated forms to measure")
-    ap.add_argument("--case", default=None, choices=["surrogate_rows", "surrogate_train", "surrogate_coarse_osem", "setup"],
+    ap.add_argument("--case", default=None, choices=["row", "row_rows", "surrogate_rows", "surrogate_train", "surrogate_coarse_osem", "setup"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
     return ap.parse_args()
 
@@ -138,11 +138,14 @@ def measured_peaks():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# current k_row revision on this workload, in the tile size the autotuner
-# picks for it (64 events: k_row<3, 0, 2>): the mean over the 8 launches of
-# one OSEM iteration in a one-pass ncu capture of the full workload.  Emptied
-# whenever k_row changes until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 308_060_544}
+# current k_row revision on this workload.  Measured on the small case
+# `--case row_rows` (60 000 events of subset 0's 8 angles, rows stored as
+# lm_osem does, 64-event tiles): 218 139 136 B read (the 8 angles' path
+# tables) + 175 910 144 B written (the row block), in a one-launch capture;
+# scaled to one OSEM launch of this workload by angles for the reads (7.5 of
+# 8) and by events for the writes (37 500 of 60 000).  Emptied whenever
+# k_row changes until the counters are taken again.
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 204_505_440 + 109_943_840}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.
@@ -957,6 +960,49 @@ def run_surrogate_rows_case(n_events=20_000, repeats=3):
     return 0
 
 
+def run_row_case(n_events=60_000, tile_events=64, repeats=3, store_rows=False):
+    """Small case for profiling the exact row kernel in the launch shape the
+    benchmark's workload uses: the 64 x 64 object (its 1.6 GB of path
+    tables), n_events MC events of the subset-0 angles (8 angles, about one
+    lm_osem sub-iteration's work), tiles of tile_events; lm_forward (forward
+    sums only) or, with store_rows, lm_backproject (the row block written, as
+    lm_osem's launches do).  One row-kernel launch per call.  Prints one
+    JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate
+    sc = preset("lmmew_64")
+    ph = sc.make_phantom()
+    ev = simulate(sc, n_events=8 * n_events, seed=3)
+    ev = ev.subset(np.nonzero(ev.angle % sc.n_subsets == 0)[0][:n_events])
+    model = lm.Model.from_scenario(sc, ph.rho)
+    model.set_tile_events(tile_events)
+    dev = lm.DeviceEvents.from_list(ev)
+    lam = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
+    wt = torch.ones(len(ev), dtype=torch.float32, device="cuda")
+
+    def call():
+        if store_rows:
+            model.backproject(dev, wt)
+        else:
+            model.forward(dev, lam)
+    model.profile_enable(True)
+    call()
+    model.profile_read()
+    for _ in range(repeats):
+        call()
+    prof = model.profile_read()
+    model.profile_enable(False)
+    print(json.dumps({"case": "row_rows" if store_rows else "row", "events": len(ev),
+                      "tile_events": tile_events,
+                      "row_ms": prof["ms"] / repeats, "terms": prof["terms"] / repeats,
+                      "Tterms_per_s": prof["terms"] / (prof["ms"] / 1e3) / 1e12}), flush=True)
+    model.close()
+    return 0
+
+
 def run_surrogate_coarse_osem_case(n_events=200_000, repeats=2):
     """Small case for the launch list of the coarse-grid surrogate form: the
     128 x 128 object, 200 000 MC events, OSEM iterations of 8 subsets with
@@ -1043,6 +1089,8 @@ def run_surrogate_train_case(steps=10, batch=16_384, n=200_000):
 def main():
     args = parse_args()
     rank, local_rank, world = dist_env()
+    if args.case in ("row", "row_rows"):
+        return run_row_case(n_events=args.events or 60_000, store_rows=args.case == "row_rows")
     if args.case == "surrogate_rows":
         return run_surrogate_rows_case()
     if args.case == "surrogate_train":

@@ -576,6 +576,25 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     m.np = (int)p_cell.size();
     m.npc = (m.np + kPC - 1) / kPC;
 
+    // The single-scatter path tables hold 3 floats per (angle, line, voxel,
+    // scatter point), padded to 32-voxel x 32-point blocks: A W Q P x 12
+    // bytes, next to the voxel-to-point line integrals and distances (Q P x
+    // 16 bytes, set-up only).  A model that does not fit the free memory is
+    // refused here, before anything large is allocated.
+    if (m.np) {
+        const size_t tab = sizeof(float) * (size_t)m.A * m.nqt * m.npc * 3 * m.W * kQT * kPC;
+        const size_t need = tab + 2 * sizeof(double) * (size_t)m.nq * m.np;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b)
+            return set_error(LMMEW_ERR_OOM,
+                             "the path tables need " + std::to_string(tab >> 20) +
+                                 " MiB (12 bytes x angles x lines x voxels x scatter points) and "
+                                 "their set-up " + std::to_string((need - tab) >> 20) +
+                                 " MiB more, beyond the " + std::to_string(free_b >> 20) +
+                                 " MiB free on the device; use a coarser scatter grid or fewer "
+                                 "angles");
+    }
+
     // collimator blur must stay positive for every point and angle
     {
         double rmax = 0.0;
@@ -729,9 +748,11 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     // single-scatter paths
     if (m.np) {
         h->tab_bytes = sizeof(float) * (size_t)m.A * m.nqt * m.npc * 3 * m.W * kQT * kPC;
-        if (cudaMalloc(&h->d_tab, h->tab_bytes) != cudaSuccess)
+        if (cudaMalloc(&h->d_tab, h->tab_bytes) != cudaSuccess) {
+            cudaGetLastError();
             return set_error(LMMEW_ERR_OOM, "cannot allocate scatter tables (" +
                                                 std::to_string(h->tab_bytes >> 20) + " MiB)");
+        }
         LMMEW_CUDA(cudaMemset(h->d_tab, 0, h->tab_bytes));
         DevBuf d_on_det;
         LMMEW_CUDA(cudaMalloc(&d_on_det.p, sizeof(double) * (size_t)m.A * m.np));

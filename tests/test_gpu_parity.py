@@ -244,3 +244,16 @@ def test_energy_model_variants_parity():
     rel = np.abs(got - ref) / np.abs(ref)
     assert float(rel.max()) < FWD_RTOL, f"max rel {rel.max():.3e}"
     gpu.close()
+
+
+def test_model_beyond_device_memory_is_refused_with_its_size():
+    """Path tables of 12 bytes x angles x lines x voxels x scatter points: a
+    256 x 256 model with a 256 x 256 scatter grid and 90 angles needs
+    several TB and is refused before anything large is allocated."""
+    sc = preset("lmmew_64").with_(n=256, pixel_cm=0.15, n_angles=90, n_bins=256, scatter_n=256)
+    ph = sc.make_phantom()
+    with pytest.raises(lm.LmmewError, match="OOM.*path tables need"):
+        lm.Model.from_scenario(sc, ph.rho)
+    # the process keeps a usable device afterwards
+    small = preset("tiny_8")
+    lm.Model.from_scenario(small, small.make_phantom().rho).close()

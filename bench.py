@@ -485,14 +485,16 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
     res = {}
-    for kind in ("exact", "surrogate", "surrogate_coarse", "none"):
-        model.set_scatter_model(kind, sur if kind.startswith("surrogate") else None)
+    for kind in ("exact", "surrogate", "surrogate_coarse", "surrogate_coarse_s3", "none"):
+        model.set_coarse_stride(3 if kind.endswith("_s3") else 2)
+        model.set_scatter_model(kind.replace("_s3", ""), sur if kind.startswith("surrogate") else None)
         y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)   # also warms up
         model.osem(dev, lam0.clone(), sc.n_subsets, 0)   # untimed: the row-kernel autotune
         img = lam0.clone()
         _, sec = timed(lambda: model.osem(dev, img, sc.n_subsets, iters))
         res[kind] = {"y": y, "img": img.cpu().numpy().astype(np.float64), "s_per_iter": sec / iters}
     model.set_scatter_model("exact")
+    model.set_coarse_stride(2)
     ex = res["exact"]
     roi_ex = roi_sums(ex["img"], ph.lesion_masks)
     samples_per_iter = surrogate_samples_in_reach(sc, ev.energy, model.nq)
@@ -510,7 +512,7 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
                         "heldout_object_mass_rel_err": mass_err,
                         "heldout_object_mass_ratio": mass_ratio},
            "exact": {"s_per_iter": ex["s_per_iter"], "roi_activity": roi_ex}}
-    for kind in ("surrogate", "surrogate_coarse", "none"):
+    for kind in ("surrogate", "surrogate_coarse", "surrogate_coarse_s3", "none"):
         r = res[kind]
         roi = roi_sums(r["img"], ph.lesion_masks)
         out[kind] = {"s_per_iter": r["s_per_iter"],
@@ -635,20 +637,24 @@ def run_c3_forms(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, seed=3,
     # the combined form on the same realisations
     sur, t_sample, t_train, _, _ = train_surrogate_on_random_objects(
         sc, n_objects, n_samples, 20_000, sur_seed)
-    model.set_scatter_model("surrogate_coarse", sur)
-    t_comb, imgs_c = batched()
-    model.set_scatter_model("exact")
-    dev = np.asarray([[abs(a - b) / b for a, b in zip(roi_sums(imgs_c[r], ph.lesion_masks),
-                                                       exact_roi[r])] for r in range(n_real)])
-    out["combined"] = {"form": "BF16 tensor-core surrogate on the coarse grid + batched "
-                               "realisations in one CUDA graph",
+    out["combined"] = {"form": "BF16 tensor-core surrogate on the coarse grid (node stride 2 "
+                               "or 3 pixels) + batched realisations in one CUDA graph",
                        "surrogate_training": {"objects": n_objects, "samples": n_samples,
-                                              "sample_s": t_sample, "train_s": t_train},
-                       "batch_s": t_comb,
-                       "speedup_vs_exact_fp32_one_at_a_time": float(seq.sum()) / t_comb,
-                       "speedup_vs_exact_fp32_batched": t_batch / t_comb,
-                       "roi_rel_dev_vs_exact": {"mean": float(dev.mean()), "max": float(dev.max()),
-                                                "per_lesion_mean": dev.mean(axis=0).tolist()}}
+                                              "sample_s": t_sample, "train_s": t_train}}
+    for stride in (2, 3):
+        model.set_coarse_stride(stride)
+        model.set_scatter_model("surrogate_coarse", sur)
+        t_comb, imgs_c = batched()
+        model.set_scatter_model("exact")
+        dev = np.asarray([[abs(a - b) / b for a, b in zip(roi_sums(imgs_c[r], ph.lesion_masks),
+                                                           exact_roi[r])] for r in range(n_real)])
+        out["combined"][f"stride_{stride}"] = {
+            "batch_s": t_comb,
+            "speedup_vs_exact_fp32_one_at_a_time": float(seq.sum()) / t_comb,
+            "speedup_vs_exact_fp32_batched": t_batch / t_comb,
+            "roi_rel_dev_vs_exact": {"mean": float(dev.mean()), "max": float(dev.max()),
+                                     "per_lesion_mean": dev.mean(axis=0).tolist()}}
+    model.set_coarse_stride(2)
     sur.close()
     model.close()
     return out
@@ -882,16 +888,19 @@ def run_gpu(args, rank, local_rank, world):
         c3 = line["forms"].get("batching", {}).get("lmmew_64_256", {}).get("combined")
         if c3:
             chosen["realisations_256"] = {
-                "workload": line["forms"]["batching"]["lmmew_64_256"]["workload"],
-                "speedup_vs_plain_fp32_one_at_a_time": c3["speedup_vs_exact_fp32_one_at_a_time"],
-                "speedup_vs_plain_fp32_batched": c3["speedup_vs_exact_fp32_batched"],
-                "roi_rel_dev_vs_plain_fp32": c3["roi_rel_dev_vs_exact"]}
+                "workload": line["forms"]["batching"]["lmmew_64_256"]["workload"]}
+            for k in ("stride_2", "stride_3"):
+                chosen["realisations_256"][k] = {
+                    "speedup_vs_plain_fp32_one_at_a_time": c3[k]["speedup_vs_exact_fp32_one_at_a_time"],
+                    "speedup_vs_plain_fp32_batched": c3[k]["speedup_vs_exact_fp32_batched"],
+                    "roi_rel_dev_vs_plain_fp32": c3[k]["roi_rel_dev_vs_exact"]}
         c4 = line["forms"].get("surrogate")
         if c4:
-            chosen["single_128_2m"] = {
-                "workload": c4["workload"],
-                "speedup_vs_plain_fp32": c4["surrogate_coarse"]["speedup_vs_exact"],
-                "roi_rel_dev_vs_plain_fp32": c4["surrogate_coarse"]["roi_rel_dev_vs_exact"]}
+            chosen["single_128_2m"] = {"workload": c4["workload"]}
+            for k, kind in (("stride_2", "surrogate_coarse"), ("stride_3", "surrogate_coarse_s3")):
+                chosen["single_128_2m"][k] = {
+                    "speedup_vs_plain_fp32": c4[kind]["speedup_vs_exact"],
+                    "roi_rel_dev_vs_plain_fp32": c4[kind]["roi_rel_dev_vs_exact"]}
         if len(chosen) > 1:
             line["chosen_form"] = chosen
     if world == 1 and not args.no_cpu_baseline:

@@ -294,6 +294,10 @@ class Model:
         _native.check(_native.load().lm_set_scatter_model(self._h, self.SCATTER_MODELS[model], ptr))
         self._surrogate_ref = surrogate
 
+    def set_coarse_stride(self, stride: int = 2):
+        """Node spacing (2, 3 or 4 pixels) of the 'surrogate_coarse' model."""
+        _native.check(_native.load().lm_set_coarse_stride(self._h, int(stride)))
+
     def surrogate_samples(self, events: DeviceEvents, n, seed=0, stream=None):
         """n training samples (x [n, 32], target [n]) for the surrogate: random
         (event, voxel, line) with the exact ln(S_w + 1e-8) as target."""

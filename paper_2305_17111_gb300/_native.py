@@ -84,6 +84,7 @@ SYMBOLS = {
     "lm_set_tile_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_set_energy_pruning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "lm_set_coarse_stride": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lm_last_error": (ctypes.c_char_p, []),
     "lm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

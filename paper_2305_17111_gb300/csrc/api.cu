@@ -263,9 +263,12 @@ ForwardPlan forward_plan(const lm_handle* h, int64_t n, int64_t cap_max) {
     p.G = sort_groups(h, h->mc.A);
     const int te = h->tile_ev;
     p.n = n;
-    p.cap = std::max<int64_t>(te, std::min<int64_t>(n + (int64_t)p.G * te, cap_max));
-    p.tpc = (int)(p.cap / te);
-    p.blocks = (int)((((n + te - 1) / te) + p.G + p.tpc - 1) / p.tpc);
+    // at most ceil(n / te) + G tiles: one row block of that many whole tiles
+    // when it fits cap_max, else blocks of as many tiles as fit
+    const int64_t tiles_max = (n + te - 1) / te + p.G;
+    p.tpc = (int)std::max<int64_t>(1, std::min<int64_t>(tiles_max, cap_max / te));
+    p.cap = (int64_t)p.tpc * te;
+    p.blocks = (int)((tiles_max + p.tpc - 1) / p.tpc);
     return p;
 }
 
@@ -800,10 +803,11 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
     // has at most ceil(n / tile_ev) + (its groups) tiles
     const int te = se.tile_ev, C = se.n_classes, rs = row_stride_of(h);
     const int64_t g_sub = (int64_t)first_ranks * C;
-    const int64_t cap = std::max<int64_t>(
-        te, std::min<int64_t>(n + g_sub * te, (int64_t)(kRowBudgetFloats / rs)));
-    const int tpc = (int)(cap / te);
-    const int blocks = (int)((((n + te - 1) / te) + g_sub + tpc - 1) / tpc);
+    const int64_t tiles_max = (n + te - 1) / te + g_sub;
+    const int tpc = (int)std::max<int64_t>(
+        1, std::min<int64_t>(tiles_max, (int64_t)(kRowBudgetFloats / rs) / te));
+    const int64_t cap = (int64_t)tpc * te;
+    const int blocks = (int)((tiles_max + tpc - 1) / tpc);
     const int64_t ppc = bp_parts(cap);
     rc = ensure(h, h->scratch_work,
                 bump_bytes(sizeof(float) * m.nq) + bump_bytes(sizeof(float) * (size_t)rs * cap) +

@@ -154,6 +154,7 @@ struct lm_handle {
     int scatter_model = 0;         // 0 exact, 1 surrogate, 2 none, 3 surrogate on the coarse grid
     // coarse-grid surrogate: network nodes and each voxel's interpolation
     int n_nodes = 0;
+    int coarse_stride = 2;         // node spacing in pixels (lm_set_coarse_stride)
     int* d_node_q = nullptr;       // [n_nodes] support voxel of each node
     int4* d_interp_node = nullptr; // [nq] up to 4 nodes of each voxel (-1: none)
     float4* d_interp_w = nullptr;  // [nq] their weights (sum 1)

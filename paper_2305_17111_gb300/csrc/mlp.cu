@@ -1143,9 +1143,10 @@ int build_coarse_nodes(lm_handle* h) {
     std::vector<float4> wt(nq);
     for (int q = 0; q < nq; ++q) {
         const int ix = q_pix[q] % n, iy = q_pix[q] / n;
-        const int x0 = ix & ~1, y0 = iy & ~1;
-        const double tx = 0.5 * (ix - x0), ty = 0.5 * (iy - y0);
-        const int cx[4] = {x0, x0 + 2, x0, x0 + 2}, cy[4] = {y0, y0, y0 + 2, y0 + 2};
+        const int st = h->coarse_stride;
+        const int x0 = ix - ix % st, y0 = iy - iy % st;
+        const double tx = (double)(ix - x0) / st, ty = (double)(iy - y0) / st;
+        const int cx[4] = {x0, x0 + st, x0, x0 + st}, cy[4] = {y0, y0, y0 + st, y0 + st};
         const double w0[4] = {(1 - tx) * (1 - ty), tx * (1 - ty), (1 - tx) * ty, tx * ty};
         int cq[4];
         double sum = 0.0;

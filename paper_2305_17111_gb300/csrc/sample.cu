@@ -140,6 +140,23 @@ extern "C" int lm_surrogate_sample(lm_handle* h, const lm_events* ev, int64_t n,
     return LMMEW_OK;
 }
 
+extern "C" int lm_set_coarse_stride(lm_handle* h, int stride) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    if (stride < 2 || stride > 4) return set_error(LMMEW_ERR_INVALID_ARG, "stride must be 2, 3 or 4");
+    if (stride == h->coarse_stride) return LMMEW_OK;
+    // the node tables of the old spacing go; the coarse form rebuilds them
+    cudaFree(h->d_node_q);
+    cudaFree(h->d_interp_node);
+    cudaFree(h->d_interp_w);
+    h->d_node_q = nullptr;
+    h->d_interp_node = nullptr;
+    h->d_interp_w = nullptr;
+    h->n_nodes = 0;
+    h->coarse_stride = stride;
+    if (h->scatter_model == LMMEW_SCATTER_SURROGATE_COARSE) return build_coarse_nodes(h);
+    return LMMEW_OK;
+}
+
 extern "C" int lm_set_scatter_model(lm_handle* h, int model, const lm_surrogate* s) {
     if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
     if (model < 0 || model > 3) return set_error(LMMEW_ERR_INVALID_ARG, "unknown scatter model");

@@ -56,19 +56,21 @@ def events_of(angle, bin_, energy) -> synthetic.EventList:
                                np.zeros(k, bool))
 
 
-def coarse_interpolation(pix, n):
+def coarse_interpolation(pix, n, stride=2):
     """[nq][nq] interpolation of the coarse-grid surrogate, restated from its
     definition: voxel (ix, iy) takes the bilinear weights of the corners
-    (ix - ix % 2, iy - iy % 2) .. (+2, +2) that lie in the support,
-    renormalised to sum 1; with no such corner it is its own node."""
+    (ix - ix % s, iy - iy % s) .. (+s, +s) that lie in the support (s the
+    node stride), renormalised to sum 1; with no such corner it is its own
+    node."""
     q_of = {int(p): q for q, p in enumerate(pix)}
     M = np.zeros((len(pix), len(pix)))
+    s = int(stride)
     for q, p in enumerate(pix):
         ix, iy = int(p) % n, int(p) // n
-        x0, y0 = ix - ix % 2, iy - iy % 2
-        tx, ty = (ix - x0) / 2.0, (iy - y0) / 2.0
-        corners = [(x0, y0, (1 - tx) * (1 - ty)), (x0 + 2, y0, tx * (1 - ty)),
-                   (x0, y0 + 2, (1 - tx) * ty), (x0 + 2, y0 + 2, tx * ty)]
+        x0, y0 = ix - ix % s, iy - iy % s
+        tx, ty = (ix - x0) / float(s), (iy - y0) / float(s)
+        corners = [(x0, y0, (1 - tx) * (1 - ty)), (x0 + s, y0, tx * (1 - ty)),
+                   (x0, y0 + s, (1 - tx) * ty), (x0 + s, y0 + s, tx * ty)]
         keep = [(q_of[cy * n + cx], w) for cx, cy, w in corners
                 if w > 0 and cx < n and cy < n and (cy * n + cx) in q_of]
         if not keep:

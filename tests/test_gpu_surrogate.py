@@ -375,22 +375,25 @@ def test_surrogate_fit_on_held_out_samples():
     assert mass_err < 0.35, mass_err
 
 
-@pytest.mark.parametrize("model", ["surrogate", "surrogate_coarse"])
-def test_surrogate_rows_match_primary_plus_oracle_network(model):
+@pytest.mark.parametrize("model,stride", [("surrogate", 2), ("surrogate_coarse", 2),
+                                          ("surrogate_coarse", 3)])
+def test_surrogate_rows_match_primary_plus_oracle_network(model, stride):
     sc, ph, orc, gpu, ev, dev = _fine_model()
     s, _ = _trained_surrogate()
     p = s.get_params()
     orc0 = oracle.Model.from_scenario(sc.with_(scatter_n=0), ph.rho)
     lam = (np.random.default_rng(2).uniform(0.2, 3, ph.rho.size) * (ph.rho.reshape(-1) > 0))
     lam = lam.astype(np.float32)
+    gpu.set_coarse_stride(stride)
     gpu.set_scatter_model(model, s)
     try:
         got = gpu.forward(dev, torch.from_numpy(lam).cuda()).cpu().numpy().astype(np.float64)
     finally:
         gpu.set_scatter_model("exact")
+        gpu.set_coarse_stride(2)
     lam_q = lam.astype(np.float64)[orc.voxel_pixels]
-    interp = (coarse_interpolation(orc.voxel_pixels, sc.n) if model == "surrogate_coarse"
-              else None)
+    interp = (coarse_interpolation(orc.voxel_pixels, sc.n, stride=stride)
+              if model == "surrogate_coarse" else None)
     W = len(sc.line_keV)
     checked = 0
     for j in range(0, len(ev), 97):

@@ -266,33 +266,35 @@ def test_scatter_reach_bounds_the_oracles_single_scatter():
     assert checked >= 8
 
 
-def test_coarse_interpolation_restatement():
+@pytest.mark.parametrize("stride", [2, 3])
+def test_coarse_interpolation_restatement(stride):
     """The coarse-grid surrogate's interpolation as the tests restate it: rows
-    sum to 1, only even-coordinate support voxels (or a voxel itself) are
-    referenced, even-coordinate voxels map to themselves, and a function
-    linear in the pixel coordinates is reproduced exactly wherever all four
-    corners lie in the support (bilinear interpolation is exact for it)."""
+    sum to 1, only node voxels (both pixel coordinates multiples of the
+    stride) or a voxel itself are referenced, nodes map to themselves, and a
+    function linear in the pixel coordinates is reproduced exactly wherever
+    all four corners lie in the support (bilinear interpolation is exact for
+    it)."""
     from oracle_util import coarse_interpolation
     from synthetic import preset
     sc = preset("lmmew_32")
     ph = sc.make_phantom()
     pix = np.nonzero(ph.rho.reshape(-1) > 0)[0]
-    n = sc.n
-    M = coarse_interpolation(pix, n)
+    n, s = sc.n, stride
+    M = coarse_interpolation(pix, n, stride=s)
     np.testing.assert_allclose(M.sum(axis=1), 1.0, rtol=0, atol=1e-12)
     ix, iy = pix % n, pix // n
-    even = (ix % 2 == 0) & (iy % 2 == 0)
+    node = (ix % s == 0) & (iy % s == 0)
     for q in range(len(pix)):
         cols = np.nonzero(M[q])[0]
-        assert np.all(even[cols]) or list(cols) == [q], q
-        if even[q]:
+        assert np.all(node[cols]) or list(cols) == [q], q
+        if node[q]:
             assert M[q, q] == 1.0
     f = 0.7 + 0.3 * ix - 1.1 * iy            # linear in the pixel coordinates
     g = M @ f
     sup = set(int(p) for p in pix)
     full = [q for q in range(len(pix))
-            if all((iy[q] - iy[q] % 2 + dy) * n + (ix[q] - ix[q] % 2 + dx) in sup
-                   for dx in (0, 2) for dy in (0, 2))]
+            if all((iy[q] - iy[q] % s + dy) * n + (ix[q] - ix[q] % s + dx) in sup
+                   for dx in (0, s) for dy in (0, s))]
     assert len(full) > len(pix) // 2
     np.testing.assert_allclose(g[full], f[full], rtol=0, atol=1e-12)
     # at the support edge the renormalised weights still average nearby values

@@ -311,8 +311,8 @@ __global__ void k_point_order(ModelConst m, const double* cs_a, const int* p_cel
 }
 
 // Collimator bin probabilities: voxels [A][B][nq], scatter points [A][npc][B][kCPad]
-// with the points of each angle in the order of k_point_order.  Scatter-point
-// probabilities below kCollimatorFloor are stored as 0.
+// with the points of each angle in the order of k_point_order (k_chunk_range
+// then applies the floor to the scatter points).
 __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
                              const int* p_cell, const int* inv, float* cv, float* csp) {
     const int a = blockIdx.z, b = blockIdx.y;
@@ -333,23 +333,31 @@ __global__ void k_collimator(ModelConst m, const double* cs_a, const int* q_pix,
             double x, y;
             point_cm(m, false, inv[(size_t)a * m.np + r], q_pix, p_cell, &x, &y);
             const double u = -x * s + y * c, sg = sigma_coll(m, m.r_det - (x * c + y * s));
-            const double v = gauss_mass(lo, hi, u, sg);
-            val = v < kCollimatorFloor ? 0.f : (float)v;
+            val = (float)gauss_mass(lo, hi, u, sg);
         }
         const int pc = r / kPC, pl = r % kPC;
         csp[(((size_t)a * m.npc + pc) * m.B + b) * kCPad + pl] = val;
     }
 }
 
-// For every (angle, bin): the run of ordered points whose collimator
-// probability for that bin is non-zero, as [first, last + 1) (0, 0 if none).
-__global__ void k_chunk_range(ModelConst m, const float* csp, int2* range) {
+// For every (angle, bin): the floor on the scatter points' collimator
+// probabilities, then the run of ordered points whose probability for that
+// bin is non-zero, as [first, last + 1) (0, 0 if none).
+__global__ void k_chunk_range(ModelConst m, float* csp, int2* range) {
     const int a = blockIdx.y;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= m.B) return;
+    auto at = [&](int r) -> float& {
+        return csp[(((size_t)a * m.npc + r / kPC) * m.B + b) * kCPad + (r % kPC)];
+    };
+    // probabilities below kCollimatorFloorRel of this (angle, bin)'s largest become 0
+    float vmax = 0.f;
+    for (int r = 0; r < m.np; ++r) vmax = fmaxf(vmax, at(r));
+    const float floor_ab = kCollimatorFloorRel * vmax;
     int first = -1, last = -1;
     for (int r = 0; r < m.np; ++r) {
-        const float v = csp[(((size_t)a * m.npc + r / kPC) * m.B + b) * kCPad + (r % kPC)];
+        float& v = at(r);
+        if (v < floor_ab) v = 0.f;
         if (v != 0.f) {
             if (first < 0) first = r;
             last = r;

@@ -382,10 +382,6 @@ constexpr float kSurrogateEps = 1e-8f;   // target = ln(S + eps)
 // exp(-32) of its largest value and the surrogate's part is 0.
 constexpr float kSurrogateReachSigmas = kScatterReachSigmas;
 constexpr float kElectronRestKeV = 510.99895f;
-// Inputs 8 j .. 8 j + 7 (j = 0..3) of one (event, voxel, line); g8 holds the
-// 8 rho line integrals of the voxel at this angle.  Four threads can build
-// one sample's inputs side by side; surrogate_features calls this for all j,
-// so every kernel computes the same values.
 // Division in the network's input features: the fast approximate form on the
 // device (about 2 ulp; the inputs are rounded to BF16 afterwards), IEEE on the
 // host.
@@ -396,25 +392,26 @@ __host__ __device__ __forceinline__ float feature_div(float a, float b) {
     return a / b;
 #endif
 }
-__host__ __device__ __forceinline__ void surrogate_features_chunk(
-    int j, float xq, float yq, float ca, float sa, float ub, float e_hat, int w, float e_line,
-    float mu_w, const float* g8, const float* rho, int n, float h, float* f8) {
-    if (j == 0) {
-        f8[0] = xq * 0.05f;
-        f8[1] = yq * 0.05f;
-        f8[2] = ca;
-        f8[3] = sa;
-        f8[4] = ub * 0.05f;
-        f8[5] = (e_hat - 150.f) * 0.01f;
-        f8[6] = w == 0 ? 1.f : 0.f;
-        f8[7] = w == 1 ? 1.f : 0.f;
-        return;
-    }
-    if (j == 1) {
-        f8[0] = w == 2 ? 1.f : 0.f;
-        for (int k = 0; k < 7; ++k) f8[1 + k] = mu_w * g8[k] * 0.25f;
-        return;
-    }
+// The 32 inputs of one (event, voxel, line); g8 holds the 8 rho line
+// integrals of the voxel at this angle.  Every kernel builds them here, so
+// they all compute the same values.
+__host__ __device__ __forceinline__ void surrogate_features(float xq, float yq, float ca, float sa,
+                                                            float ub, float e_hat, int w,
+                                                            float e_line, float mu_w,
+                                                            const float* g8, const float* rho,
+                                                            int n, float h, float* f) {
+    f[0] = xq * 0.05f;
+    f[1] = yq * 0.05f;
+    f[2] = ca;
+    f[3] = sa;
+    f[4] = ub * 0.05f;
+    f[5] = (e_hat - 150.f) * 0.01f;
+    f[6] = w == 0 ? 1.f : 0.f;
+    f[7] = w == 1 ? 1.f : 0.f;
+    f[8] = w == 2 ? 1.f : 0.f;
+    for (int k = 0; k < 8; ++k) f[9 + k] = mu_w * g8[k] * 0.25f;
+    // detector coordinate and depth of the voxel, the Compton kappa of the
+    // recorded energy, and the scatter point p* on the bin's projection line
     const float uq = -xq * sa + yq * ca, tq = xq * ca + yq * sa;
     const float du = ub - uq;
     const float kappa = kElectronRestKeV * (feature_div(1.f, e_hat) - feature_div(1.f, e_line));
@@ -424,35 +421,22 @@ __host__ __device__ __forceinline__ void surrogate_features_chunk(
     const float dt = fminf(fmaxf(feature_div(fabsf(du) * c, s), -lim), lim);
     const float tp = tq + dt;
     const float xp = tp * ca - ub * sa, yp = tp * sa + ub * ca;
-    if (j == 2) {
-        f8[0] = mu_w * g8[7] * 0.25f;
-        f8[1] = du * 0.2f;
-        f8[2] = tq * 0.05f;
-        f8[3] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
-        f8[4] = feature_div(e_hat, e_line);
-        f8[5] = fabsf(du) * 0.2f;
-        f8[6] = xp * 0.05f;
-        f8[7] = yp * 0.05f;
-        return;
-    }
+    f[17] = du * 0.2f;
+    f[18] = tq * 0.05f;
+    f[19] = fminf(fmaxf(kappa, -2.f), 4.f) * 0.5f;
+    f[20] = feature_div(e_hat, e_line);
+    f[21] = fabsf(du) * 0.2f;
+    f[22] = xp * 0.05f;
+    f[23] = yp * 0.05f;
     const float r = sqrtf(dt * dt + du * du);
-    f8[0] = r * 0.05f;
-    f8[1] = c;
-    f8[2] = feature_div(h, r + h);
-    f8[3] = kappa < 0.f ? 1.f : 0.f;
+    f[24] = r * 0.05f;
+    f[25] = c;
+    f[26] = feature_div(h, r + h);
+    f[27] = kappa < 0.f ? 1.f : 0.f;
     const float gx = floorf(feature_div(xp, h) + 0.5f * n), gy = floorf(feature_div(yp, h) + 0.5f * n);
-    f8[4] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n) ? rho[(int)gy * n + (int)gx]
-                                                                       : 0.f;
-    f8[5] = f8[6] = f8[7] = 0.f;
-}
-__host__ __device__ __forceinline__ void surrogate_features(float xq, float yq, float ca, float sa,
-                                                            float ub, float e_hat, int w,
-                                                            float e_line, float mu_w,
-                                                            const float* g8, const float* rho,
-                                                            int n, float h, float* f) {
-    for (int j = 0; j < 4; ++j)
-        surrogate_features_chunk(j, xq, yq, ca, sa, ub, e_hat, w, e_line, mu_w, g8, rho, n, h,
-                                 f + 8 * j);
+    f[28] = (gx >= 0.f && gx < (float)n && gy >= 0.f && gy < (float)n) ? rho[(int)gy * n + (int)gx]
+                                                                      : 0.f;
+    f[29] = f[30] = f[31] = 0.f;
 }
 
 #ifdef __CUDACC__

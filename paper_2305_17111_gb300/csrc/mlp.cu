@@ -512,76 +512,82 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                 tc_mma(G.tmem, umma_desc(a0 + off), umma_desc(b0 + off), kTcIdesc, ks > 0 ? 1u : 0u);
             }
             tc_commit(G.bar);
-            if (!mbar_wait_bounded(G.bar, phase & 1)) {
-                S.abort[G.g] = 1;
-                atomicOr(status, kStatusTimeout);
-            }
         }
+        // every thread waits for the MMAs itself (no group barrier here); a
+        // warp in which a wait ran out skips the epilogue (its TMEM loads are
+        // warp-collective) and flags the group, which stops after the barrier
+        // that ends the layer
+        const bool done = __all_sync(0xffffffffu, mbar_wait_bounded(G.bar, phase & 1));
         ++phase;
-        group_sync(G.g);
-        if (S.abort[G.g]) return false;
+        if (!done) {
+            S.abort[G.g] = 1;
+            atomicOr(status, kStatusTimeout);
+        }
         tc_fence_after();
+        if (done) {
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-            const int cb = cc * 32;   // columns cb .. cb + 31
-            float v[32];
-            tc_ld32(G.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb, v);
-            const float4* bias4 = reinterpret_cast<const float4*>(F + layer * kHid + cb);
-            if (layer < 2) {
-                uint32_t hb[16];
+            for (int cc = 0; cc < 4; ++cc) {
+                const int cb = cc * 32;   // columns cb .. cb + 31
+                float v[32];
+                tc_ld32(G.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb, v);
+                const float4* bias4 = reinterpret_cast<const float4*>(F + layer * kHid + cb);
+                if (layer < 2) {
+                    uint32_t hb[16];
 #pragma unroll
-                for (int i = 0; i < 32; i += 4) {
-                    f32x2 z0 = pk(v[i], v[i + 1]), z1 = pk(v[i + 2], v[i + 3]);
-                    if (layer > 0) {   // the first layer's bias comes out of the MMA
-                        const float4 b = bias4[i >> 2];
-                        z0 = add2(z0, pk(b.x, b.y));
-                        z1 = add2(z1, pk(b.z, b.w));
+                    for (int i = 0; i < 32; i += 4) {
+                        f32x2 z0 = pk(v[i], v[i + 1]), z1 = pk(v[i + 2], v[i + 3]);
+                        if (layer > 0) {   // the first layer's bias comes out of the MMA
+                            const float4 b = bias4[i >> 2];
+                            z0 = add2(z0, pk(b.x, b.y));
+                            z1 = add2(z1, pk(b.z, b.w));
+                        }
+                        if (kStoreZ && z_row) {
+                            float a0, a1, a2, a3;
+                            upk(z0, a0, a1);
+                            upk(z1, a2, a3);
+                            __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
+                                z_row + layer * z_stride + cb + i);
+                            zp[0] = __floats2bfloat162_rn(a0, a1);
+                            zp[1] = __floats2bfloat162_rn(a2, a3);
+                        }
+                        float h0, h1, h2, h3;
+                        upk(gelu2_doubled(z0), h0, h1);
+                        upk(gelu2_doubled(z1), h2, h3);
+                        const __nv_bfloat162 t0 = __floats2bfloat162_rn(h0, h1);
+                        const __nv_bfloat162 t1 = __floats2bfloat162_rn(h2, h3);
+                        hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t0);
+                        hb[(i >> 1) + 1] = *reinterpret_cast<const uint32_t*>(&t1);
                     }
-                    if (kStoreZ && z_row) {
-                        float a0, a1, a2, a3;
-                        upk(z0, a0, a1);
-                        upk(z1, a2, a3);
-                        __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
-                            z_row + layer * z_stride + cb + i);
-                        zp[0] = __floats2bfloat162_rn(a0, a1);
-                        zp[1] = __floats2bfloat162_rn(a2, a3);
-                    }
-                    float h0, h1, h2, h3;
-                    upk(gelu2_doubled(z0), h0, h1);
-                    upk(gelu2_doubled(z1), h2, h3);
-                    const __nv_bfloat162 t0 = __floats2bfloat162_rn(h0, h1);
-                    const __nv_bfloat162 t1 = __floats2bfloat162_rn(h2, h3);
-                    hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t0);
-                    hb[(i >> 1) + 1] = *reinterpret_cast<const uint32_t*>(&t1);
-                }
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, cc >> 1, (cc & 1) * 4 + c)) =
-                        make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
-            } else {
-                const float4* w44 = reinterpret_cast<const float4*>(F + 3 * kHid + cb);
+                    for (int c = 0; c < 4; ++c)
+                        *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, cc >> 1, (cc & 1) * 4 + c)) =
+                            make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
+                } else {
+                    const float4* w44 = reinterpret_cast<const float4*>(F + 3 * kHid + cb);
 #pragma unroll
-                for (int i = 0; i < 32; i += 4) {
-                    const float4 b = bias4[i >> 2], ww = w44[i >> 2];
-                    const f32x2 z0 = add2(pk(v[i], v[i + 1]), pk(b.x, b.y));
-                    const f32x2 z1 = add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w));
-                    if (kStoreZ && z_row) {
-                        float a0, a1, a2, a3;
-                        upk(z0, a0, a1);
-                        upk(z1, a2, a3);
-                        __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
-                            z_row + layer * z_stride + cb + i);
-                        zp[0] = __floats2bfloat162_rn(a0, a1);
-                        zp[1] = __floats2bfloat162_rn(a2, a3);
+                    for (int i = 0; i < 32; i += 4) {
+                        const float4 b = bias4[i >> 2], ww = w44[i >> 2];
+                        const f32x2 z0 = add2(pk(v[i], v[i + 1]), pk(b.x, b.y));
+                        const f32x2 z1 = add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w));
+                        if (kStoreZ && z_row) {
+                            float a0, a1, a2, a3;
+                            upk(z0, a0, a1);
+                            upk(z1, a2, a3);
+                            __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(
+                                z_row + layer * z_stride + cb + i);
+                            zp[0] = __floats2bfloat162_rn(a0, a1);
+                            zp[1] = __floats2bfloat162_rn(a2, a3);
+                        }
+                        sacc2 = fma2(gelu2_doubled(z0), pk(ww.x, ww.y), sacc2);
+                        sacc2 = fma2(gelu2_doubled(z1), pk(ww.z, ww.w), sacc2);
                     }
-                    sacc2 = fma2(gelu2_doubled(z0), pk(ww.x, ww.y), sacc2);
-                    sacc2 = fma2(gelu2_doubled(z1), pk(ww.z, ww.w), sacc2);
                 }
             }
         }
         if (layer < 2) fence_async_smem();
         tc_fence_before();
         group_sync(G.g);
+        if (S.abort[G.g]) return false;
     }
     float s_even, s_odd;
     upk(sacc2, s_even, s_odd);
@@ -968,29 +974,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_surrogate_rows(const Surrogat
             const int n_act = Cnt[wl];
             const uint8_t* act = Act + wl * 128;
             for (int c = 0; c < (n_act + 3) / 4 && ok; ++c) {
-                // inputs 8 j .. 8 j + 7 of sample smp (listed event 4c + smp / 32,
-                // voxel smp mod 32) into chunk j of row smp of X
-                for (int k = gt; k < 128 * 4; k += kGrpThreads) {
-                    const int smp = k & 127, j = k >> 7;   // j is the same across a warp
-                    const int slot = c * 4 + (smp >> 5), ql = smp & 31;
-                    float f8[8];
+                // the 32 inputs of the thread's own sample gt (listed event
+                // 4c + gt / 32, voxel gt mod 32) into row gt of X, built in one
+                // piece so the geometry shared by the last 16 is formed once
+                {
+                    const int slot = c * 4 + (gt >> 5), ql = gt & 31;
+                    float f[32];
                     if (slot < n_act && ql < nq_here) {
                         const int e = act[slot];
-                        surrogate_features_chunk(j, Vxy[2 * ql], Vxy[2 * ql + 1], ca, sa,
-                                                 Eeu[2 * e + 1], Eeu[2 * e], wl, P.e_line[wl],
-                                                 P.mu_line[wl], Vg8 + ql * 8, P.rho, P.n, P.h, f8);
+                        surrogate_features(Vxy[2 * ql], Vxy[2 * ql + 1], ca, sa, Eeu[2 * e + 1],
+                                           Eeu[2 * e], wl, P.e_line[wl], P.mu_line[wl],
+                                           Vg8 + ql * 8, P.rho, P.n, P.h, f);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) f8[i] = 0.f;
+                        for (int i = 0; i < 32; ++i) f[i] = 0.f;
                     }
-                    uint32_t u[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const __nv_bfloat162 t = __floats2bfloat162_rn(f8[2 * i], f8[2 * i + 1]);
-                        u[i] = *reinterpret_cast<const uint32_t*>(&t);
+                    for (int j = 0; j < 4; ++j) {
+                        uint32_t u[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const __nv_bfloat162 t =
+                                __floats2bfloat162_rn(f[8 * j + 2 * i], f[8 * j + 2 * i + 1]);
+                            u[i] = *reinterpret_cast<const uint32_t*>(&t);
+                        }
+                        *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(gt, 0, j)) =
+                            make_uint4(u[0], u[1], u[2], u[3]);
                     }
-                    *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(smp, 0, j)) =
-                        make_uint4(u[0], u[1], u[2], u[3]);
                 }
                 tc_input_constants(S, G);
                 fence_async_smem();

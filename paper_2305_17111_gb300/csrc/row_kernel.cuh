@@ -185,7 +185,7 @@ __device__ __forceinline__ void stage_fp32(const unsigned char* sb, const float*
                                            int pq0, int pq1) {
     const float* tb = reinterpret_cast<const float*>(sb) + v0 * kPC;
     const int lo = kFull ? 0 : pq0, hi = kFull ? kPC / 4 : pq1;
-#pragma unroll 4
+#pragma unroll 2
     for (int pq = lo; pq < hi; ++pq) {
         f32x2 cA[EPL], cB[EPL];
 #pragma unroll

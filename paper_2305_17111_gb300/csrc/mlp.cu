@@ -501,15 +501,23 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
     const int row = G.gt;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
     f32x2 sacc2 = pk(0.f, 0.f);   // output layer: even and odd columns
+    // descriptors of the operands' first K slices; a slice off bytes further
+    // on is the same descriptor plus off / 16 (the 14-bit address field of a
+    // shared-memory operand below 256 KB does not carry)
+    const uint64_t da = umma_desc(S.sbase + G.h);
+    // the three layers one after the other, each specialised at compile time
+#pragma unroll
     for (int layer = 0; layer < 3; ++layer) {
         if (G.gt == 0) {
             tc_fence_after();
-            const uint32_t a0 = S.sbase + G.h;
-            const uint32_t b0 = S.sbase + (layer == 0 ? kTcOffW1 : layer == 1 ? kTcOffW2 : kTcOffW3);
-            const int ksteps = layer == 0 ? 4 : 8;
-            for (int ks = 0; ks < ksteps; ++ks) {
+            const uint64_t db =
+                umma_desc(S.sbase + (layer == 0 ? kTcOffW1 : layer == 1 ? kTcOffW2 : kTcOffW3));
+            constexpr int kMaxSteps = 8;
+#pragma unroll
+            for (int ks = 0; ks < kMaxSteps; ++ks) {
+                if (layer == 0 && ks >= 4) break;
                 const uint32_t off = (uint32_t)(ks >> 2) * kAtomBlock + (uint32_t)(ks & 3) * 32u;
-                tc_mma(G.tmem, umma_desc(a0 + off), umma_desc(b0 + off), kTcIdesc, ks > 0 ? 1u : 0u);
+                tc_mma(G.tmem, da + (off >> 4), db + (off >> 4), kTcIdesc, ks > 0 ? 1u : 0u);
             }
             tc_commit(G.bar);
         }

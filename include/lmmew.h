@@ -294,6 +294,45 @@ int lm_batch_tuning(const lm_handle* h, double* out5);
  * depend on it.  Not part of the paper's method.  Errors: INVALID_ARG. */
 int lm_set_tile_events(lm_handle* h, int tile_events);
 
+/* Streamed single-scatter path tables.  The tables the row kernel reads hold
+ * the per-path quantities of Eq. (s_p) with n = 1 for every (angle, line,
+ * voxel, scatter point): 12 bytes x A x W x Q x P (1.6 GB for 64^2 with a
+ * 64^2 scatter grid, 14 GB for 128^2).  The paper computes them per detector
+ * angle inside the angle's kernel (Algorithm 1); here they are tabulated
+ * once, which costs memory that grows as A W Q P.  With max_angles > 0 the
+ * handle keeps the tables of at most max_angles angles: each row launch of
+ * lm_forward, lm_backproject and lm_osem covers its angles in blocks of that
+ * many, rebuilding a block's tables on the device (the set-up's own kernel,
+ * so the values are the same bits) unless they are the resident ones.
+ * Results are bit-identical to resident tables; a rebuild per block and
+ * sub-iteration costs about 1/A of lm_create's set-up time per angle.
+ * max_angles = 0 (or >= n_angles) makes every angle resident again.
+ * lm_create streams by itself when all angles' tables do not fit 90 % of the
+ * free device memory or the process's table budget (lm_set_table_budget),
+ * with as many angles as fit half the free memory (or the budget).
+ * Streamed tables serve the exact scatter model of lm_forward,
+ * lm_forward_noalloc, lm_backproject and lm_osem; lm_osem keeps the
+ * handle's tile size instead of autotuning; the reduced-precision form
+ * (lm_set_scatter_precision), lm_osem_batch with the exact model and
+ * lm_surrogate_sample return NOT_IMPLEMENTED until the tables are resident
+ * again.  The call synchronises the device.  Not part of the paper's
+ * method.  Errors: INVALID_ARG (max_angles < 0), NOT_IMPLEMENTED (reduced
+ * precision selected), OOM (the new buffer does not fit: the old one is
+ * kept). */
+int lm_set_table_streaming(lm_handle* h, int max_angles);
+
+/* The table mode: *max_angles = angles the streamed buffer holds (0: every
+ * angle resident), *table_bytes = device bytes of the table buffer.  Errors:
+ * INVALID_ARG. */
+int lm_table_streaming(const lm_handle* h, int* max_angles, int64_t* table_bytes);
+
+/* Process-wide limit in bytes on the path tables lm_create keeps resident;
+ * a model whose tables exceed it is created with streamed tables (see
+ * lm_set_table_streaming).  0 (the default): only the device's free memory
+ * limits them.  Applies to later lm_create calls of every thread.  Not part
+ * of the paper's method.  Errors: INVALID_ARG (bytes < 0). */
+int lm_set_table_budget(int64_t bytes);
+
 /* Energy-window pruning of the single-scatter terms (on by default).  A
  * photon of line w scattered once leaves with E' between its backscatter
  * energy E_w / (1 + 2 E_w / m_e c^2) and E_w (Compton's relation, paper

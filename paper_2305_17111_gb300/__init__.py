@@ -29,6 +29,13 @@ def probe_ex2_rate(stream=None) -> dict:
     return {"f32": out[0], "f16x2": out[1], "bf16x2": out[2], "sm_mhz": out[3]}
 
 
+def set_table_budget(nbytes: int) -> None:
+    """Process-wide limit on the path-table bytes Model creation keeps
+    resident; larger tables are created streamed (0: no limit beyond the
+    device's free memory)."""
+    _native.check(_native.load().lm_set_table_budget(int(nbytes)))
+
+
 def _torch():
     import torch
     return torch
@@ -272,6 +279,21 @@ class Model:
         """Evaluate each event's single-scatter terms only for the lines whose
         scatter can reach its recorded energy (default), or for every line."""
         _native.check(_native.load().lm_set_energy_pruning(self._h, 1 if enable else 0))
+
+    def set_table_streaming(self, max_angles: int = 0):
+        """Keep the single-scatter path tables of at most max_angles angles on
+        the device, rebuilding each block of angles a row launch needs (0:
+        every angle resident).  Results are bit-identical either way."""
+        _native.check(_native.load().lm_set_table_streaming(self._h, int(max_angles)))
+
+    def table_streaming(self):
+        """(angles the streamed table buffer holds, 0 if every angle is
+        resident; bytes of the table buffer)."""
+        slots = ctypes.c_int(0)
+        nbytes = ctypes.c_int64(0)
+        _native.check(_native.load().lm_table_streaming(self._h, ctypes.byref(slots),
+                                                         ctypes.byref(nbytes)))
+        return slots.value, nbytes.value
 
     PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 

@@ -83,6 +83,10 @@ SYMBOLS = {
     "lm_batch_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "lm_set_tile_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_set_energy_pruning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lm_set_table_streaming": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lm_table_streaming": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "lm_set_table_budget": (ctypes.c_int, [ctypes.c_int64]),
     "lm_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lm_set_coarse_stride": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lm_destroy": (ctypes.c_int, [ctypes.c_void_p]),

@@ -258,6 +258,32 @@ int launch_row_profiled(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     return LMMEW_OK;
 }
 
+// The row launch L, whose tiles belong to ranks [r_lo, r_hi) of the sort
+// (rank r_lo + i holds angle a_first + i a_step).  With the exact scatter
+// model and streamed path tables, the ranks go in blocks of as many angles
+// as the table buffer holds: each block's tables are built unless they are
+// resident, and the launch is clipped on the device to the block's tiles.
+int launch_row_ranks(lm_handle* h, const RowLaunch& L, const SortedEvents& se, int r_lo,
+                     int r_hi, int a_first, int a_step, cudaStream_t st) {
+    if (!h->tab_slots || h->scatter_model != LMMEW_SCATTER_EXACT || h->mc.np == 0)
+        return launch_row_profiled(h, L, st);
+    if (!L.range)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED, "streamed path tables need a planned row range");
+    const int C = se.n_classes;
+    for (int r0 = r_lo; r0 < r_hi; r0 += h->tab_slots) {
+        const int r1 = std::min(r_hi, r0 + h->tab_slots);
+        int rc = stream_tables(h, a_first + (r0 - r_lo) * a_step, a_step, r1 - r0, st);
+        if (rc == LMMEW_OK) rc = launch_clip_range(h, L.range, se, r0 * C, r1 * C, h->d_clip, st);
+        if (rc != LMMEW_OK) return rc;
+        RowLaunch Lc = L;
+        Lc.range = h->d_clip;
+        if (r0 != r_lo) Lc.n_events = 0;
+        rc = launch_row_profiled(h, Lc, st);
+        if (rc != LMMEW_OK) return rc;
+    }
+    return LMMEW_OK;
+}
+
 ForwardPlan forward_plan(const lm_handle* h, int64_t n, int64_t cap_max) {
     ForwardPlan p;
     p.G = sort_groups(h, h->mc.A);
@@ -293,7 +319,7 @@ int forward_async(lm_handle* h, const lm_events* ev, const float* image, float* 
                     k == 0 ? p.n : 0};
         L.tile_ev = se.tile_ev;
         L.range = ranges + k;
-        rc = launch_row_profiled(h, L, st);
+        rc = launch_row_ranks(h, L, se, 0, h->mc.A, 0, 1, st);   // one subset: rank = angle
         if (rc == LMMEW_OK)
             rc = launch_forward_out_range(h, ypart, p.cap, p.cap, ranges + k, se.perm, out_y, st);
     }
@@ -445,6 +471,16 @@ int lm_destroy(lm_handle* h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     cudaFree(h->d_tabh);
     cudaFree(h->d_tscale);
+    cudaFree(h->d_cs_a);
+    cudaFree(h->d_p_cell);
+    cudaFree(h->d_p_rho);
+    cudaFree(h->d_gqp);
+    cudaFree(h->d_dqp);
+    cudaFree(h->d_gp);
+    cudaFree(h->d_on_det);
+    cudaFree(h->d_inv);
+    cudaFree(h->d_mu_line);
+    cudaFree(h->d_clip);
     cudaFree(h->d_term_counter);
     cudaFree(h->d_work);
     cudaFree(h->d_cv);
@@ -749,7 +785,7 @@ int lm_backproject(lm_handle* h, const lm_events* ev, const float* weight, float
                     k == 0 ? n : 0};
         L.tile_ev = se.tile_ev;
         L.range = ranges + k;
-        rc = launch_row_profiled(h, L, st);
+        rc = launch_row_ranks(h, L, se, 0, m.A, 0, 1, st);   // one subset: rank = angle
         if (rc == LMMEW_OK)
             rc = launch_bp_partial_range(h, rows, rs, nullptr, 0, fp.cap, ranges + k, se.perm,
                                          weight, bpart, (int64_t)k * ppc, nullptr, st);
@@ -791,7 +827,10 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
     // tuned once (set-up: the counts are read back and trial launches timed)
     const int first_ranks = (m.A + n_subsets - 1) / n_subsets;
     const uint64_t key = tune_key_for(h, (double)n / m.A);
-    if (!tune_known(h, key)) {
+    // (the trial launches would read every angle of the first ranks: with
+    // streamed tables the handle's tile size is kept as it is)
+    const bool streamed = h->tab_slots && h->scatter_model == LMMEW_SCATTER_EXACT && m.np > 0;
+    if (!streamed && !tune_known(h, key)) {
         rc = read_back_counts(h, &se, st);
         if (rc == LMMEW_OK) rc = autotune_run(h, se, first_ranks, key, st);
         if (rc != LMMEW_OK) return rc;
@@ -828,6 +867,9 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
     ChunkRange* ranges = bump<ChunkRange>(w, (size_t)n_subsets * blocks);
     rc = launch_gather_image(h, image, lam_v, st);
     if (rc == LMMEW_OK) rc = launch_plan(h, se, n_subsets, blocks, tpc, ranges, st);
+    // the first rank of each subset (subsets ascending, angles ascending inside one)
+    std::vector<int> r_first(n_subsets + 1, 0);
+    for (int s = 0; s < n_subsets; ++s) r_first[s + 1] = r_first[s] + (m.A - s + n_subsets - 1) / n_subsets;
     for (int it = start_iter; it < n_iters && rc == LMMEW_OK; ++it) {
         for (int s = (it == start_iter ? start_subset : 0); s < n_subsets && rc == LMMEW_OK; ++s) {
             const ChunkRange* rg = ranges + (size_t)s * blocks;
@@ -836,7 +878,7 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
                             (s == 0 && k == 0) ? n : 0};
                 L.tile_ev = te;
                 L.range = rg + k;
-                rc = launch_row_profiled(h, L, st);
+                rc = launch_row_ranks(h, L, se, r_first[s], r_first[s + 1], s, n_subsets, st);
                 if (rc == LMMEW_OK)
                     rc = launch_bp_partial_range(h, rows, rs, ypart, cap, cap, rg + k, nullptr,
                                                  nullptr, bpart, (int64_t)k * ppc, llpart, st);
@@ -874,6 +916,10 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
     }
     if (n_total >= (int64_t(1) << 31))
         return set_error(LMMEW_ERR_INVALID_ARG, "at most 2^31 - 1 events per batch");
+    if (h->tab_slots && h->scatter_model == LMMEW_SCATTER_EXACT && m.np > 0)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "batched reconstruction needs every angle's path tables resident "
+                         "(lm_set_table_streaming(h, 0)) or a surrogate or scatter-free model");
     const int R = n_real;
     const int A_s = (m.A + n_subsets - 1) / n_subsets;
     const int64_t V = (int64_t)n_subsets * A_s;
@@ -1073,6 +1119,24 @@ int lm_set_tile_events(lm_handle* h, int tile_events) {
     if (tile_events != 32 && tile_events != 64 && tile_events != kET)
         return set_error(LMMEW_ERR_INVALID_ARG, "tile_events must be 32, 64 or 128");
     h->tile_ev = tile_events;
+    return LMMEW_OK;
+}
+
+int lm_set_table_streaming(lm_handle* h, int max_angles) {
+    if (!h) return set_error(LMMEW_ERR_INVALID_ARG, "handle is NULL");
+    return set_table_streaming(h, max_angles);
+}
+
+int lm_table_streaming(const lm_handle* h, int* max_angles, int64_t* table_bytes) {
+    if (!h || !max_angles || !table_bytes) return set_error(LMMEW_ERR_INVALID_ARG, "NULL argument");
+    *max_angles = h->tab_slots;
+    *table_bytes = (int64_t)h->tab_bytes;
+    return LMMEW_OK;
+}
+
+int lm_set_table_budget(int64_t bytes) {
+    if (bytes < 0) return set_error(LMMEW_ERR_INVALID_ARG, "the table budget must be >= 0");
+    g_table_budget = bytes;
     return LMMEW_OK;
 }
 

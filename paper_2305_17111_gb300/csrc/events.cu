@@ -354,6 +354,9 @@ int sort_and_tile(lm_handle* h, const lm_events* ev, int G, const int* rank_of_a
 int status_error(int status) {
     if (status & kStatusTimeout)
         return set_error(LMMEW_ERR_TIMEOUT, "a kernel of an earlier call timed out in a pipeline wait");
+    if (status & kStatusTables)
+        return set_error(LMMEW_ERR_CUDA,
+                         "a row launch needed path tables that were not resident (internal error)");
     if (status & kStatusOutOfRange)
         return set_error(LMMEW_ERR_OUT_OF_RANGE,
                          "an event has an angle or bin outside the model or an energy outside "
@@ -580,6 +583,26 @@ int launch_plan(lm_handle* h, const SortedEvents& se, int n_subsets, int blocks_
     k_plan<<<(total + 127) / 128, 128, 0, st>>>(se.group_start, se.tile_start, se.tiles, h->mc.A,
                                                 se.n_classes, n_subsets, blocks_per_set,
                                                 tiles_per_block, ranges);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    return LMMEW_OK;
+}
+
+namespace {
+__global__ void k_clip_range(const ChunkRange* in, const int* tile_start, int g0, int g1,
+                             ChunkRange* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ChunkRange R = *in;
+    const int x = max(R.x, tile_start[g0]);
+    R.y = max(x, min(R.y, tile_start[g1]));
+    R.x = x;
+    *out = R;
+}
+}  // namespace
+
+int launch_clip_range(lm_handle* h, const ChunkRange* in, const SortedEvents& se, int g0, int g1,
+                      ChunkRange* out, cudaStream_t st) {
+    k_clip_range<<<1, 32, 0, st>>>(in, se.tile_start, g0, g1, out);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;

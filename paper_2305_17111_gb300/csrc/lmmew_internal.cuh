@@ -38,6 +38,7 @@ constexpr float kCollimatorFloorRel = 1e-7f;
 // Status bits written by kernels into the handle's device status word.
 constexpr int kStatusOutOfRange = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusTables = 4;   // a row launch met an angle whose path tables were not resident
 
 // ---------------------------------------------------------------- model
 // Model constants passed by value to the setup kernels (FP64).
@@ -123,6 +124,22 @@ struct lm_handle {
     int grp_classes = 0;
     std::map<int, int*> grp_cache;
     size_t tab_bytes = 0;
+    // Streamed path tables: with tab_slots > 0, d_tab holds the tables of at
+    // most tab_slots angles, a0 + i astep (i < tab_count), rebuilt by k_scatter
+    // when a row launch needs other angles; 0: every angle resident
+    int tab_slots = 0;
+    int tab_a0 = 0, tab_astep = 1, tab_count = 0;
+    // what k_scatter needs to rebuild tables, kept from the set-up
+    double* d_cs_a = nullptr;      // [A][2] cos, sin of each detector direction
+    int* d_p_cell = nullptr;       // [np] cell of each scatter point
+    double* d_p_rho = nullptr;     // [np] its mean density
+    double* d_gqp = nullptr;       // [nq][np] voxel-to-point line integrals of rho
+    double* d_dqp = nullptr;       // [nq][np] voxel-to-point distances
+    double* d_gp = nullptr;        // [A][np] point-to-detector line integrals
+    double* d_on_det = nullptr;    // [A][np] collimator mass of each point on the detector
+    int* d_inv = nullptr;          // [A][np] point of each slot of an angle's point order
+    double* d_mu_line = nullptr;   // [W] mu_water at each line energy
+    lmmew::ChunkRange* d_clip = nullptr;   // a row launch's tiles clipped to one angle block
     // cached subset sensitivities for the last partition asked for
     int sens_parts = 0;
     double* d_sens_sub = nullptr;  // [parts][nq]
@@ -194,6 +211,14 @@ int cuda_error(cudaError_t e, const char* what);
 
 // setup.cu
 int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_host);
+// setup.cu: the path tables of angles a0 + i astep (i < count) into the
+// streamed table buffer (nothing to do if they are resident), and the switch
+// between streamed (max_angles > 0) and resident (0) tables
+int stream_tables(lm_handle* h, int a0, int astep, int count, cudaStream_t st);
+int set_table_streaming(lm_handle* h, int max_angles);
+// setup.cu: tables larger than this are streamed by lm_create (0: no limit
+// beyond the device's free memory)
+extern int64_t g_table_budget;
 // events.cu: the energy classes of the handle's lines and energy model
 void build_energy_classes(lm_handle* h);
 int subset_sensitivity(lm_handle* h, int n_subsets, cudaStream_t st);
@@ -270,6 +295,11 @@ int forward_async(lm_handle* h, const lm_events* ev, const float* image, float* 
 // tiles [T0 + k tpc, T0 + (k + 1) tpc) of the set's tiles [T0, T1).
 int launch_plan(lm_handle* h, const SortedEvents& se, int n_subsets, int blocks_per_set,
                 int tiles_per_block, ChunkRange* ranges, cudaStream_t st);
+// events.cu: a row block's range clipped on the device to the tiles of groups
+// [g0, g1) (one angle block of streamed path tables); row base and events
+// stay the block's
+int launch_clip_range(lm_handle* h, const ChunkRange* in, const SortedEvents& se, int g0, int g1,
+                      ChunkRange* out, cudaStream_t st);
 
 size_t sort_batch_scratch_bytes(int64_t n, int64_t G, int R);
 int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,

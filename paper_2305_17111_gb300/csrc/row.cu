@@ -15,9 +15,12 @@ namespace {
 // Kernel for W lines, scatter precision prec and tiles of tile_ev events.
 // The FP32 form with up to 4 lines has tiles of 32 and 64 events in the
 // VPL = 2 layout (2 and 4 events per lane); everything else runs 128-event
-// tiles in the VPL = 4 layout.
-RowKernel row_kernel_for(int W, int prec, int tile_ev = kET) {
+// tiles in the VPL = 4 layout.  With streamed tables (FP32 only) the
+// 64-event kernel also serves 32-event tiles.
+RowKernel row_kernel_for(int W, int prec, int tile_ev = kET, bool streamed = false) {
     if (prec != 0) return row_kernel_half(W, prec);
+    if (streamed)
+        return W <= 4 && tile_ev <= 64 ? row_kernel_f32_t64(W, true) : row_kernel_f32_t128(W, true);
     if (W <= 4 && tile_ev == 32) return row_kernel_f32_t32(W);
     if (W <= 4 && tile_ev == 64) return row_kernel_f32_t64(W);
     return row_kernel_f32_t128(W);
@@ -29,6 +32,9 @@ static RowParams make_params(lm_handle* h, const RowLaunch& L, int prec) {
     const ModelConst& m = h->mc;
     RowParams P;
     P.tab = h->d_tab;
+    P.tab_a0 = h->tab_slots ? h->tab_a0 : 0;
+    P.tab_astep = h->tab_slots ? h->tab_astep : 1;
+    P.tab_nslots = h->tab_slots ? h->tab_count : h->mc.A;
     P.tabh = h->d_tabh;
     P.tscale = h->d_tscale;
     P.cs = h->d_cs;
@@ -97,14 +103,17 @@ int row_kernel_occupancy(lm_handle* h) {
             continue;
         }
         LMMEW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-        // the 32- and 64-event tile kernels of the FP32 form (same stages)
-        for (int te = 32; prec == 0 && te < kET; te *= 2) {
-            RowKernel small = row_kernel_for(h->mc.W, 0, te);
-            if (small == kern) continue;
-            cudaFuncAttributes fs;
-            LMMEW_CUDA(cudaFuncGetAttributes(&fs, small));
-            LMMEW_CUDA(cudaFuncSetAttribute(small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            max_optin - (int)fs.sharedSizeBytes));
+        // the 32- and 64-event tile kernels of the FP32 form and the
+        // streamed-table kernels (same stages)
+        for (int te = 32; prec == 0 && te <= kET; te *= 2) {
+            for (int streamed = 0; streamed < 2; ++streamed) {
+                RowKernel other = row_kernel_for(h->mc.W, 0, te, streamed != 0);
+                if (other == kern) continue;
+                cudaFuncAttributes fs;
+                LMMEW_CUDA(cudaFuncGetAttributes(&fs, other));
+                LMMEW_CUDA(cudaFuncSetAttribute(other, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                max_optin - (int)fs.sharedSizeBytes));
+            }
         }
         int blocks = 0;
         LMMEW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kRowThreads, smem));
@@ -127,7 +136,8 @@ int launch_row_kernel(lm_handle* h, const RowLaunch& L, cudaStream_t st) {
     // the tiles were cut with L.tile_ev events; the 128-event kernel serves
     // any tile (and every form without small tiles)
     LMMEW_CUDA(cudaMemsetAsync(h->d_work, 0, sizeof(int), st));
-    row_kernel_for(h->mc.W, prec, L.tile_ev)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
+    const bool streamed = h->tab_slots != 0 && prec == 0;
+    row_kernel_for(h->mc.W, prec, L.tile_ev, streamed)<<<grid, kRowThreads, 2 * P.stage_bytes, st>>>(P);
     ++h->launches;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
@@ -207,6 +217,10 @@ int set_precision(lm_handle* h, int prec) {
         h->prec = 0;
         return LMMEW_OK;
     }
+    if (h->tab_slots)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "the reduced-precision form needs every angle's path tables resident "
+                         "(lm_set_table_streaming(h, 0))");
     if (!row_kernel_for(h->mc.W, prec) || h->row_blocks[prec] == 0)
         return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
                          "the reduced-precision form supports up to 4 lines");

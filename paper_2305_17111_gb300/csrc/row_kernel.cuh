@@ -44,7 +44,9 @@
 namespace lmmew {
 
 struct RowParams {
-    const float* tab;     // [A][nqt][npc][3][W][kQT][kPC]: nlh, sr, m
+    const float* tab;     // [slots][nqt][npc][3][W][kQT][kPC]: nlh, sr, m
+    int tab_a0, tab_astep;   // angle a's tables in slot (a - tab_a0) / tab_astep
+    int tab_nslots;          // slots holding tables (a unit outside them is skipped and flagged)
     const float* tabh;    // reduced-precision form: [A][nqt][npc]{-E' f32 [W][kQT][kPC],
                           //   (lh - base, nk) halves [W][kQT][kPC/4][8]}
     const float* tscale;  // [A][nqt][npc] 2^base of each block (reduced precision)
@@ -82,9 +84,13 @@ typedef void (*RowKernel)(const RowParams);
 // parallel): FP32 tiles of 32 and 64 events (up to 4 lines), FP32 tiles of
 // 128 events (any line count) and the reduced-precision forms (128-event
 // tiles, up to 4 lines).  nullptr where a combination does not exist.
+// With streamed path tables (`streamed`), the forms that read them index a
+// block of angles (RowParams::tab_a0, tab_astep) and check that every tile's
+// angle is in it: separate instantiations of the 64- and 128-event kernels,
+// so that the resident form's code is left as it is.
 RowKernel row_kernel_f32_t32(int W);
-RowKernel row_kernel_f32_t64(int W);
-RowKernel row_kernel_f32_t128(int W);
+RowKernel row_kernel_f32_t64(int W, bool streamed = false);
+RowKernel row_kernel_f32_t128(int W, bool streamed = false);
 RowKernel row_kernel_half(int W, int prec);
 
 #ifdef LMMEW_ROW_KERNEL_BODY
@@ -310,8 +316,9 @@ __device__ __forceinline__ void stage_half_n(int nw, const unsigned char* sb, co
 // the warp, each for 16 events at a time (EPL per lane, tiles of 16 EPL), so
 // a table entry read from shared memory (one broadcast per half-warp) feeds
 // twice the events of the VPL = 4 layout at the same tile size.
-template <int W, int PREC, int EPL, int VPL>
+template <int W, int PREC, int EPL, int VPL, bool kStream = false>
 __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
+    static_assert(!kStream || PREC == 0, "streamed tables are FP32");
     static_assert(VPL == 4 || VPL == 2, "4 or 2 voxels per lane");
     constexpr int kLanesEv = VPL == 4 ? 32 : 16;     // lanes that share one voxel set
     extern __shared__ __align__(128) unsigned char smem[];
@@ -389,6 +396,18 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
                 p_hi = max(p_hi, r.y);
             }
         }
+        // the slot of the angle's tables; with streamed tables a tile whose
+        // angle is not in the buffer is a planning error: its scatter terms
+        // are not read, and the status word says so
+        int slot = T.a;
+        if constexpr (kStream) {
+            slot = (T.a - P.tab_a0) / P.tab_astep;
+            if (nw > 0 && !(slot >= 0 && slot < P.tab_nslots && P.tab_a0 + slot * P.tab_astep == T.a)) {
+                if (tid == 0) atomicOr(P.status, kStatusTables);
+                p_hi = 0;
+                p_lo = P.np;
+            }
+        }
         const int pc_lo = p_lo < p_hi ? p_lo / kPC : 0;
         const int pc_hi = p_lo < p_hi ? (p_hi + kPC - 1) / kPC : 0;
         if (P.term_counter && tid == 0) {
@@ -399,7 +418,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
         }
         if (pc_lo < pc_hi) {
             const float* tab_u = (PREC == 0 ? P.tab : P.tabh) +
-                                 ((size_t)T.a * P.nqt + qt) * P.npc * (size_t)kTabBlock;
+                                 ((size_t)slot * P.nqt + qt) * P.npc * (size_t)kTabBlock;
             const float* scale_u = P.tscale + ((size_t)T.a * P.nqt + qt) * P.npc;
             const float* cs_u = P.cs + ((size_t)T.a * P.npc * P.B + b_lo) * kCPad;
             // A stage holds kc point chunks: kc blocks [component][staged

@@ -97,6 +97,10 @@ extern "C" int lm_surrogate_sample(lm_handle* h, const lm_events* ev, int64_t n,
     if (m.W > 3) return set_error(LMMEW_ERR_NOT_IMPLEMENTED, "the surrogate covers up to 3 lines");
     if (m.nq <= 0 || m.W <= 0) return set_error(LMMEW_ERR_INVALID_ARG, "the model has no voxels");
     if (n == 0) return LMMEW_OK;
+    if (h->tab_slots && m.np > 0)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "sampling exact targets reads every angle's path tables; make them "
+                         "resident first (lm_set_table_streaming(h, 0))");
     cudaStream_t st = (cudaStream_t)stream;
     SampleParams P;
     P.tab = h->d_tab;

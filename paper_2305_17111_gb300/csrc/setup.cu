@@ -411,13 +411,19 @@ __global__ void k_on_detector(ModelConst m, const double* cs_a, const int* p_cel
                    sigma_coll(m, m.r_det - (xpc * c + ypc * s)));
 }
 
-__global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_a,
-                                                 const int* q_pix, const int* p_cell,
-                                                 const double* p_rho, const double* g_qp,
-                                                 const double* d_qp, const double* g_p,
-                                                 const double* mu_line, const int* inv,
-                                                 const double* on_det, float* tab, double* sens_a) {
-    const int a = blockIdx.y;
+// Block (x, y): 8 voxels (a warp each) of angle a0 + y astep, whose tables go
+// to slot y of tab; with kSens the angle's scatter sensitivity is added to
+// sens_a (the set-up pass over every angle), without it only the tables are
+// written (a streamed angle block rebuilt; the same table values).
+template <bool kSens>
+__global__ void __launch_bounds__(256) k_scatter(ModelConst m, int a0, int astep,
+                                                 const double* cs_a, const int* q_pix,
+                                                 const int* p_cell, const double* p_rho,
+                                                 const double* g_qp, const double* d_qp,
+                                                 const double* g_p, const double* mu_line,
+                                                 const int* inv, const double* on_det, float* tab,
+                                                 double* sens_a) {
+    const int slot = blockIdx.y, a = a0 + slot * astep;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.x * 8 + warp;
     if (q >= m.nq) return;
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
     double sens = 0.0;
     for (int pc = 0; pc < m.npc; ++pc) {
         const int r = pc * kPC + lane;   // slot in this angle's point order
-        float* base = tab + (((size_t)a * m.nqt + qt) * m.npc + pc) * (size_t)(3 * m.W * kQT * kPC);
+        float* base = tab + (((size_t)slot * m.nqt + qt) * m.npc + pc) * (size_t)(3 * m.W * kQT * kPC);
         if (r >= m.np) {
             for (int w = 0; w < m.W; ++w) {
                 base[((0 * m.W + w) * kQT + ql) * kPC + lane] = kPosHuge;
@@ -491,13 +497,15 @@ __global__ void __launch_bounds__(256) k_scatter(ModelConst m, const double* cs_
                 wgt > 0.0 ? (float)(att - log2_pos_f(pref * pre)) : kPosHuge;
             base[((1 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)sr : 0.f;
             base[((2 * m.W + w) * kQT + ql) * kPC + lane] = wgt > 0.0 ? (float)(-sr * e1) : 0.f;
-            if (path > 0.0)
+            if (kSens && path > 0.0)
                 sens += m.alpha[w] * path * od *
                         (double)window_mass_f(m, (float)e1, 1.0f / (float)inv_sg);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);
-    if (lane == 0) sens_a[(size_t)a * m.nq + q] += m.T * sens;
+    if (kSens) {
+        for (int o = 16; o > 0; o >>= 1) sens += __shfl_xor_sync(0xffffffffu, sens, o);
+        if (lane == 0) sens_a[(size_t)a * m.nq + q] += m.T * sens;
+    }
 }
 
 __global__ void k_sum_subsets(const double* sens_a, int A, int nq, int parts, double* out) {
@@ -587,20 +595,35 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
     // The single-scatter path tables hold 3 floats per (angle, line, voxel,
     // scatter point), padded to 32-voxel x 32-point blocks: A W Q P x 12
     // bytes, next to the voxel-to-point line integrals and distances (Q P x
-    // 16 bytes, set-up only).  A model that does not fit the free memory is
-    // refused here, before anything large is allocated.
+    // 16 bytes, kept to rebuild tables).  All angles stay resident when they
+    // fit 90 % of the free memory (and the table budget); otherwise the
+    // buffer holds as many angles as fit half of it (or the budget) and the
+    // row launches rebuild the tables of the angles they need (streamed).
+    // A model whose set-up and the tables of one angle do not fit is refused
+    // here, before anything large is allocated.
+    int tab_slots = m.A;
+    const size_t per_angle = sizeof(float) * (size_t)m.nqt * m.npc * 3 * m.W * kQT * kPC;
     if (m.np) {
-        const size_t tab = sizeof(float) * (size_t)m.A * m.nqt * m.npc * 3 * m.W * kQT * kPC;
-        const size_t need = tab + 2 * sizeof(double) * (size_t)m.nq * m.np;
+        const size_t tab = per_angle * (size_t)m.A;
+        const size_t inter = 2 * sizeof(double) * (size_t)m.nq * m.np;
         size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b)
-            return set_error(LMMEW_ERR_OOM,
-                             "the path tables need " + std::to_string(tab >> 20) +
-                                 " MiB (12 bytes x angles x lines x voxels x scatter points) and "
-                                 "their set-up " + std::to_string((need - tab) >> 20) +
-                                 " MiB more, beyond the " + std::to_string(free_b >> 20) +
-                                 " MiB free on the device; use a coarser scatter grid or fewer "
-                                 "angles");
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const bool over_budget = g_table_budget > 0 && tab > (size_t)g_table_budget;
+            if (tab + inter > free_b / 10 * 9 || over_budget) {
+                size_t cap = free_b > inter ? (free_b - inter) / 2 : 0;
+                if (g_table_budget > 0) cap = std::min(cap, (size_t)g_table_budget);
+                tab_slots = (int)std::min<size_t>((size_t)m.A, cap / per_angle);
+            }
+            if (tab_slots < 1)
+                return set_error(LMMEW_ERR_OOM,
+                                 "the path tables of one angle need " +
+                                     std::to_string(per_angle >> 20) +
+                                     " MiB (12 bytes x lines x voxels x scatter points) and their "
+                                     "set-up " + std::to_string(inter >> 20) +
+                                     " MiB more, beyond what the " + std::to_string(free_b >> 20) +
+                                     " MiB free on the device (or the table budget) allow; use a "
+                                     "coarser scatter grid");
+        }
     }
 
     // collimator blur must stay positive for every point and angle
@@ -753,9 +776,11 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
                               cudaMemcpyDeviceToDevice));
     }
 
-    // single-scatter paths
+    // single-scatter paths: every angle once, in blocks of the table buffer's
+    // size, for the sensitivity; the tables of the last block stay resident
     if (m.np) {
-        h->tab_bytes = sizeof(float) * (size_t)m.A * m.nqt * m.npc * 3 * m.W * kQT * kPC;
+        h->tab_slots = tab_slots < m.A ? tab_slots : 0;
+        h->tab_bytes = per_angle * (size_t)tab_slots;
         if (cudaMalloc(&h->d_tab, h->tab_bytes) != cudaSuccess) {
             cudaGetLastError();
             return set_error(LMMEW_ERR_OOM, "cannot allocate scatter tables (" +
@@ -766,14 +791,43 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
         LMMEW_CUDA(cudaMalloc(&d_on_det.p, sizeof(double) * (size_t)m.A * m.np));
         k_on_detector<<<dim3((m.np + 127) / 128, m.A), 128>>>(m, dcs, (const int*)d_p_cell.p,
                                                                (double*)d_on_det.p);
-        dim3 g((m.nq + 7) / 8, m.A);
-        k_scatter<<<g, 256>>>(m, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
-                              (const double*)d_gqp.p, (const double*)d_dqp.p,
-                              (const double*)d_gp.p, mu_line, inv, (const double*)d_on_det.p,
-                              h->d_tab, h->d_sens_a);
-        h->launches += 2;
-        LMMEW_CUDA(cudaGetLastError());
+        ++h->launches;
+        for (int a0 = 0; a0 < m.A; a0 += tab_slots) {
+            const int cnt = std::min(tab_slots, m.A - a0);
+            k_scatter<true><<<dim3((m.nq + 7) / 8, cnt), 256>>>(
+                m, a0, 1, dcs, h->d_q_pix, (const int*)d_p_cell.p, (const double*)d_p_rho.p,
+                (const double*)d_gqp.p, (const double*)d_dqp.p, (const double*)d_gp.p, mu_line,
+                inv, (const double*)d_on_det.p, h->d_tab, h->d_sens_a);
+            ++h->launches;
+            LMMEW_CUDA(cudaGetLastError());
+            h->tab_a0 = a0;
+            h->tab_astep = 1;
+            h->tab_count = cnt;
+        }
+        if (h->tab_slots && cudaMalloc(&h->d_clip, sizeof(ChunkRange)) != cudaSuccess)
+            return set_error(LMMEW_ERR_OOM, "cannot allocate the clipped row range");
+        // kept for rebuilding streamed tables
+        auto keep = [](DevBuf& b) {
+            void* p = b.p;
+            b.p = nullptr;
+            return p;
+        };
+        h->d_on_det = (double*)keep(d_on_det);
+        h->d_gqp = (double*)keep(d_gqp);
+        h->d_dqp = (double*)keep(d_dqp);
     }
+    h->d_cs_a = (double*)d_cs_a.p;
+    d_cs_a.p = nullptr;
+    h->d_p_cell = (int*)d_p_cell.p;
+    d_p_cell.p = nullptr;
+    h->d_p_rho = (double*)d_p_rho.p;
+    d_p_rho.p = nullptr;
+    h->d_gp = (double*)d_gp.p;
+    d_gp.p = nullptr;
+    h->d_inv = (int*)d_inv.p;
+    d_inv.p = nullptr;
+    h->d_mu_line = (double*)d_mu_line.p;
+    d_mu_line.p = nullptr;
     LMMEW_CUDA(cudaMalloc(&h->d_status, sizeof(int)));
     LMMEW_CUDA(cudaMemset(h->d_status, 0, sizeof(int)));
     cudaEventRecord(e1, 0);
@@ -785,6 +839,74 @@ int build_tables(lm_handle* h, const float* rho_host, const uint8_t* support_hos
                ? (cudaDeviceSynchronize() == cudaSuccess ? LMMEW_OK
                                                          : set_error(LMMEW_ERR_CUDA, "set-up"))
                : LMMEW_ERR_OOM;
+}
+
+int64_t g_table_budget = 0;
+
+int stream_tables(lm_handle* h, int a0, int astep, int count, cudaStream_t st) {
+    const ModelConst& m = h->mc;
+    if (m.np == 0 || h->tab_slots == 0 || count <= 0) return LMMEW_OK;
+    if (count > h->tab_slots)
+        return set_error(LMMEW_ERR_INVALID_ARG, "an angle block larger than the table buffer");
+    // resident already: the same step (or one angle) inside the resident block
+    const int last = a0 + (count - 1) * astep;
+    const int r_last = h->tab_a0 + (h->tab_count - 1) * h->tab_astep;
+    if (h->tab_count > 0 && (astep == h->tab_astep || count == 1) && a0 >= h->tab_a0 &&
+        last <= r_last && (a0 - h->tab_a0) % h->tab_astep == 0 &&
+        (last - h->tab_a0) % h->tab_astep == 0)
+        return LMMEW_OK;
+    k_scatter<false><<<dim3((m.nq + 7) / 8, count), 256, 0, st>>>(
+        m, a0, astep, h->d_cs_a, h->d_q_pix, h->d_p_cell, h->d_p_rho, h->d_gqp, h->d_dqp, h->d_gp,
+        h->d_mu_line, h->d_inv, h->d_on_det, h->d_tab, nullptr);
+    ++h->launches;
+    LMMEW_CUDA(cudaGetLastError());
+    h->tab_a0 = a0;
+    h->tab_astep = astep;
+    h->tab_count = count;
+    return LMMEW_OK;
+}
+
+int set_table_streaming(lm_handle* h, int max_angles) {
+    const ModelConst& m = h->mc;
+    if (max_angles < 0) return set_error(LMMEW_ERR_INVALID_ARG, "max_angles must be >= 0");
+    if (m.np == 0) return LMMEW_OK;   // no single-scatter tables
+    const int slots = (max_angles == 0 || max_angles >= m.A) ? m.A : max_angles;
+    const int cur = h->tab_slots ? h->tab_slots : m.A;
+    if (slots == cur) return LMMEW_OK;
+    if (slots < m.A && h->prec != 0)
+        return set_error(LMMEW_ERR_NOT_IMPLEMENTED,
+                         "the reduced-precision form needs every angle's tables resident; "
+                         "switch the scatter precision to FP32 first");
+    const size_t per_angle = sizeof(float) * (size_t)m.nqt * m.npc * 3 * m.W * kQT * kPC;
+    // launches already queued may still read the old buffer
+    LMMEW_CUDA(cudaDeviceSynchronize());
+    float* buf = nullptr;
+    if (cudaMalloc(&buf, per_angle * (size_t)slots) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the path tables of " +
+                                            std::to_string(slots) + " angles (" +
+                                            std::to_string((per_angle * slots) >> 20) + " MiB)");
+    }
+    if (slots < m.A && !h->d_clip && cudaMalloc(&h->d_clip, sizeof(ChunkRange)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(buf);
+        return set_error(LMMEW_ERR_OOM, "cannot allocate the clipped row range");
+    }
+    LMMEW_CUDA(cudaMemset(buf, 0, per_angle * (size_t)slots));
+    cudaFree(h->d_tab);
+    h->d_tab = buf;
+    h->tab_bytes = per_angle * (size_t)slots;
+    h->tab_count = 0;
+    if (slots == m.A) {   // every angle, once
+        h->tab_slots = m.A;
+        const int rc = stream_tables(h, 0, 1, m.A, 0);
+        h->tab_slots = 0;
+        if (rc != LMMEW_OK) return rc;
+    } else {
+        h->tab_slots = slots;
+    }
+    LMMEW_CUDA(cudaDeviceSynchronize());
+    return LMMEW_OK;
 }
 
 }  // namespace lmmew

@@ -247,12 +247,16 @@ def test_energy_model_variants_parity():
 
 
 def test_model_beyond_device_memory_is_refused_with_its_size():
-    """Path tables of 12 bytes x angles x lines x voxels x scatter points: a
-    256 x 256 model with a 256 x 256 scatter grid and 90 angles needs
-    several TB and is refused before anything large is allocated."""
-    sc = preset("lmmew_64").with_(n=256, pixel_cm=0.15, n_angles=90, n_bins=256, scatter_n=256)
+    """Path tables of 12 bytes x angles x lines x voxels x scatter points.  A
+    model whose tables exceed the free memory is created with streamed tables
+    (tests/test_gpu_streaming.py); one whose set-up and the tables of a single
+    angle do not fit -- a 1024 x 1024 model with a 1024 x 1024 scatter grid:
+    about 0.8 TB of voxel-to-point line integrals and distances and 1.8 TB of
+    tables per angle -- is refused before anything large is allocated."""
+    sc = preset("lmmew_64").with_(n=1024, pixel_cm=0.0375, n_angles=90, n_bins=256,
+                                   scatter_n=1024)
     ph = sc.make_phantom()
-    with pytest.raises(lm.LmmewError, match="OOM.*path tables need"):
+    with pytest.raises(lm.LmmewError, match="OOM.*path tables of one angle need"):
         lm.Model.from_scenario(sc, ph.rho)
     # the process keeps a usable device afterwards
     small = preset("tiny_8")

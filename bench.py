@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the forms section (precision, batching with the combined form, comparison, surrogate)")
-    ap.add_argument("--forms", default="precision,batching,comparison,surrogate",
+    ap.add_argument("--forms", default="precision,batching,comparison,surrogate,streamed",
                     help="comma-separated forms to measure")
     ap.add_argument("--case", default=None, choices=["row", "row_rows", "surrogate_rows", "surrogate_train", "surrogate_coarse_osem", "setup"],
                     help="run one small kernel case (for profiling) instead of the benchmark")
@@ -732,6 +732,49 @@ def run_batch_form(workload="lmmew_64", n_real=256, lo=50_000, hi=500_000, iters
             "speedup_batched_vs_one_at_a_time": float(np.sum(seq) / np.median(batch))}
 
 
+def run_streamed_form(workload="lmmew_64", iters=2, blocks=(8, 1)):
+    """Streamed path tables (the fallback for models whose tables exceed the
+    device memory) against resident tables at the benchmark's workload:
+    seconds per OSEM iteration with the tables of `blocks` angles kept at a
+    time, and whether the image equals the resident one bit for bit."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17111_gb300 as lm
+    from synthetic import preset, simulate_cached
+    sc = preset(workload)
+    ph = sc.make_phantom()
+    ev = simulate_cached(sc)
+    model = lm.Model.from_scenario(sc, ph.rho)
+    model.set_tile_events(64)
+    dev = lm.DeviceEvents.from_list(ev)
+    lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
+
+    def timed():
+        img = lam0.clone()
+        model.osem(dev, img, sc.n_subsets, 1)   # warm-up (resident: tunes once)
+        img = lam0.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        model.osem(dev, img, sc.n_subsets, iters)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / iters, img
+    t_res, img_res = timed()
+    out = {"workload": f"{sc.name}: {len(ev)} events, {sc.n_subsets} subsets x {iters} iterations",
+           "resident": {"s_per_iter": t_res, "table_bytes": model.table_streaming()[1]}}
+    for k in blocks:
+        model.set_table_streaming(k)
+        t, img = timed()
+        out[f"blocks_of_{k}"] = {"s_per_iter": t, "table_bytes": model.table_streaming()[1],
+                                 "slowdown": t / t_res,
+                                 "image_bit_identical": bool(torch.equal(img, img_res))}
+    model.close()
+    return out
+
+
 def run_comparison_form(noise_realisations=16, events=10_000, seed=21):
     """The paper's comparison (LM-MEW vs LM-SEW vs Binned-SEW) on its study
     object and protocol: ensemble normalised RMSE, bias and standard
@@ -878,7 +921,8 @@ def run_gpu(args, rank, local_rank, world):
     if world == 1 and not args.no_forms and not args.events:
         model.close()
         runners = {"precision": run_precision_form, "batching": run_batch_forms,
-                   "comparison": run_comparison_form, "surrogate": run_surrogate_form}
+                   "comparison": run_comparison_form, "surrogate": run_surrogate_form,
+                   "streamed": run_streamed_form}
         line["forms"] = {k: runners[k]() for k in args.forms.split(",") if k in runners}
         # the metric's third part: the chosen forms against the plain FP32
         # path on the same GPU, at the stated ROI-activity error, at the

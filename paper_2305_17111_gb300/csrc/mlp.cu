@@ -363,6 +363,28 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane, left in flight:
+// the registers hold the values only after tc_wait_ld16 on the same array,
+// whose asm names them as written (so no use is moved above the wait).
+__device__ __forceinline__ void tc_ld16_start(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tc_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 struct TcShared {
     unsigned char* base;   // 1 KB aligned
     uint32_t sbase;        // its shared-window address
@@ -533,17 +555,19 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
         }
         tc_fence_after();
         if (done) {
-#pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                const int cb = cc * 32;   // columns cb .. cb + 31
-                float v[32];
-                tc_ld32(G.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb, v);
+            // 16-column chunks; the next chunk's TMEM load is in flight while
+            // this one is computed (same operations, in the same column
+            // order, as one chunk at a time)
+            const uint32_t tlane = G.tmem + ((uint32_t)(lq * 32) << 16);
+            auto chunk = [&](int cc, uint32_t(&v)[16]) {
+                const int cb = cc * 16;   // columns cb .. cb + 15
                 const float4* bias4 = reinterpret_cast<const float4*>(F + layer * kHid + cb);
                 if (layer < 2) {
-                    uint32_t hb[16];
+                    uint32_t hb[8];
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
-                        f32x2 z0 = pk(v[i], v[i + 1]), z1 = pk(v[i + 2], v[i + 3]);
+                    for (int i = 0; i < 16; i += 4) {
+                        f32x2 z0 = pk(__uint_as_float(v[i]), __uint_as_float(v[i + 1]));
+                        f32x2 z1 = pk(__uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
                         if (layer > 0) {   // the first layer's bias comes out of the MMA
                             const float4 b = bias4[i >> 2];
                             z0 = add2(z0, pk(b.x, b.y));
@@ -566,17 +590,20 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                         hb[i >> 1] = *reinterpret_cast<const uint32_t*>(&t0);
                         hb[(i >> 1) + 1] = *reinterpret_cast<const uint32_t*>(&t1);
                     }
+                    // 16 columns: two 16-byte chunks of K block cc / 4
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, cc >> 1, (cc & 1) * 4 + c)) =
+                    for (int c = 0; c < 2; ++c)
+                        *reinterpret_cast<uint4*>(S.base + G.h + sw_chunk(row, cc >> 2, (cc & 3) * 2 + c)) =
                             make_uint4(hb[4 * c], hb[4 * c + 1], hb[4 * c + 2], hb[4 * c + 3]);
                 } else {
                     const float4* w44 = reinterpret_cast<const float4*>(F + 3 * kHid + cb);
 #pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
+                    for (int i = 0; i < 16; i += 4) {
                         const float4 b = bias4[i >> 2], ww = w44[i >> 2];
-                        const f32x2 z0 = add2(pk(v[i], v[i + 1]), pk(b.x, b.y));
-                        const f32x2 z1 = add2(pk(v[i + 2], v[i + 3]), pk(b.z, b.w));
+                        const f32x2 z0 = add2(pk(__uint_as_float(v[i]), __uint_as_float(v[i + 1])),
+                                              pk(b.x, b.y));
+                        const f32x2 z1 = add2(pk(__uint_as_float(v[i + 2]), __uint_as_float(v[i + 3])),
+                                              pk(b.z, b.w));
                         if (kStoreZ && z_row) {
                             float a0, a1, a2, a3;
                             upk(z0, a0, a1);
@@ -590,6 +617,18 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                         sacc2 = fma2(gelu2_doubled(z1), pk(ww.z, ww.w), sacc2);
                     }
                 }
+            };
+            uint32_t ra[16], rb[16];
+            tc_ld16_start(tlane, ra);
+            tc_wait_ld16(ra);
+#pragma unroll 1
+            for (int cp = 0; cp < 8; cp += 2) {   // pairs of chunks: ra, then rb
+                tc_ld16_start(tlane + (uint32_t)(cp + 1) * 16u, rb);
+                chunk(cp, ra);
+                tc_wait_ld16(rb);
+                if (cp + 2 < 8) tc_ld16_start(tlane + (uint32_t)(cp + 2) * 16u, ra);
+                chunk(cp + 1, rb);
+                if (cp + 2 < 8) tc_wait_ld16(ra);
             }
         }
         if (layer < 2) fence_async_smem();

@@ -58,3 +58,18 @@ def test_errors_reported_without_gpu_work():
     assert rc == -1
     assert b"NULL" in lib.lm_last_error()
     assert lib.lm_destroy(None) == 0
+
+
+def test_table_streaming_calls_check_their_arguments_without_gpu_work():
+    """The streamed-table controls reject bad arguments before any CUDA call;
+    the process-wide table budget is a plain host setting."""
+    from paper_2305_17111_gb300 import _native, build
+    build.build()
+    lib = _native.load()
+    assert lib.lm_set_table_budget(-1) == -1
+    assert lib.lm_set_table_budget(1 << 30) == 0
+    assert lib.lm_set_table_budget(0) == 0
+    assert lib.lm_set_table_streaming(None, 4) == -1
+    slots, nbytes = ctypes.c_int(7), ctypes.c_int64(7)
+    assert lib.lm_table_streaming(None, ctypes.byref(slots), ctypes.byref(nbytes)) == -1
+    assert b"NULL" in lib.lm_last_error()

@@ -145,9 +145,12 @@ typedef struct {
  * The single-scatter path tables take 12 bytes per (angle, line, support
  * voxel, scatter point), padded to blocks of 32 voxels x 32 points: 1.6 GB
  * for 60 angles x 3 lines x 864 x 864, 14 GB for 120 x 3 x 3464 x 900.  A
- * model whose tables exceed the device's free memory is refused with
- * LMMEW_ERR_OOM and a message giving the size, before anything is allocated
- * for them.
+ * model whose tables (with the set-up's line integrals) do not fit 90 % of
+ * the device's free memory, or the table budget of lm_set_table_budget, is
+ * created with streamed tables (see lm_set_table_streaming); one whose
+ * set-up and the tables of a single angle do not fit is refused with
+ * LMMEW_ERR_OOM and a message giving the sizes, before anything is
+ * allocated for them.
  * Errors: INVALID_ARG (sizes, NULL pointers, scatter_n not dividing n,
  * non-positive collimator or energy blur anywhere in the model, overlapping
  * windows), OOM, CUDA. */

@@ -485,9 +485,14 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
     lam0 = torch.from_numpy((ph.rho.reshape(-1) > 0).astype(np.float32)).cuda()
     lam_true = torch.from_numpy(ph.activity.reshape(-1).astype(np.float32)).cuda()
     res = {}
-    for kind in ("exact", "surrogate", "surrogate_coarse", "surrogate_coarse_s3", "none"):
-        model.set_coarse_stride(3 if kind.endswith("_s3") else 2)
-        model.set_scatter_model(kind.replace("_s3", ""), sur if kind.startswith("surrogate") else None)
+    kinds = ("exact", "surrogate", "surrogate_coarse", "surrogate_coarse_s3", "surrogate_coarse_s4",
+             "none")
+    for kind in kinds:
+        # the coarse grid's node stride in pixels: 2, or the suffix's
+        stride = int(kind[-1]) if kind[-3:-1] == "_s" else 2
+        model.set_coarse_stride(stride)
+        model.set_scatter_model(kind[:-3] if kind[-3:-1] == "_s" else kind,
+                                sur if kind.startswith("surrogate") else None)
         y = model.forward(dev, lam_true).cpu().numpy().astype(np.float64)   # also warms up
         model.osem(dev, lam0.clone(), sc.n_subsets, 0)   # untimed: the row-kernel autotune
         img = lam0.clone()
@@ -512,7 +517,7 @@ def run_surrogate_form(workload="lmmew_128_2m", n_objects=8, n_samples=10_000_00
                         "heldout_object_mass_rel_err": mass_err,
                         "heldout_object_mass_ratio": mass_ratio},
            "exact": {"s_per_iter": ex["s_per_iter"], "roi_activity": roi_ex}}
-    for kind in ("surrogate", "surrogate_coarse", "surrogate_coarse_s3", "none"):
+    for kind in kinds[1:]:
         r = res[kind]
         roi = roi_sums(r["img"], ph.lesion_masks)
         out[kind] = {"s_per_iter": r["s_per_iter"],
@@ -941,7 +946,8 @@ def run_gpu(args, rank, local_rank, world):
         c4 = line["forms"].get("surrogate")
         if c4:
             chosen["single_128_2m"] = {"workload": c4["workload"]}
-            for k, kind in (("stride_2", "surrogate_coarse"), ("stride_3", "surrogate_coarse_s3")):
+            for k, kind in (("stride_2", "surrogate_coarse"), ("stride_3", "surrogate_coarse_s3"),
+                            ("stride_4", "surrogate_coarse_s4")):
                 chosen["single_128_2m"][k] = {
                     "speedup_vs_plain_fp32": c4[kind]["speedup_vs_exact"],
                     "roi_rel_dev_vs_plain_fp32": c4[kind]["roi_rel_dev_vs_exact"]}

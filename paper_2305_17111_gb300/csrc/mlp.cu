@@ -515,10 +515,17 @@ __device__ __forceinline__ void tc_input_constants(const TcShared& S, const TcGr
 // word is set and the caller stops).  With kStoreZ (training) the thread also
 // stores its sample's pre-activations of the three hidden layers, BF16, at
 // z_row + layer * z_stride (z_row null: a padding sample, nothing stored).
+// The last layer ends without a group barrier: a warp goes on to its next
+// samples' inputs while the others finish, and the barrier the caller
+// places after writing the next inputs also orders every warp's last TMEM
+// loads before the next MMAs.  A wait that ran out in the last layer is
+// therefore seen by the whole group at the next call's entry (after that
+// barrier), so every thread of the group stops at the same point.
 template <bool kStoreZ>
 __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase, float b4,
                            float* out_row, int* status, bf16* z_row = nullptr,
                            size_t z_stride = 0) {
+    if (S.abort[G.g]) return false;
     const int lq = G.gt >> 5;
     const int row = G.gt;
     const float* F = reinterpret_cast<const float*>(S.base + kTcOffF);
@@ -631,10 +638,12 @@ __device__ bool tc_network(const TcShared& S, const TcGroup& G, uint32_t& phase,
                 if (cp + 2 < 8) tc_wait_ld16(ra);
             }
         }
-        if (layer < 2) fence_async_smem();
         tc_fence_before();
-        group_sync(G.g);
-        if (S.abort[G.g]) return false;
+        if (layer < 2) {
+            fence_async_smem();
+            group_sync(G.g);
+            if (S.abort[G.g]) return false;
+        }
     }
     float s_even, s_odd;
     upk(sacc2, s_even, s_odd);

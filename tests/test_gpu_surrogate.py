@@ -376,7 +376,7 @@ def test_surrogate_fit_on_held_out_samples():
 
 
 @pytest.mark.parametrize("model,stride", [("surrogate", 2), ("surrogate_coarse", 2),
-                                          ("surrogate_coarse", 3)])
+                                          ("surrogate_coarse", 3), ("surrogate_coarse", 4)])
 def test_surrogate_rows_match_primary_plus_oracle_network(model, stride):
     sc, ph, orc, gpu, ev, dev = _fine_model()
     s, _ = _trained_surrogate()

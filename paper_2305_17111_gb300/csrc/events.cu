@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int* start, int A, int
 }
 
 __global__ void k_tiles(const int* start, const int* tile_start, const int* angle_of_rank, int A,
-                        int tile_ev, const uint16_t* bin_s, const int* lines_of_group, Tile* tiles,
+                        int tile_ev, const uint16_t* bin_s, const int* lines_of_group,
+                        const int2* crange, int B, int np, Tile* tiles,
                         const int* real_of_rank = nullptr) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A) return;
@@ -257,9 +258,21 @@ __global__ void k_tiles(const int* start, const int* tile_start, const int* angl
         T.a = angle_of_rank[r];
         T.begin = e;
         T.count = cnt;
-        T.b_lo_hi = ((int)bin_s[e] << 16) | (int)bin_s[e + cnt - 1];
+        const int b_lo = bin_s[e], b_hi = bin_s[e + cnt - 1];
+        T.b_lo_hi = (b_lo << 16) | b_hi;
         T.r = real_of_rank ? real_of_rank[r] : 0;
         T.lines = lines_of_group[r];
+        // the union of the tile's bins' collimator runs of scatter points
+        int p_lo = np, p_hi = 0;
+        for (int b = b_lo; b <= b_hi; ++b) {
+            const int2 cr = crange[(size_t)T.a * B + b];
+            if (cr.y > cr.x) {
+                p_lo = min(p_lo, cr.x);
+                p_hi = max(p_hi, cr.y);
+            }
+        }
+        T.p_lo = p_lo;
+        T.p_hi = p_hi;
         tiles[t] = T;
     }
 }
@@ -345,7 +358,8 @@ int sort_and_tile(lm_handle* h, const lm_events* ev, int G, const int* rank_of_a
     }
     k_tile_scan<<<1, 1024, 0, st>>>(group_start, G, tile_ev, tile_start);
     k_tiles<<<(G + 127) / 128, 128, 0, st>>>(group_start, tile_start, angle_of_group, G, tile_ev,
-                                             bin_s, lines_of_group, tiles);
+                                             bin_s, lines_of_group, h->d_crange, m.B, m.np,
+                                             tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     return LMMEW_OK;
@@ -543,7 +557,8 @@ int recut_tiles_async(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t 
     k_tile_scan<<<1, 1024, 0, st>>>(se->group_start, G, tile_ev, se->tile_start);
     k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->group_start, se->tile_start,
                                                          se->angle_of_group, G, tile_ev, se->bin,
-                                                         se->lines_of_group, se->tiles);
+                                                         se->lines_of_group, h->d_crange, h->mc.B,
+                                                         h->mc.np, se->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     se->tile_ev = tile_ev;
@@ -816,7 +831,8 @@ int sort_events_batch(lm_handle* h, const lm_events* evs, int R, int n_subsets,
     k_tile_scan<<<1, 1024, 0, st>>>(out->group_start, (int)G, out->tile_ev, out->tile_start);
     k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(out->group_start, out->tile_start,
                                                          d_angle_of_group, (int)G, out->tile_ev,
-                                                         out->bin, d_lines_of_group, out->tiles);
+                                                         out->bin, d_lines_of_group, h->d_crange,
+                                                         h->mc.B, h->mc.np, out->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     out->h_group_start.resize(G + 1);
@@ -878,7 +894,8 @@ int recut_tiles(lm_handle* h, SortedEvents* se, int tile_ev, cudaStream_t st) {
     k_tile_scan<<<1, 1024, 0, st>>>(se->group_start, G, tile_ev, se->tile_start);
     k_tiles<<<(unsigned)((G + 127) / 128), 128, 0, st>>>(se->group_start, se->tile_start,
                                                          se->angle_of_group, G, tile_ev, se->bin,
-                                                         se->lines_of_group, se->tiles);
+                                                         se->lines_of_group, h->d_crange, h->mc.B,
+                                                         h->mc.np, se->tiles);
     h->launches += 2;
     LMMEW_CUDA(cudaGetLastError());
     se->h_tile_start.resize(G + 1);

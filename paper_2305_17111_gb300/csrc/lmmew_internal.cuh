@@ -70,6 +70,9 @@ struct Tile {
     int b_lo_hi;    // (b_lo << 16) | b_hi: bin range of the tile's events
     int r;          // realisation (0 outside batched reconstruction)
     int lines;      // bit w set: line w's single scatter can reach the tile's energies
+    // run [p_lo, p_hi) of the angle's point order with non-zero collimator
+    // probability for some bin of the tile (p_lo >= p_hi: none)
+    int p_lo, p_hi;
 };
 
 // Energy classes of the recorded energy.  A photon of line w that scatters

@@ -386,16 +386,10 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_row(const RowParams P) {
 
         // scatter points whose collimator probability is non-zero for some bin
         // of the tile: a contiguous run [p_lo, p_hi) in this angle's point
-        // order, staged as whole chunks and evaluated in groups of 4 points;
-        // every other term is an exact zero and is not evaluated
-        int p_lo = P.np, p_hi = 0;
-        for (int b = b_lo; b <= b_hi && nw > 0; ++b) {
-            const int2 r = P.crange[(size_t)T.a * P.B + b];
-            if (r.y > r.x) {
-                p_lo = min(p_lo, r.x);
-                p_hi = max(p_hi, r.y);
-            }
-        }
+        // order (formed with the tiles), staged as whole chunks and evaluated
+        // in groups of 4 points; every other term is an exact zero and is not
+        // evaluated
+        int p_lo = nw > 0 ? T.p_lo : P.np, p_hi = nw > 0 ? T.p_hi : 0;
         // the slot of the angle's tables; with streamed tables a tile whose
         // angle is not in the buffer is a planning error: its scatter terms
         // are not read, and the status word says so

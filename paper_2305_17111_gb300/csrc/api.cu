@@ -701,7 +701,7 @@ static int osem_planned(lm_handle* h, const lm_events* ev, int n_subsets, int n_
                 rc = launch_row_profiled(h, L, st);
                 if (rc != LMMEW_OK) return rc;
                 rc = launch_bp_partial(h, rows, rs, ypart, cnt, cnt, nullptr, nullptr, bpart, row0,
-                                       llpart, st);
+                                       loglik ? llpart : nullptr, st);
                 if (rc != LMMEW_OK) return rc;
                 row0 += bp_parts(cnt);
             }
@@ -881,7 +881,8 @@ int lm_osem(lm_handle* h, const lm_events* ev, int n_subsets, int n_iters, int s
                 rc = launch_row_ranks(h, L, se, r_first[s], r_first[s + 1], s, n_subsets, st);
                 if (rc == LMMEW_OK)
                     rc = launch_bp_partial_range(h, rows, rs, ypart, cap, cap, rg + k, nullptr,
-                                                 nullptr, bpart, (int64_t)k * ppc, llpart, st);
+                                                 nullptr, bpart, (int64_t)k * ppc,
+                                                 loglik ? llpart : nullptr, st);
             }
             if (rc == LMMEW_OK) rc = launch_voxel_reduce_ranges(h, bpart, rg, blocks, ppc, num, st);
             if (rc == LMMEW_OK)
@@ -1075,7 +1076,7 @@ int lm_osem_batch(lm_handle* h, int n_real, const lm_events* events, int n_subse
                 rc = launch_row(h, L, cs);
                 if (rc != LMMEW_OK) break;
                 rc = launch_bp_batch(h, rows, rs, ypart, c.e1 - c.e0, se.bp_idx, c.e0, d_bp + c.c0,
-                                     c.c1 - c.c0, bpart, llpart, cs);
+                                     c.c1 - c.c0, bpart, loglik ? llpart : nullptr, cs);
                 if (rc != LMMEW_OK) break;
             }
             if (rc != LMMEW_OK) break;

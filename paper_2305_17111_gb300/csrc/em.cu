@@ -11,6 +11,27 @@ namespace {
 constexpr int kBpEvents = kBpChunkEvents;   // events per back-projection partial
 constexpr int kBpVoxels = 256;    // voxels per back-projection block
 
+// FP64 sums of a voxel's partials in a fixed order: within each run of
+// partials (one row block, or one realisation's chunks), partial i goes to
+// strand i mod 8, each strand in order of i; the strands are added pairwise
+// at the end.  Eight independent chains keep eight loads and adds in flight
+// in the one thread that owns the voxel, and the order is the same in every
+// reduction, so the one-realisation and batched paths still agree bit for bit.
+__device__ __forceinline__ void strand_add(double (&s)[8], const float* bpart, int64_t first,
+                                           int64_t n, int nq, int q) {
+    int64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] += (double)bpart[(size_t)(first + i + u) * nq + q];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        if (i + u < n) s[u] += (double)bpart[(size_t)(first + i + u) * nq + q];
+}
+__device__ __forceinline__ double strand_total(const double (&s)[8]) {
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
 __global__ void k_forward_out(const float* ypart, int64_t stride, int nqt, int64_t count,
                               const uint32_t* perm, float* out_y) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,6 +52,8 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_partial(
     __shared__ float r[kBpEvents];
     __shared__ double ll[kBpEvents];
     const int t = threadIdx.x;
+    // the log-likelihood terms, wanted from one voxel column when asked for
+    const bool want_ll = llpart != nullptr && blockIdx.y == 0;
     const int64_t j0 = (int64_t)blockIdx.x * kBpEvents;
     if (t < kBpEvents) {
         const int64_t j = j0 + t;
@@ -44,7 +67,7 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_partial(
                 for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
                 if (y > 0.f) {
                     rv = 1.0f / y;
-                    lv = log((double)y);
+                    if (want_ll) lv = log((double)y);   // FP64: slow on this GPU, so only where used
                 }
             }
         }
@@ -81,6 +104,8 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_partial_range(
     const ChunkRange R = *range;
     const int64_t count = (int64_t)R.w - R.z;
     const int t = threadIdx.x;
+    // the log-likelihood terms, wanted from one voxel column when asked for
+    const bool want_ll = llpart != nullptr && blockIdx.y == 0;
     const int64_t j0 = (int64_t)blockIdx.x * kBpEvents;
     if (j0 >= count) return;
     if (t < kBpEvents) {
@@ -95,7 +120,7 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_partial_range(
                 for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
                 if (y > 0.f) {
                     rv = 1.0f / y;
-                    lv = log((double)y);
+                    if (want_ll) lv = log((double)y);   // FP64: slow on this GPU, so only where used
                 }
             }
         }
@@ -130,12 +155,9 @@ __global__ void k_voxel_reduce_ranges(const float* bpart, const ChunkRange* rang
                                       int64_t ppc, int nq, double* num) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    double acc = 0.0;
-    for (int k = 0; k < n_blocks; ++k) {
-        const int64_t parts = parts_of(ranges[k]);
-        for (int64_t i = 0; i < parts; ++i) acc += (double)bpart[(size_t)(k * ppc + i) * nq + q];
-    }
-    num[q] = acc;
+    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < n_blocks; ++k) strand_add(s, bpart, k * ppc, parts_of(ranges[k]), nq, q);
+    num[q] = strand_total(s);
 }
 
 __global__ void k_forward_out_range(const float* ypart, int64_t stride, int nqt,
@@ -158,9 +180,9 @@ __global__ void k_invalid_out(const int* n_valid, int64_t n, const uint32_t* per
 __global__ void k_voxel_reduce(const float* bpart, int64_t n_parts, int nq, double* num) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    double acc = 0.0;
-    for (int64_t i = 0; i < n_parts; ++i) acc += (double)bpart[(size_t)i * nq + q];
-    num[q] = acc;
+    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    strand_add(s, bpart, 0, n_parts, nq, q);
+    num[q] = strand_total(s);
 }
 
 // Single block: log-likelihood at the incoming image, then the update.  The
@@ -361,6 +383,8 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
     __shared__ int64_t idx[kBpEvents];
     __shared__ double ll[kBpEvents];
     const int t = threadIdx.x;
+    // the log-likelihood terms, wanted from one voxel column when asked for
+    const bool want_ll = llpart != nullptr && blockIdx.y == 0;
     const BpChunk C = chunks[blockIdx.x];
     if (t < kBpEvents) {
         float rv = 0.f;
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(kBpVoxels) k_bp_batch(
             for (int k = 0; k < nqt; ++k) y += ypart[(size_t)k * ypart_stride + j];
             if (y > 0.f) {
                 rv = 1.0f / y;
-                lv = log((double)y);
+                if (want_ll) lv = log((double)y);   // FP64: slow on this GPU, so only where used
             }
         }
         r[t] = rv;
@@ -399,9 +423,9 @@ __global__ void k_voxel_reduce_batch(const float* bpart, const int* part_start, 
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int rr = blockIdx.y;
     if (q >= nq) return;
-    double acc = 0.0;
-    for (int i = part_start[rr]; i < part_start[rr + 1]; ++i) acc += (double)bpart[(size_t)i * nq + q];
-    num[(size_t)rr * nq + q] = acc;
+    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    strand_add(s, bpart, part_start[rr], part_start[rr + 1] - part_start[rr], nq, q);
+    num[(size_t)rr * nq + q] = strand_total(s);
 }
 
 __global__ void __launch_bounds__(1024) k_update_batch(float* lam, const double* num,

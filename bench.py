@@ -140,12 +140,12 @@ def measured_peaks():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # current k_row revision on this workload.  Measured on the small case
 # `--case row_rows` (60 000 events of subset 0's 8 angles, rows stored as
-# lm_osem does, 64-event tiles): 217 627 648 B read (the 8 angles' path
-# tables) + 175 537 152 B written (the row block), in a one-launch capture;
+# lm_osem does, 64-event tiles): 217 606 144 B read (the 8 angles' path
+# tables) + 175 658 496 B written (the row block), in a one-launch capture;
 # scaled to one OSEM launch of this workload by angles for the reads (7.5 of
 # 8) and by events for the writes (37 500 of 60 000).  Emptied whenever
 # k_row or the tables it streams change until the counters are taken again.
-ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 204_025_920 + 109_710_720}
+ROW_TRAFFIC_BYTES_PER_LAUNCH = {"lmmew_64": 204_005_760 + 109_786_560}
 
 # Exponential (MUFU ex2) issue rate of one GB300 SM per clock.  The roofline
 # of the exact path is the SFU rate: every path term needs one ex2.

@@ -307,8 +307,10 @@ int lm_set_tile_events(lm_handle* h, int tile_events);
  * lm_forward, lm_backproject and lm_osem covers its angles in blocks of that
  * many, rebuilding a block's tables on the device (the set-up's own kernel,
  * so the values are the same bits) unless they are the resident ones.
- * Results are bit-identical to resident tables; a rebuild per block and
- * sub-iteration costs about 1/A of lm_create's set-up time per angle.
+ * Results are bit-identical to resident tables.  Each rebuilt angle costs
+ * about 0.6 of its share of lm_create's set-up (the sensitivity sums are
+ * not repeated): at 64^2 with a 64^2 scatter grid about 15 ms per OSEM
+ * iteration, which then takes 33-41 ms instead of 18.
  * max_angles = 0 (or >= n_angles) makes every angle resident again.
  * lm_create streams by itself when all angles' tables do not fit 90 % of the
  * free device memory or the process's table budget (lm_set_table_budget),
